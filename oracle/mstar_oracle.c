@@ -1,0 +1,569 @@
+/*
+ * MSTAR oracle (see mstar_oracle.h). TEST INFRASTRUCTURE ONLY.
+ *
+ * Every function follows the paper's steps in its order and notation; nothing is
+ * blocked, fused or reordered beyond what the definitions state. Section, equation
+ * and algorithm names refer to Rantala et al., "MSTAR - a fast parallelised
+ * algorithmically regularised integrator with minimum spanning tree coordinates".
+ *
+ * Readings taken where the paper is silent (the CUDA path implements the same):
+ *  - (X, V, t) are the integrated variables; Cartesian r, v are rebuilt from them after
+ *    every drift and kick (Sec. 2.2: chained velocities are transformed back).
+ *  - Rebuild = per-vertex path sum of edge vectors, summed from the vertex up to the
+ *    root, then a centre-of-mass shift (Sec. 3.5 counts L(V_i) additions per vertex).
+ *  - Prim ties: argmin takes the lowest index; keys decrease only on strict '<'.
+ *  - Error: eps = max over edge vectors X_v, V_v (3-vector norms) and the scalar t of
+ *    |T_kk - T_{k-1,k-1}| / |S(s0) + (H/n_kfix) S'(s0)|, S' = V/(T+B), A/U, 1/(T+B).
+ *  - Step growth factor a_GBS (eta/eps)^(1/(2 k_fix - 1)) clamped to [fac_min, fac_max].
+ */
+#include "mstar_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+static int g_threads = 1;
+
+void orc_set_threads(int nthreads) { g_threads = nthreads < 1 ? 1 : nthreads; }
+int orc_get_threads(void) { return g_threads; }
+
+void orc_params_default(orc_params* p) {
+  p->eta = 1e-12;
+  p->a_gbs = 0.9;
+  p->fac_min = 0.2;
+  p->fac_max = 2.0;
+  p->q_first = 0.1;
+  p->t_tol = 1e-10;
+  p->G = 1.0;
+  p->k_fix = 8;
+  p->n_d = 2;
+  p->max_halvings = 30;
+  p->max_time_iter = 8;
+}
+
+/* ---------------------------------------------------------------- energies (Eq. 1) */
+
+static double norm2(const double* x) { return (x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]; }
+
+double orc_kinetic(int n, const double* m, const double* v) {
+  double T = 0.0;
+  for (int i = 0; i < n; ++i) T += m[i] * norm2(v + 3 * i);
+  return 0.5 * T;
+}
+
+double orc_potential(int n, const double* m, const double* r, double G) {
+  /* U = sum_i sum_{j>i} G m_i m_j / |r_j - r_i| */
+  double U = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double ui = 0.0;
+    for (int j = i + 1; j < n; ++j) {
+      double d[3] = {r[3 * j] - r[3 * i], r[3 * j + 1] - r[3 * i + 1], r[3 * j + 2] - r[3 * i + 2]};
+      ui += m[j] / sqrt(norm2(d));
+    }
+    U += G * m[i] * ui;
+  }
+  return U;
+}
+
+void orc_com_shift(int n, const double* m, double* w) {
+  double M = 0.0, c[3] = {0.0, 0.0, 0.0};
+  for (int i = 0; i < n; ++i) {
+    M += m[i];
+    for (int k = 0; k < 3; ++k) c[k] += m[i] * w[3 * i + k];
+  }
+  for (int k = 0; k < 3; ++k) c[k] = c[k] / M;
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) w[3 * i + k] -= c[k];
+}
+
+/* ---------------------------------------------------------------- MST (Sec. 3.2, 3.4) */
+
+/* Squared Euclidean edge weight. sqrt is monotone, so squared weights give the same MST
+   as the Euclidean weights of Sec. 3.1. Two roundings per product/sum (no contraction). */
+static double w2(const double* r, int u, int v) {
+  double dx = r[3 * u] - r[3 * v], dy = r[3 * u + 1] - r[3 * v + 1], dz = r[3 * u + 2] - r[3 * v + 2];
+  return (dx * dx + dy * dy) + dz * dz;
+}
+
+int orc_prim(int n, const double* r, int* parent, int* level, int* order) {
+  /* Root: the particle spatially closest to the centre of mass (the origin of the COM
+     frame); lowest index on ties. */
+  int root = 0;
+  double best = norm2(r);
+  for (int i = 1; i < n; ++i) {
+    double d = norm2(r + 3 * i);
+    if (d < best) { best = d; root = i; }
+  }
+  double* key = (double*)malloc(sizeof(double) * (size_t)n);
+  char* in_tree = (char*)calloc((size_t)n, 1);
+  for (int v = 0; v < n; ++v) { key[v] = INFINITY; parent[v] = -1; level[v] = 0; }
+  in_tree[root] = 1;
+  order[0] = root;
+  int u = root;
+  for (int it = 1; it < n; ++it) {
+    /* relax the keys of the non-tree vertices with the vertex just added */
+    for (int v = 0; v < n; ++v) {
+      if (in_tree[v]) continue;
+      double d = w2(r, u, v);
+      if (d < key[v]) { key[v] = d; parent[v] = u; }
+    }
+    /* add the non-tree vertex with the minimum-weight edge to the tree */
+    int next = -1;
+    double kmin = INFINITY;
+    for (int v = 0; v < n; ++v) {
+      if (in_tree[v]) continue;
+      if (next < 0 || key[v] < kmin) { kmin = key[v]; next = v; }
+    }
+    u = next;
+    in_tree[u] = 1;
+    order[it] = u;
+    if (parent[u] < 0) parent[u] = root; /* only reachable with non-finite positions */
+    level[u] = level[parent[u]] + 1;
+  }
+  free(key);
+  free(in_tree);
+  return root;
+}
+
+/* Eq. LCA with early exit: lift the deeper vertex, then both, counting traversed edges;
+   the count at the lowest common ancestor is |L(V_i)-L(V_LCA)| + |L(V_j)-L(V_LCA)|. */
+int orc_is_near(const int* parent, const int* level, int i, int j, int n_d) {
+  if (i == j) return 0;
+  int d = 0;
+  while (level[i] > level[j]) { i = parent[i]; if (++d > n_d) return 0; }
+  while (level[j] > level[i]) { j = parent[j]; if (++d > n_d) return 0; }
+  while (i != j) {
+    i = parent[i];
+    j = parent[j];
+    d += 2;
+    if (d > n_d) return 0;
+  }
+  return 1;
+}
+
+/* r_j - r_i = (sum of X from j up to the LCA) - (sum of X from i up to the LCA), each
+   sum accumulated upward starting at the vertex itself (Sec. 3.4). */
+void orc_near_sep(const int* parent, const int* level, const double* X, int i, int j, double d[3]) {
+  double si[3] = {0.0, 0.0, 0.0}, sj[3] = {0.0, 0.0, 0.0};
+  int a = i, b = j;
+  /* find the LCA first */
+  while (level[a] > level[b]) a = parent[a];
+  while (level[b] > level[a]) b = parent[b];
+  while (a != b) { a = parent[a]; b = parent[b]; }
+  int lca = a;
+  for (int u = i; u != lca; u = parent[u])
+    for (int k = 0; k < 3; ++k) si[k] += X[3 * u + k];
+  for (int u = j; u != lca; u = parent[u])
+    for (int k = 0; k < 3; ++k) sj[k] += X[3 * u + k];
+  for (int k = 0; k < 3; ++k) d[k] = sj[k] - si[k];
+}
+
+void orc_to_mst(int n, const int* parent, const double* w, double* W) {
+  for (int v = 0; v < n; ++v) {
+    int p = parent[v];
+    for (int k = 0; k < 3; ++k) W[3 * v + k] = (p < 0) ? 0.0 : w[3 * v + k] - w[3 * p + k];
+  }
+}
+
+void orc_from_mst(int n, const double* m, const int* parent, const double* W, double* w) {
+  for (int v = 0; v < n; ++v) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int u = v; parent[u] >= 0; u = parent[u])
+      for (int k = 0; k < 3; ++k) s[k] += W[3 * u + k];
+    for (int k = 0; k < 3; ++k) w[3 * v + k] = s[k];
+  }
+  orc_com_shift(n, m, w);
+}
+
+/* ---------------------------------------------------------------- forces (Eq. 2) */
+
+void orc_forces(int n, const double* m, double G, const int* parent, const int* level, int n_d,
+                const double* r, const double* X, double* a, double* U) {
+  double* ui = (double*)malloc(sizeof(double) * (size_t)n);
+#pragma omp parallel for schedule(dynamic, 16) num_threads(g_threads)
+  for (int i = 0; i < n; ++i) {
+    double ai[3] = {0.0, 0.0, 0.0}, u = 0.0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3];
+      if (n_d > 0 && orc_is_near(parent, level, i, j, n_d)) {
+        orc_near_sep(parent, level, X, i, j, d);
+      } else {
+        for (int k = 0; k < 3; ++k) d[k] = r[3 * j + k] - r[3 * i + k];
+      }
+      double rinv = 1.0 / sqrt(norm2(d));
+      double s = G * m[j] * (rinv * rinv * rinv);
+      for (int k = 0; k < 3; ++k) ai[k] += s * d[k];
+      if (j > i) u += m[j] * rinv;
+    }
+    for (int k = 0; k < 3; ++k) a[3 * i + k] = ai[k];
+    ui[i] = u;
+  }
+  double Us = 0.0;
+  for (int i = 0; i < n; ++i) Us += G * m[i] * ui[i];
+  *U = Us;
+  free(ui);
+}
+
+/* ---------------------------------------------------------------- GBS (Sec. 2.3, 4.2) */
+
+typedef void (*orc_op)(void* ctx, double h);
+
+/* The leapfrog with n substeps over an interval h:
+   D(h/2n) [K(h/n) D(h/n)]^(n-1) K(h/n) D(h/2n). */
+static void orc_dkd(int n, double h, orc_op drift, orc_op kick, void* ctx) {
+  double d = h / n;
+  drift(ctx, 0.5 * d);
+  for (int i = 0; i < n - 1; ++i) {
+    kick(ctx, d);
+    drift(ctx, d);
+  }
+  kick(ctx, d);
+  drift(ctx, 0.5 * d);
+}
+
+void orc_neville(int kf, const int* nseq, int nvar, const double* S, double* Tkk, double* Tprev) {
+  double* prev = (double*)malloc(sizeof(double) * (size_t)kf);
+  double* cur = (double*)malloc(sizeof(double) * (size_t)kf);
+  for (int q = 0; q < nvar; ++q) {
+    for (int k = 0; k < kf; ++k) {
+      cur[0] = S[(size_t)k * nvar + q];
+      for (int j = 1; j <= k; ++j) {
+        double ratio = (double)nseq[k] / (double)nseq[k - j];
+        cur[j] = cur[j - 1] + (cur[j - 1] - prev[j - 1]) / (ratio * ratio - 1.0);
+      }
+      if (k == kf - 2) Tprev[q] = cur[k];
+      double* t = prev; prev = cur; cur = t;
+    }
+    Tkk[q] = prev[kf - 1];
+  }
+  free(prev);
+  free(cur);
+}
+
+int orc_div_assign(int kf, int ndiv, int* group) {
+  int* load = (int*)calloc((size_t)ndiv, sizeof(int));
+  for (int k = kf; k >= 1; --k) { /* n_k = 2k, largest first */
+    int g = 0;
+    for (int i = 1; i < ndiv; ++i)
+      if (load[i] < load[g]) g = i;
+    load[g] += 2 * k;
+    group[k - 1] = g;
+  }
+  int mx = 0;
+  for (int i = 0; i < ndiv; ++i) if (load[i] > mx) mx = load[i];
+  free(load);
+  return mx;
+}
+
+/* harmonic oscillator with the plain (0,0,1) leapfrog: drift x += h p, kick p -= h w^2 x */
+typedef struct { double x, p, w; } harm_ctx;
+static void harm_drift(void* c, double h) { harm_ctx* s = (harm_ctx*)c; s->x += h * s->p; }
+static void harm_kick(void* c, double h) { harm_ctx* s = (harm_ctx*)c; s->p -= h * (s->w * s->w) * s->x; }
+
+void orc_gbs_harmonic(double w, double x0, double p0, double H, int kf, double* out, double* out_prev) {
+  int* nseq = (int*)malloc(sizeof(int) * (size_t)kf);
+  double* S = (double*)malloc(sizeof(double) * 2 * (size_t)kf);
+  for (int k = 0; k < kf; ++k) {
+    nseq[k] = 2 * (k + 1);
+    harm_ctx c = {x0, p0, w};
+    orc_dkd(nseq[k], H, harm_drift, harm_kick, &c);
+    S[2 * k] = c.x;
+    S[2 * k + 1] = c.p;
+  }
+  orc_neville(kf, nseq, 2, S, out, out_prev);
+  free(nseq);
+  free(S);
+}
+
+/* ---------------------------------------------------------------- N-body system */
+
+struct orc_system {
+  int n;
+  orc_params p;
+  double *m, *r, *v;  /* Cartesian state, COM frame */
+  double t, B, H;     /* physical time, binding energy B = -H_ham, next fictitious step */
+  long long force_evals;
+  /* per-step work */
+  int *parent, *level, *order;
+  int root;
+  double *X0, *V0, *a0, *A0;
+  double T0, U0;
+  /* per-division work */
+  double *S;          /* kf x (6n+1) division results */
+  double *Tkk, *Tprev;
+};
+
+/* one leapfrog division's mutable state (the LogH equations of motion, Sec. 2.1-2.2) */
+typedef struct {
+  orc_system* s;
+  double *X, *V, *r, *v, *a;
+  double t, T, U;
+} orc_div;
+
+/* D(h): dX/ds = V/(T+B), dt/ds = 1/(T+B); then the Cartesian positions are rebuilt. */
+static void nb_drift(void* c, double h) {
+  orc_div* d = (orc_div*)c;
+  orc_system* s = d->s;
+  double f = h / (d->T + s->B);
+  for (int v = 0; v < s->n; ++v)
+    for (int k = 0; k < 3; ++k) d->X[3 * v + k] += f * d->V[3 * v + k];
+  d->t += f;
+  orc_from_mst(s->n, s->m, s->parent, d->X, d->r);
+}
+
+/* K(h): dV/ds = A/U with A_v = a_v - a_parent(v); then v is rebuilt and T updated. */
+static void nb_kick(void* c, double h) {
+  orc_div* d = (orc_div*)c;
+  orc_system* s = d->s;
+  orc_forces(s->n, s->m, s->p.G, s->parent, s->level, s->p.n_d, d->r, d->X, d->a, &d->U);
+  s->force_evals++;
+  double f = h / d->U;
+  for (int v = 0; v < s->n; ++v) {
+    int pv = s->parent[v];
+    if (pv < 0) continue;
+    for (int k = 0; k < 3; ++k) d->V[3 * v + k] += f * (d->a[3 * v + k] - d->a[3 * pv + k]);
+  }
+  orc_from_mst(s->n, s->m, s->parent, d->V, d->v);
+  d->T = orc_kinetic(s->n, s->m, d->v);
+}
+
+static int all_finite(int n, const double* x) {
+  for (int i = 0; i < n; ++i) if (!isfinite(x[i])) return 0;
+  return 1;
+}
+
+orc_system* orc_create(int n, const double* m, const double* r, const double* v, const orc_params* p) {
+  if (n < 2 || !p || p->k_fix < 2 || p->n_d < 0) return NULL;
+  for (int i = 0; i < n; ++i) if (!(m[i] > 0.0) || !isfinite(m[i])) return NULL;
+  if (!all_finite(3 * n, r) || !all_finite(3 * n, v)) return NULL;
+  orc_system* s = (orc_system*)calloc(1, sizeof(orc_system));
+  s->n = n;
+  s->p = *p;
+  size_t n3 = sizeof(double) * 3 * (size_t)n;
+  s->m = (double*)malloc(sizeof(double) * (size_t)n);
+  s->r = (double*)malloc(n3);
+  s->v = (double*)malloc(n3);
+  memcpy(s->m, m, sizeof(double) * (size_t)n);
+  memcpy(s->r, r, n3);
+  memcpy(s->v, v, n3);
+  orc_com_shift(n, s->m, s->r);
+  orc_com_shift(n, s->m, s->v);
+  double T = orc_kinetic(n, s->m, s->v), U = orc_potential(n, s->m, s->r, p->G);
+  s->B = U - T; /* B = -H with H = T - U (Eq. 1) */
+  s->t = 0.0;
+  s->H = 0.0;   /* unset: the first step uses ds = q U dt */
+  s->parent = (int*)malloc(sizeof(int) * (size_t)n);
+  s->level = (int*)malloc(sizeof(int) * (size_t)n);
+  s->order = (int*)malloc(sizeof(int) * (size_t)n);
+  s->X0 = (double*)malloc(n3);
+  s->V0 = (double*)malloc(n3);
+  s->a0 = (double*)malloc(n3);
+  s->A0 = (double*)malloc(n3);
+  size_t nv = 6 * (size_t)n + 1;
+  s->S = (double*)malloc(sizeof(double) * nv * (size_t)p->k_fix);
+  s->Tkk = (double*)malloc(sizeof(double) * nv);
+  s->Tprev = (double*)malloc(sizeof(double) * nv);
+  return s;
+}
+
+void orc_free(orc_system* s) {
+  if (!s) return;
+  free(s->m); free(s->r); free(s->v);
+  free(s->parent); free(s->level); free(s->order);
+  free(s->X0); free(s->V0); free(s->a0); free(s->A0);
+  free(s->S); free(s->Tkk); free(s->Tprev);
+  free(s);
+}
+
+void orc_get_state(const orc_system* s, double* t, double* r, double* v, double* H, double* B) {
+  size_t n3 = sizeof(double) * 3 * (size_t)s->n;
+  if (t) *t = s->t;
+  if (r) memcpy(r, s->r, n3);
+  if (v) memcpy(v, s->v, n3);
+  if (H) *H = s->H;
+  if (B) *B = s->B;
+}
+
+void orc_set_H(orc_system* s, double H) { s->H = H; }
+
+/* Start of a GBS step: MST of the current positions, edge vectors, and the derivative
+   information at s0 that the convergence criterion needs (one force evaluation). */
+static void orc_prepare(orc_system* s) {
+  int n = s->n;
+  s->root = orc_prim(n, s->r, s->parent, s->level, s->order);
+  orc_to_mst(n, s->parent, s->r, s->X0);
+  orc_to_mst(n, s->parent, s->v, s->V0);
+  s->T0 = orc_kinetic(n, s->m, s->v);
+  orc_forces(n, s->m, s->p.G, s->parent, s->level, s->p.n_d, s->r, s->X0, s->a0, &s->U0);
+  s->force_evals++;
+  orc_to_mst(n, s->parent, s->a0, s->A0);
+}
+
+static double vnorm(double x, double y, double z) { return sqrt((x * x + y * y) + z * z); }
+
+/* k_fix leapfrog divisions from the current state, Neville-Aitken extrapolation, and the
+   error of Eq. gbs-criterion. Leaves T_{kf,kf} in s->Tkk. Returns eps (NaN if any ratio
+   is not a number). */
+static double orc_divisions(orc_system* s, double H) {
+  int n = s->n, kf = s->p.k_fix;
+  size_t nv = 6 * (size_t)n + 1, n3 = sizeof(double) * 3 * (size_t)n;
+  int* nseq = (int*)malloc(sizeof(int) * (size_t)kf);
+  orc_div d;
+  d.s = s;
+  d.X = (double*)malloc(n3); d.V = (double*)malloc(n3);
+  d.r = (double*)malloc(n3); d.v = (double*)malloc(n3); d.a = (double*)malloc(n3);
+  for (int k = 0; k < kf; ++k) {
+    nseq[k] = 2 * (k + 1);
+    memcpy(d.X, s->X0, n3); memcpy(d.V, s->V0, n3);
+    memcpy(d.r, s->r, n3); memcpy(d.v, s->v, n3);
+    d.t = s->t; d.T = s->T0; d.U = s->U0;
+    orc_dkd(nseq[k], H, nb_drift, nb_kick, &d);
+    double* Sk = s->S + (size_t)k * nv;
+    memcpy(Sk, d.X, n3);
+    memcpy(Sk + 3 * (size_t)n, d.V, n3);
+    Sk[6 * (size_t)n] = d.t;
+  }
+  orc_neville(kf, nseq, (int)nv, s->S, s->Tkk, s->Tprev);
+  /* Eq. gbs-criterion with h/n = H/n_kfix and S' taken at s0 */
+  double delta = H / nseq[kf - 1];
+  double rate = 1.0 / (s->T0 + s->B);
+  double eps = 0.0;
+  int nan_seen = 0;
+  for (int v = 0; v < n; ++v) {
+    if (s->parent[v] < 0) continue;
+    const double* dX = s->Tkk + 3 * v; const double* pX = s->Tprev + 3 * v;
+    const double* dV = s->Tkk + 3 * (size_t)n + 3 * v; const double* pV = s->Tprev + 3 * (size_t)n + 3 * v;
+    const double* X0 = s->X0 + 3 * v; const double* V0 = s->V0 + 3 * v; const double* A0 = s->A0 + 3 * v;
+    double num = vnorm(dX[0] - pX[0], dX[1] - pX[1], dX[2] - pX[2]);
+    double den = vnorm(X0[0] + delta * (V0[0] * rate), X0[1] + delta * (V0[1] * rate),
+                       X0[2] + delta * (V0[2] * rate));
+    double q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+    num = vnorm(dV[0] - pV[0], dV[1] - pV[1], dV[2] - pV[2]);
+    den = vnorm(V0[0] + delta * (A0[0] / s->U0), V0[1] + delta * (A0[1] / s->U0),
+                V0[2] + delta * (A0[2] / s->U0));
+    q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+  }
+  {
+    double num = fabs(s->Tkk[6 * (size_t)n] - s->Tprev[6 * (size_t)n]);
+    double den = fabs(s->t + delta * rate);
+    double q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+  }
+  free(nseq);
+  free(d.X); free(d.V); free(d.r); free(d.v); free(d.a);
+  return nan_seen ? NAN : eps;
+}
+
+int orc_attempt(orc_system* s, double H, double* eps, double* r_out, double* v_out, double* t_out,
+                double* U0_out) {
+  int n = s->n;
+  orc_prepare(s);
+  double e = orc_divisions(s, H);
+  if (eps) *eps = e;
+  if (U0_out) *U0_out = s->U0;
+  if (r_out) orc_from_mst(n, s->m, s->parent, s->Tkk, r_out);
+  if (v_out) orc_from_mst(n, s->m, s->parent, s->Tkk + 3 * (size_t)n, v_out);
+  if (t_out) *t_out = s->Tkk[6 * (size_t)n];
+  return ORC_OK;
+}
+
+int orc_leapfrog(orc_system* s, int nsub, double H, double* r_out, double* v_out, double* t_out) {
+  int n = s->n;
+  size_t n3 = sizeof(double) * 3 * (size_t)n;
+  orc_prepare(s);
+  orc_div d;
+  d.s = s;
+  d.X = (double*)malloc(n3); d.V = (double*)malloc(n3);
+  d.r = (double*)malloc(n3); d.v = (double*)malloc(n3); d.a = (double*)malloc(n3);
+  memcpy(d.X, s->X0, n3); memcpy(d.V, s->V0, n3);
+  memcpy(d.r, s->r, n3); memcpy(d.v, s->v, n3);
+  d.t = s->t; d.T = s->T0; d.U = s->U0;
+  orc_dkd(nsub, H, nb_drift, nb_kick, &d);
+  if (r_out) orc_from_mst(n, s->m, s->parent, d.X, r_out);
+  if (v_out) orc_from_mst(n, s->m, s->parent, d.V, v_out);
+  if (t_out) *t_out = d.t;
+  free(d.X); free(d.V); free(d.r); free(d.v); free(d.a);
+  return ORC_OK;
+}
+
+void orc_set_state(orc_system* s, double t, const double* r, const double* v) {
+  size_t n3 = sizeof(double) * 3 * (size_t)s->n;
+  s->t = t;
+  memcpy(s->r, r, n3);
+  memcpy(s->v, v, n3);
+}
+
+int orc_integrate(orc_system* s, double t_end, int max_steps, orc_stats* st) {
+  const orc_params* p = &s->p;
+  int kf = p->k_fix;
+  orc_stats local;
+  if (!st) st = &local;
+  memset(st, 0, sizeof(*st));
+  long long fe0 = s->force_evals;
+  int rc = ORC_OK;
+  double tol = p->t_tol * fabs(t_end);
+  while (st->accepted < max_steps) {
+    if (fabs(t_end - s->t) <= tol) break;
+    orc_prepare(s);
+    /* Sec. 2.4: the first step is ds = q U dt; afterwards the GBS controller's step,
+       clamped so that the estimated end time t + ds/U does not pass t_end; past t_end
+       (an overshoot) further steps of ds = U (t_end - t) head back to it. */
+    double dt = t_end - s->t;
+    double Hs = (s->H == 0.0) ? p->q_first * s->U0 * dt : fabs(s->H) * (dt < 0 ? -1.0 : 1.0);
+    int clamped = 0;
+    if (fabs(Hs / s->U0) >= fabs(dt)) { Hs = s->U0 * dt; clamped = 1; }
+    if (clamped) {
+      if (st->time_iters >= p->max_time_iter) break;
+      st->time_iters++;
+    }
+    double eps = 0.0;
+    int halvings = 0;
+    for (;;) {
+      eps = orc_divisions(s, Hs);
+      if (eps <= p->eta) break;
+      st->rejected++;
+      if (++halvings > p->max_halvings) { rc = ORC_ERR_NO_CONVERGENCE; goto done; }
+      Hs *= 0.5;
+    }
+    /* accept: deconstruct the extrapolated MST coordinates into the Cartesian state */
+    orc_from_mst(s->n, s->m, s->parent, s->Tkk, s->r);
+    orc_from_mst(s->n, s->m, s->parent, s->Tkk + 3 * (size_t)s->n, s->v);
+    s->t = s->Tkk[6 * (size_t)s->n];
+    /* Eq. hnext with k = k_fix */
+    double fac = (eps > 0.0) ? p->a_gbs * pow(p->eta / eps, 1.0 / (2 * kf - 1)) : p->fac_max;
+    if (fac < p->fac_min) fac = p->fac_min;
+    if (fac > p->fac_max) fac = p->fac_max;
+    s->H = fac * Hs;
+    st->accepted++;
+    st->eps_last = eps;
+  }
+done:
+  st->force_evals = s->force_evals - fe0;
+  st->H = s->H;
+  st->t = s->t;
+  return rc;
+}
+
+void orc_energy(const orc_system* s, double* E, double* T, double* U, double P[3], double L[3]) {
+  int n = s->n;
+  double t = orc_kinetic(n, s->m, s->v), u = orc_potential(n, s->m, s->r, s->p.G);
+  if (T) *T = t;
+  if (U) *U = u;
+  if (E) *E = t - u;
+  double p[3] = {0, 0, 0}, l[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    const double* r = s->r + 3 * i; const double* v = s->v + 3 * i;
+    for (int k = 0; k < 3; ++k) p[k] += s->m[i] * v[k];
+    l[0] += s->m[i] * (r[1] * v[2] - r[2] * v[1]);
+    l[1] += s->m[i] * (r[2] * v[0] - r[0] * v[2]);
+    l[2] += s->m[i] * (r[0] * v[1] - r[1] * v[0]);
+  }
+  if (P) for (int k = 0; k < 3; ++k) P[k] = p[k];
+  if (L) for (int k = 0; k < 3; ++k) L[k] = l[k];
+}
