@@ -1,0 +1,161 @@
+/*
+ * mstar.h - C ABI of the GB300 (sm_103a) FP64 implementation of the MSTAR hot path:
+ * one GBS extrapolation step of the algorithmically regularised integrator with
+ * minimum-spanning-tree (MST) coordinates (Rantala, Pihajoki, Mannerkoski, Johansson &
+ * Naab, "MSTAR - a fast parallelised algorithmically regularised integrator with minimum
+ * spanning tree coordinates", MNRAS 2020).
+ *
+ * Problem (Sec. 2.1, Eq. 1-2): N point masses m_i with positions r_i and velocities v_i,
+ * Newtonian gravity with constant G, H = T - U. The integrator uses the logarithmic
+ * Hamiltonian time transformation (triplet (1,0,0), Eq. ttl): dt/ds = 1/(T+B),
+ * dr/ds = v/(T+B), dv/ds = a/U with B = -H. One GBS step over a fictitious interval H
+ * builds the MST with Prim's algorithm (Sec. 3.2), switches to MST edge coordinates
+ * (Sec. 3.4), runs k_fix leapfrog divisions with n_k = 2k substeps (Eq. seq-deuflhard,
+ * Sec. 2.3) concurrently (Sec. 4.2), extrapolates them with the Aitken-Neville
+ * polynomial scheme (Sec. 4.2) and tests convergence (Eq. gbs-criterion). Steps are
+ * halved on failure, grown by Eq. hnext on success, and clamped to reach an exact end
+ * time (Sec. 2.4).
+ *
+ * Conventions for every entry point:
+ *  - All arithmetic is IEEE binary64 (FP64). G defaults to 1.
+ *  - Arrays of vectors are n x 3 row-major doubles (x0 y0 z0 x1 ...).
+ *  - Array arguments may be host or device pointers; the library detects which with
+ *    cudaPointerGetAttributes. The caller owns every array it passes; inputs are copied,
+ *    outputs are written before the call returns (the call synchronises its stream).
+ *  - A context owns its device memory: either the caller-provided workspace (at least
+ *    mstar_workspace_bytes() bytes, 256-byte aligned, owned by the caller and kept alive
+ *    until mstar_free) or, when workspace is NULL, memory the library allocates itself.
+ *  - All GPU work of a context runs on the CUDA stream given at init (NULL = legacy
+ *    default stream). Contexts are not thread-safe; distinct contexts are independent.
+ *  - Return value: MSTAR_OK (0) or a negative MSTAR_ERR_* code. No call throws.
+ *    After MSTAR_ERR_CUDA the context must be freed.
+ */
+#ifndef MSTAR_H
+#define MSTAR_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define MSTAR_API __attribute__((visibility("default")))
+#else
+#define MSTAR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSTAR_OK 0
+#define MSTAR_ERR_INVALID_ARG (-1)    /* bad size, pointer, parameter, mass <= 0 */
+#define MSTAR_ERR_NONFINITE (-2)      /* non-finite input value */
+#define MSTAR_ERR_NO_CONVERGENCE (-3) /* more than max_halvings step rejections */
+#define MSTAR_ERR_TIMEOUT (-4)        /* a bounded device wait gave up */
+#define MSTAR_ERR_CUDA (-5)           /* a CUDA runtime call failed */
+#define MSTAR_ERR_UNSUPPORTED (-6)    /* outside the sizes this build supports */
+#define MSTAR_ERR_NOMEM (-7)          /* workspace too small or allocation failed */
+
+/* Largest system a single context accepts (the one-CTA Prim kernel keeps the tree in
+   shared memory and registers). */
+#define MSTAR_MAX_N 10240
+
+typedef struct mstar_ctx mstar_ctx;
+
+/* Parameters; mstar_default_params() fills the defaults given beside each field. */
+typedef struct {
+  double eta_gbs;    /* GBS tolerance eta_GBS of Eq. gbs-criterion. 1e-12 */
+  double a_gbs;      /* safety factor a_GBS in (0,1] of Eq. hnext. 0.9 */
+  double fac_min;    /* lower clamp of the step-growth factor of Eq. hnext. 0.2 */
+  double fac_max;    /* upper clamp of the step-growth factor. 2.0 */
+  double q_first;    /* first step ds = q U dt (Sec. 2.4), dt = t_end - t. 0.1 */
+  double t_tol;      /* relative end-time tolerance |t - t_end| <= t_tol |t_end|. 1e-10 */
+  double G;          /* gravitational constant. 1.0 */
+  int k_fix;         /* number of substep divisions, n_k = 2k, 2 <= k_fix <= 12. 8 */
+  int n_d;           /* near-pair tree distance N_d of Eq. LCA, 0 <= n_d <= 2. 2 */
+  int max_halvings;  /* rejections of one step before MSTAR_ERR_NO_CONVERGENCE. 30 */
+  int max_time_iter; /* end-time-clamped steps per mstar_step call (Sec. 2.4). 8 */
+} mstar_params;
+
+/* Counters of one mstar_step call, and the state after it. */
+typedef struct {
+  long long accepted;    /* accepted GBS steps */
+  long long rejected;    /* rejected attempts (each halved H) */
+  long long force_evals; /* pair-loop evaluations (73 per attempt at k_fix = 8) */
+  long long time_iters;  /* steps whose H was clamped to land on t_end */
+  double eps_last;       /* error of the last accepted step (Eq. gbs-criterion) */
+  double H;              /* fictitious step proposed for the next step (Eq. hnext) */
+  double t;              /* physical time reached */
+} mstar_stats;
+
+MSTAR_API void mstar_default_params(mstar_params* p);
+
+/* Device bytes a context for n bodies needs under p (for a caller-provided workspace). */
+MSTAR_API size_t mstar_workspace_bytes(int n, const mstar_params* p);
+
+/* Create a context: copies m[n] (> 0), r[n x 3], v[n x 3], shifts them to the centre-of-
+   mass frame, and computes B = U - T (B = -H, Sec. 2.1). The physical time starts at 0
+   and the next fictitious step is unset (the first mstar_step uses ds = q U dt).
+   n must be in [2, MSTAR_MAX_N]. cuda_stream is a cudaStream_t (NULL: default stream).
+   Errors: INVALID_ARG, NONFINITE, UNSUPPORTED, NOMEM, CUDA. On error *out is NULL. */
+MSTAR_API int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const double* v,
+               const mstar_params* p, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* Take accepted GBS steps towards t_end (Sec. 2.3-2.4) until |t - t_end| <= t_tol |t_end|,
+   or max_gbs_steps steps were accepted, or max_time_iter clamped steps were taken.
+   Each step: MST (Prim), edge coordinates, one pair-loop evaluation at the step start
+   (for the error norm's S'), k_fix concurrent leapfrog divisions, Neville-Aitken
+   extrapolation, the convergence test; rejected steps are retried with H/2.
+   out (may be NULL) receives the counters of this call. Errors: NO_CONVERGENCE, CUDA. */
+MSTAR_API int mstar_step(mstar_ctx* ctx, double t_end, int max_gbs_steps, mstar_stats* out);
+
+/* One GBS step attempt with fictitious step H > 0 (or < 0) from the current state,
+   without step control; the state is not changed. Writes the error eps of Eq.
+   gbs-criterion and the extrapolated state (r_out, v_out: n x 3, COM frame; t_out);
+   any output pointer may be NULL. */
+MSTAR_API int mstar_attempt(mstar_ctx* ctx, double H, double* eps, double* r_out, double* v_out,
+                  double* t_out);
+
+/* Energy diagnostics of the current state (Eq. 1): E = T - U with the Cartesian pair
+   sum, total momentum P and angular momentum L about the origin. NULL outputs skipped. */
+MSTAR_API int mstar_energy(mstar_ctx* ctx, double* E, double* T, double* U, double P[3], double L[3]);
+
+/* Read / replace the current state (t, r[n x 3], v[n x 3]); set_state keeps B and H. */
+MSTAR_API int mstar_get_state(mstar_ctx* ctx, double* t, double* r, double* v);
+MSTAR_API int mstar_set_state(mstar_ctx* ctx, double t, const double* r, const double* v);
+
+/* Set the next fictitious step H (0 = unset: the next mstar_step uses ds = q U dt). */
+MSTAR_API int mstar_set_H(mstar_ctx* ctx, double H);
+
+/* Prim's MST of the current positions (Sec. 3.2) and its indexing (Sec. 3.4): root
+   (closest to the centre of mass, lowest index on ties), parent[n] (-1 at the root),
+   level[n], order[n] (insertion order). Ties: argmin takes the lowest index, keys are
+   replaced only by strictly smaller squared distances. Any output may be NULL. */
+MSTAR_API int mstar_get_mst(mstar_ctx* ctx, int* root, int* parent, int* level, int* order);
+
+/* One pair-loop evaluation on the current state (Eq. 2 with the near/far separation rule
+   of Sec. 3.4 on the current MST): accelerations a[n x 3] and force function U. */
+MSTAR_API int mstar_accelerations(mstar_ctx* ctx, double* a, double* U);
+
+MSTAR_API void mstar_free(mstar_ctx* ctx);
+MSTAR_API const char* mstar_strerror(int code);
+
+/* Kernel launches the context has issued since init (for launch accounting). */
+MSTAR_API long long mstar_launch_count(const mstar_ctx* ctx);
+
+/* Device timing of the pair-loop kernel (the dominant kernel), for roofline reporting.
+   While enabled, every launch of the tiled pair kernel is bracketed by CUDA events on the
+   context's stream; mstar_profile_read sums their elapsed times. Enabling resets the
+   counters. */
+typedef struct {
+  long long pair_launches;    /* tiled pair-kernel launches timed */
+  double pair_ms;             /* summed device time of those launches */
+  double pair_interactions;   /* unordered pair interactions they evaluated (N(N-1)/2
+                                 per force evaluation, near pairs included) */
+  long long force_evals;      /* force evaluations those launches covered */
+} mstar_profile;
+MSTAR_API int mstar_profile_enable(mstar_ctx* ctx, int on);
+MSTAR_API int mstar_profile_read(mstar_ctx* ctx, mstar_profile* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSTAR_H */

@@ -1,0 +1,661 @@
+// C ABI of libmstar (include/mstar.h): contexts, workspace layout, and the host-side
+// control of the GBS integrator (Sec. 2.3-2.4). Every vector operation of the path runs
+// in the kernels of prim.cu, pair.cu and step.cu; the host only holds scalars (t, B, H)
+// and makes the accept/reject and step-size decisions from the few values it reads back.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "device.cuh"
+#include "internal.h"
+
+using namespace mstar;
+
+namespace {
+
+#define CK(call)                         \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) return fail(e_); \
+  } while (0)
+
+int fail(cudaError_t e) {
+  (void)e;
+  return MSTAR_ERR_CUDA;
+}
+
+// --------------------------------------------------------------------------- layout
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct Shape {
+  int n, npad, K, S, W, T, NT, nblk;
+};
+
+Shape shape_of(int n, const mstar_params& p) {
+  Shape s{};
+  s.n = n;
+  s.W = choose_tile_warps(n);
+  s.T = 32 * s.W;
+  s.npad = (n + s.T - 1) / s.T * s.T;
+  s.K = p.k_fix;
+  s.S = p.k_fix + 1;
+  s.NT = s.npad / s.T;
+  s.nblk = (s.npad + kBlock - 1) / kBlock;
+  return s;
+}
+
+// Assigns every device array of a context (base == nullptr: only measures). Returns bytes.
+size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
+  Carver c(base);
+  const size_t np = s.npad, n3 = 3 * np, S = s.S;
+  Dev t{};
+  t.m = c.take<double>(np);
+  t.r = c.take<double>(n3);
+  t.v = c.take<double>(n3);
+  t.parent = c.take<int>(np);
+  t.gp = c.take<int>(np);
+  t.level = c.take<int>(np);
+  t.order = c.take<int>(np);
+  t.root = c.take<int>(1);
+  t.child_off = c.take<int>(np + 1);
+  t.child_idx = c.take<int>(np);
+  t.X0 = c.take<double>(n3);
+  t.V0 = c.take<double>(n3);
+  t.A0 = c.take<double>(n3);
+  t.sX = c.take<double>(S * n3);
+  t.sV = c.take<double>(S * n3);
+  t.sr = c.take<double>(S * n3);
+  t.sv = c.take<double>(S * n3);
+  t.sa = c.take<double>(S * n3);
+  t.P = c.take<double>(S * (size_t)s.NT * 4 * np);
+  t.Ublk = c.take<double>(S * s.nblk);
+  t.Tblk = c.take<double>(S * s.nblk);
+  t.comblk = c.take<double>(S * s.nblk * 3);
+  t.sc = c.take<double>(S * kScal);
+  t.Tkk = c.take<double>(6 * np + 1);
+  t.epsblk = c.take<double>(s.nblk);
+  t.res = c.take<double>(8);
+  t.mom = c.take<double>((size_t)s.nblk * 8);
+  double* st = c.take<double>(2 * n3);
+  if (d) *d = t;
+  if (stage) *stage = st;
+  return (c.off + 255) & ~size_t(255);
+}
+
+bool valid_params(const mstar_params* p) {
+  if (!p) return false;
+  if (!(p->eta_gbs > 0.0) || !std::isfinite(p->eta_gbs)) return false;
+  if (!(p->a_gbs > 0.0 && p->a_gbs <= 1.0)) return false;
+  if (!(p->fac_min > 0.0 && p->fac_min <= p->fac_max) || !std::isfinite(p->fac_max)) return false;
+  if (!(p->q_first > 0.0) || !std::isfinite(p->q_first)) return false;
+  if (!(p->t_tol >= 0.0) || !std::isfinite(p->t_tol)) return false;
+  if (!(p->G > 0.0) || !std::isfinite(p->G)) return false;
+  if (p->k_fix < 2 || p->k_fix > kMaxKfix) return false;
+  if (p->n_d < 0 || p->n_d > 2) return false;
+  if (p->max_halvings < 0 || p->max_time_iter < 0) return false;
+  return true;
+}
+
+// --------------------------------------------------------------------------- small kernels
+
+__global__ void k_aos_to_soa(int n, int npad, const double* __restrict__ aos, double* __restrict__ soa) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    for (int c = 0; c < 3; ++c) soa[(size_t)c * npad + i] = aos[3 * (size_t)i + c];
+}
+
+__global__ void k_soa_to_aos(int n, int npad, const double* __restrict__ soa, double* __restrict__ aos) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n)
+    for (int c = 0; c < 3; ++c) aos[3 * (size_t)i + c] = soa[(size_t)c * npad + i];
+}
+
+// flag bit 0: a non-finite value; bit 1: a mass <= 0; bit 2: |coordinate| >= 1e15
+__global__ void k_validate(int n, const double* __restrict__ m, const double* __restrict__ r,
+                           const double* __restrict__ v, int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int f = 0;
+  const double mi = m[i];
+  if (!isfinite(mi)) f |= 1;
+  if (!(mi > 0.0)) f |= 2;
+  for (int c = 0; c < 3; ++c) {
+    const double x = r[3 * (size_t)i + c], u = v[3 * (size_t)i + c];
+    if (!isfinite(x) || !isfinite(u)) f |= 1;
+    if (fabs(x) >= 1e15) f |= 4;
+  }
+  if (f) atomicOr(flag, f);
+}
+
+__global__ void k_fill_int(int* __restrict__ p, int count, int value) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) p[i] = value;
+}
+
+struct Staging {
+  double* dev = nullptr;
+};
+
+int blocks_for(int n) { return (n + kBlock - 1) / kBlock; }
+
+// Copy an n x 3 array (host or device) into the context's AoS staging area, then into
+// three SoA planes.
+int load_vectors(mstar_ctx* c, double* stage, const double* src, double* dst_planes) {
+  CK(cudaMemcpyAsync(stage, src, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDefault, c->stream));
+  k_aos_to_soa<<<blocks_for(c->n), kBlock, 0, c->stream>>>(c->n, c->npad, stage, dst_planes);
+  MSTAR_LAUNCHED(c);
+  CK(cudaGetLastError());
+  return MSTAR_OK;
+}
+
+int store_vectors(mstar_ctx* c, double* stage, const double* src_planes, double* dst) {
+  k_soa_to_aos<<<blocks_for(c->n), kBlock, 0, c->stream>>>(c->n, c->npad, src_planes, stage);
+  MSTAR_LAUNCHED(c);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(dst, stage, sizeof(double) * 3 * (size_t)c->n, cudaMemcpyDefault, c->stream));
+  return MSTAR_OK;
+}
+
+double* stage_of(mstar_ctx* c) {
+  double* st = nullptr;
+  Shape s = shape_of(c->n, c->p);
+  carve(s, c->ws, nullptr, &st);
+  return st;
+}
+
+int sync_read_res(mstar_ctx* c) {
+  CK(cudaMemcpyAsync(c->host_res, c->d.res, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
+
+void prof_flush(mstar_ctx* c) {
+  for (size_t i = 0; i < c->prof_used; ++i) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, c->prof_pool[i].a, c->prof_pool[i].b) == cudaSuccess) {
+      const int nsl = c->prof_pool[i].nsl;
+      c->prof_ms += ms;
+      c->prof_launches += 1;
+      c->prof_evals += nsl;
+      c->prof_pairs += (double)nsl * 0.5 * (double)c->n * (double)(c->n - 1);
+    }
+  }
+  c->prof_used = 0;
+}
+
+// --------------------------------------------------------------------------- the GBS step
+
+// MST of the current positions, edge coordinates, and the derivative information at the
+// step start (one force evaluation); reads U0 and T0 back.
+int prepare_step(mstar_ctx* c, double* U0, double* T0) {
+  if (!c->mst_valid) {
+    CK(launch_prim(c));
+    CK(launch_tree(c));
+    c->mst_valid = true;
+  }
+  CK(launch_prepare(c));
+  CK(launch_forces(c, c->K, c->K + 1, c->p.n_d));
+  CK(launch_start_derivs(c));
+  int rc = sync_read_res(c);
+  if (rc) return rc;
+  prof_flush(c);
+  *U0 = c->host_res[2];
+  *T0 = c->host_res[3];
+  return MSTAR_OK;
+}
+
+// One attempt with fictitious step H: all divisions level by level, then the
+// extrapolation; reads eps and the extrapolated time back.
+int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
+  const int K = c->K;
+  const size_t st = (size_t)3 * c->npad;
+  CK(launch_init_drift(c, H));
+  for (int tau = 1; tau <= 2 * K; ++tau) {
+    const int lo = (tau + 1) / 2 - 1;  // divisions with n_k >= tau kick and drift
+    CK(launch_forces(c, lo, K, c->p.n_d));
+    CK(launch_kick(c, lo, K, H));
+    CK(launch_rebuild(c, c->d.sV + lo * st, c->d.sv + lo * st, st, K - lo, 1, c->d.Tblk + (size_t)lo * c->nblk,
+                      c->d.comblk + (size_t)lo * c->nblk * 3));
+    CK(launch_drift(c, lo, K, H, tau));
+    const int lo2 = tau / 2;  // divisions with n_k > tau need positions for the next kick
+    if (lo2 < K)
+      CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
+                        c->d.comblk + (size_t)lo2 * c->nblk * 3));
+  }
+  CK(launch_extrapolate(c, H));
+  int rc = sync_read_res(c);
+  if (rc) return rc;
+  prof_flush(c);
+  *eps = c->host_res[0];
+  *tnew = c->host_res[1];
+  return MSTAR_OK;
+}
+
+// The extrapolated MST coordinates become the Cartesian state (COM frame).
+int accept_state(mstar_ctx* c) {
+  const size_t n3 = (size_t)3 * c->npad;
+  CK(launch_rebuild(c, c->d.Tkk, c->d.r, 0, 1, 0, nullptr, c->d.comblk));
+  CK(launch_rebuild(c, c->d.Tkk + n3, c->d.v, 0, 1, 0, nullptr, c->d.comblk));
+  c->mst_valid = false;
+  return MSTAR_OK;
+}
+
+int extract_out(mstar_ctx* c, double* r_out, double* v_out, const double* Xsrc, const double* Vsrc) {
+  // rebuild into the step-start slot's r/v buffers (free after the attempt) and copy out
+  const size_t n3 = (size_t)3 * c->npad;
+  double* rr = c->d.sr + (size_t)c->K * n3;
+  double* vv = c->d.sv + (size_t)c->K * n3;
+  CK(launch_rebuild(c, Xsrc, rr, 0, 1, 0, nullptr, c->d.comblk));
+  CK(launch_rebuild(c, Vsrc, vv, 0, 1, 0, nullptr, c->d.comblk));
+  double* stage = stage_of(c);
+  int rc;
+  if (r_out && (rc = store_vectors(c, stage, rr, r_out))) return rc;
+  if (v_out && (rc = store_vectors(c, stage + n3, vv, v_out))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- internals
+
+namespace mstar {
+
+int choose_tile_warps(int n) { return n <= 512 ? 1 : 4; }
+
+size_t workspace_bytes(int n, const mstar_params& p, int* npad_out, int* W_out) {
+  Shape s = shape_of(n, p);
+  if (npad_out) *npad_out = s.npad;
+  if (W_out) *W_out = s.W;
+  return carve(s, nullptr, nullptr, nullptr);
+}
+
+void prof_begin(mstar_ctx* c) {
+  if (c->prof_used == c->prof_pool.size()) {
+    mstar_prof_rec r{};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+      c->prof = false;
+      return;
+    }
+    c->prof_pool.push_back(r);
+  }
+  cudaEventRecord(c->prof_pool[c->prof_used].a, c->stream);
+}
+
+void prof_end(mstar_ctx* c, int nsl) {
+  if (!c->prof || c->prof_used >= c->prof_pool.size()) return;
+  cudaEventRecord(c->prof_pool[c->prof_used].b, c->stream);
+  c->prof_pool[c->prof_used].nsl = nsl;
+  c->prof_used++;
+}
+
+}  // namespace mstar
+
+// --------------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+void mstar_default_params(mstar_params* p) {
+  if (!p) return;
+  p->eta_gbs = 1e-12;
+  p->a_gbs = 0.9;
+  p->fac_min = 0.2;
+  p->fac_max = 2.0;
+  p->q_first = 0.1;
+  p->t_tol = 1e-10;
+  p->G = 1.0;
+  p->k_fix = 8;
+  p->n_d = 2;
+  p->max_halvings = 30;
+  p->max_time_iter = 8;
+}
+
+size_t mstar_workspace_bytes(int n, const mstar_params* p) {
+  mstar_params d;
+  if (!p) {
+    mstar_default_params(&d);
+    p = &d;
+  }
+  if (n < 2 || n > MSTAR_MAX_N || !valid_params(p)) return 0;
+  return workspace_bytes(n, *p);
+}
+
+const char* mstar_strerror(int code) {
+  switch (code) {
+    case MSTAR_OK: return "ok";
+    case MSTAR_ERR_INVALID_ARG: return "invalid argument";
+    case MSTAR_ERR_NONFINITE: return "non-finite input";
+    case MSTAR_ERR_NO_CONVERGENCE: return "GBS step did not converge within max_halvings";
+    case MSTAR_ERR_TIMEOUT: return "device wait timed out";
+    case MSTAR_ERR_CUDA: return "CUDA runtime error";
+    case MSTAR_ERR_UNSUPPORTED: return "unsupported size";
+    case MSTAR_ERR_NOMEM: return "workspace too small or allocation failed";
+    default: return "unknown error";
+  }
+}
+
+void mstar_free(mstar_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& r : c->prof_pool) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->host_res) cudaFreeHost(c->host_res);
+  if (c->host_buf) cudaFreeHost(c->host_buf);
+  delete c;
+}
+
+int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const double* v, const mstar_params* p,
+               void* workspace, size_t workspace_bytes, void* cuda_stream) {
+  if (!out) return MSTAR_ERR_INVALID_ARG;
+  *out = nullptr;
+  mstar_params pd;
+  if (!p) {
+    mstar_default_params(&pd);
+    p = &pd;
+  }
+  if (!m || !r || !v || !valid_params(p)) return MSTAR_ERR_INVALID_ARG;
+  if (n < 2) return MSTAR_ERR_INVALID_ARG;
+  if (n > MSTAR_MAX_N) return MSTAR_ERR_UNSUPPORTED;
+  mstar_ctx* c = new (std::nothrow) mstar_ctx();
+  if (!c) return MSTAR_ERR_NOMEM;
+  c->p = *p;
+  c->n = n;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  Shape s = shape_of(n, *p);
+  c->npad = s.npad;
+  c->K = s.K;
+  c->nslots = s.S;
+  c->W = s.W;
+  c->T = s.T;
+  c->NT = s.NT;
+  c->ntp = s.NT * (s.NT + 1) / 2;
+  c->nblk = s.nblk;
+  const size_t need = carve(s, nullptr, nullptr, nullptr);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return MSTAR_ERR_CUDA;
+  }
+  if (workspace) {
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+      delete c;
+      return MSTAR_ERR_NOMEM;
+    }
+    c->ws = workspace;
+  } else {
+    if (cudaMalloc(&c->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return MSTAR_ERR_NOMEM;
+    }
+    c->own_ws = true;
+  }
+  c->ws_bytes = need;
+  double* stage = nullptr;
+  carve(s, c->ws, &c->d, &stage);
+  if (cudaMallocHost(&c->host_res, 8 * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&c->host_buf, (size_t)c->nblk * 8 * sizeof(double) + 64) != cudaSuccess) {
+    cudaGetLastError();
+    mstar_free(c);
+    return MSTAR_ERR_NOMEM;
+  }
+  auto bail = [&](int code) {
+    mstar_free(c);
+    return code;
+  };
+  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.parent, c->npad, -1);
+  k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.gp, c->npad, -1);
+  c->launches += 2;
+  // inputs -> device (masses straight, vectors via the AoS staging area)
+  const size_t n3 = (size_t)3 * c->npad;
+  if (cudaMemcpyAsync(c->d.m, m, sizeof(double) * n, cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(stage, r, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(stage + n3, v, sizeof(double) * 3 * n, cudaMemcpyDefault, c->stream) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
+  int* flag = reinterpret_cast<int*>(c->d.res + 4);
+  k_validate<<<blocks_for(n), kBlock, 0, c->stream>>>(n, c->d.m, stage, stage + n3, flag);
+  k_aos_to_soa<<<blocks_for(n), kBlock, 0, c->stream>>>(n, c->npad, stage, c->d.r);
+  k_aos_to_soa<<<blocks_for(n), kBlock, 0, c->stream>>>(n, c->npad, stage + n3, c->d.v);
+  c->launches += 3;
+  if (cudaGetLastError() != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  // masses to the host for M (sequential sum) and the validation flag
+  std::vector<double> mh(n);
+  if (cudaMemcpyAsync(mh.data(), c->d.m, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->host_res, c->d.res, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
+  int f = 0;
+  std::memcpy(&f, reinterpret_cast<const char*>(c->host_res) + 4 * sizeof(double), sizeof(int));
+  if (f & 1) return bail(MSTAR_ERR_NONFINITE);
+  if (f & 2) return bail(MSTAR_ERR_INVALID_ARG);
+  if (f & 4) return bail(MSTAR_ERR_UNSUPPORTED);
+  double M = 0.0;
+  for (int i = 0; i < n; ++i) M += mh[i];
+  c->Mtot = M;
+  // centre-of-mass frame, then B = U - T with the Cartesian force function (Eq. 1)
+  if (launch_com_shift(c, c->d.r, nullptr) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  if (launch_com_shift(c, c->d.v, c->d.Tblk) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  if (cudaMemcpyAsync(c->d.sr + (size_t)c->K * n3, c->d.r, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                      c->stream) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
+  if (launch_forces(c, c->K, c->K + 1, 0) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  if (cudaMemcpyAsync(c->host_buf, c->d.Ublk + (size_t)c->K * c->nblk, sizeof(double) * c->nblk,
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->host_buf + c->nblk, c->d.Tblk, sizeof(double) * c->nblk, cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
+  double U = 0.0, T2 = 0.0;
+  for (int b = 0; b < c->nblk; ++b) {
+    U += c->host_buf[b];
+    T2 += c->host_buf[c->nblk + b];
+  }
+  c->B = U - 0.5 * T2;
+  c->t = 0.0;
+  c->H = 0.0;
+  c->force_evals = 0;
+  c->mst_valid = false;
+  *out = c;
+  return MSTAR_OK;
+}
+
+int mstar_set_H(mstar_ctx* c, double H) {
+  if (!c || !std::isfinite(H)) return MSTAR_ERR_INVALID_ARG;
+  c->H = H;
+  return MSTAR_OK;
+}
+
+int mstar_get_state(mstar_ctx* c, double* t, double* r, double* v) {
+  if (!c) return MSTAR_ERR_INVALID_ARG;
+  if (t) *t = c->t;
+  double* stage = stage_of(c);
+  int rc;
+  if (r && (rc = store_vectors(c, stage, c->d.r, r))) return rc;
+  if (v && (rc = store_vectors(c, stage + 3 * (size_t)c->npad, c->d.v, v))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
+
+int mstar_set_state(mstar_ctx* c, double t, const double* r, const double* v) {
+  if (!c || !r || !v || !std::isfinite(t)) return MSTAR_ERR_INVALID_ARG;
+  double* stage = stage_of(c);
+  int rc;
+  if ((rc = load_vectors(c, stage, r, c->d.r))) return rc;
+  if ((rc = load_vectors(c, stage + 3 * (size_t)c->npad, v, c->d.v))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  c->t = t;
+  c->mst_valid = false;
+  return MSTAR_OK;
+}
+
+int mstar_get_mst(mstar_ctx* c, int* root, int* parent, int* level, int* order) {
+  if (!c) return MSTAR_ERR_INVALID_ARG;
+  if (!c->mst_valid) {
+    CK(launch_prim(c));
+    CK(launch_tree(c));
+    c->mst_valid = true;
+  }
+  const size_t b = sizeof(int) * c->n;
+  if (root) CK(cudaMemcpyAsync(root, c->d.root, sizeof(int), cudaMemcpyDefault, c->stream));
+  if (parent) CK(cudaMemcpyAsync(parent, c->d.parent, b, cudaMemcpyDefault, c->stream));
+  if (level) CK(cudaMemcpyAsync(level, c->d.level, b, cudaMemcpyDefault, c->stream));
+  if (order) CK(cudaMemcpyAsync(order, c->d.order, b, cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
+
+int mstar_accelerations(mstar_ctx* c, double* a, double* U) {
+  if (!c) return MSTAR_ERR_INVALID_ARG;
+  double U0, T0;
+  int rc = prepare_step(c, &U0, &T0);
+  if (rc) return rc;
+  if (U) *U = U0;
+  if (a && (rc = store_vectors(c, stage_of(c), c->d.sa + (size_t)c->K * 3 * c->npad, a))) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
+
+int mstar_attempt(mstar_ctx* c, double H, double* eps, double* r_out, double* v_out, double* t_out) {
+  if (!c || !std::isfinite(H) || H == 0.0) return MSTAR_ERR_INVALID_ARG;
+  double U0, T0, e, tn;
+  int rc = prepare_step(c, &U0, &T0);
+  if (rc) return rc;
+  if ((rc = run_attempt(c, H, &e, &tn))) return rc;
+  if (eps) *eps = e;
+  if (t_out) *t_out = tn;
+  if (r_out || v_out) {
+    const size_t n3 = (size_t)3 * c->npad;
+    if ((rc = extract_out(c, r_out, v_out, c->d.Tkk, c->d.Tkk + n3))) return rc;
+  }
+  return MSTAR_OK;
+}
+
+int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) {
+  if (!c || !std::isfinite(t_end) || max_gbs_steps < 0) return MSTAR_ERR_INVALID_ARG;
+  const mstar_params& p = c->p;
+  mstar_stats st{};
+  const long long fe0 = c->force_evals;
+  int rc = MSTAR_OK;
+  const double tol = p.t_tol * std::fabs(t_end);
+  while (st.accepted < max_gbs_steps) {
+    if (std::fabs(t_end - c->t) <= tol) break;
+    double U0, T0;
+    if ((rc = prepare_step(c, &U0, &T0))) break;
+    // Sec. 2.4: first step ds = q U dt, then the controller's step clamped so that the
+    // estimated end time t + ds/U does not pass t_end; past t_end, steps head back.
+    const double dt = t_end - c->t;
+    double Hs = (c->H == 0.0) ? p.q_first * U0 * dt : std::fabs(c->H) * (dt < 0 ? -1.0 : 1.0);
+    bool clamped = false;
+    if (std::fabs(Hs / U0) >= std::fabs(dt)) {
+      Hs = U0 * dt;
+      clamped = true;
+    }
+    if (clamped) {
+      if (st.time_iters >= p.max_time_iter) break;
+      st.time_iters++;
+    }
+    double eps = 0.0, tn = c->t;
+    int halvings = 0;
+    for (;;) {
+      if ((rc = run_attempt(c, Hs, &eps, &tn))) goto done;
+      if (eps <= p.eta_gbs) break;
+      st.rejected++;
+      if (++halvings > p.max_halvings) {
+        rc = MSTAR_ERR_NO_CONVERGENCE;
+        goto done;
+      }
+      Hs *= 0.5;
+    }
+    if ((rc = accept_state(c))) break;
+    c->t = tn;
+    {
+      // Eq. hnext with k = k_fix
+      double fac = (eps > 0.0) ? p.a_gbs * std::pow(p.eta_gbs / eps, 1.0 / (2 * c->K - 1)) : p.fac_max;
+      if (fac < p.fac_min) fac = p.fac_min;
+      if (fac > p.fac_max) fac = p.fac_max;
+      c->H = fac * Hs;
+    }
+    st.accepted++;
+    st.eps_last = eps;
+  }
+done:
+  if (rc == MSTAR_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MSTAR_ERR_CUDA;
+  st.force_evals = c->force_evals - fe0;
+  st.H = c->H;
+  st.t = c->t;
+  if (out) *out = st;
+  return rc;
+}
+
+int mstar_energy(mstar_ctx* c, double* E, double* T, double* U, double P[3], double L[3]) {
+  if (!c) return MSTAR_ERR_INVALID_ARG;
+  const size_t n3 = (size_t)3 * c->npad;
+  CK(cudaMemcpyAsync(c->d.sr + (size_t)c->K * n3, c->d.r, sizeof(double) * n3, cudaMemcpyDeviceToDevice,
+                     c->stream));
+  CK(launch_forces(c, c->K, c->K + 1, 0));
+  CK(launch_moments(c));
+  CK(cudaMemcpyAsync(c->host_buf, c->d.Ublk + (size_t)c->K * c->nblk, sizeof(double) * c->nblk,
+                     cudaMemcpyDeviceToHost, c->stream));
+  std::vector<double> mom((size_t)c->nblk * 8);
+  CK(cudaMemcpyAsync(mom.data(), c->d.mom, sizeof(double) * mom.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  double u = 0.0, q[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int b = 0; b < c->nblk; ++b) {
+    u += c->host_buf[b];
+    for (int k = 0; k < 7; ++k) q[k] += mom[(size_t)b * 8 + k];
+  }
+  const double t = 0.5 * q[0];
+  if (T) *T = t;
+  if (U) *U = u;
+  if (E) *E = t - u;
+  if (P)
+    for (int k = 0; k < 3; ++k) P[k] = q[1 + k];
+  if (L)
+    for (int k = 0; k < 3; ++k) L[k] = q[4 + k];
+  // the step-start slot buffers were used as scratch; the MST is unaffected
+  return MSTAR_OK;
+}
+
+long long mstar_launch_count(const mstar_ctx* c) { return c ? c->launches : 0; }
+
+int mstar_profile_enable(mstar_ctx* c, int on) {
+  if (!c) return MSTAR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  prof_flush(c);
+  c->prof = on != 0;
+  c->prof_used = 0;
+  c->prof_launches = c->prof_evals = 0;
+  c->prof_ms = c->prof_pairs = 0.0;
+  return MSTAR_OK;
+}
+
+int mstar_profile_read(mstar_ctx* c, mstar_profile* out) {
+  if (!c || !out) return MSTAR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  prof_flush(c);
+  out->pair_launches = c->prof_launches;
+  out->pair_ms = c->prof_ms;
+  out->pair_interactions = c->prof_pairs;
+  out->force_evals = c->prof_evals;
+  return MSTAR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// Host-side declarations shared by the translation units of libmstar (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/mstar.h"
+
+namespace mstar {
+
+constexpr int kBlock = 256;       // threads of the O(N) kernels
+constexpr int kMaxKfix = 12;      // divisions supported (n_k = 2k <= 24)
+constexpr int kScal = 8;          // per-slot device scalars
+
+// Per-slot device scalars (sc[slot * kScal + i]).
+enum { SC_T_PHYS = 0, SC_T_KIN = 1, SC_U = 2 };
+
+// Device layout of one context. Every array of length npad (a multiple of the pair tile)
+// is zero-padded; vectors are three consecutive planes x[npad], y[npad], z[npad].
+struct Dev {
+  double* m;        // masses (0 in the padding)
+  double* r;        // current state positions, COM frame (3 planes)
+  double* v;        // current state velocities, COM frame
+  int* parent;      // MST parent (-1 root, -3 padding)
+  int* gp;          // grandparent (-1 if none, -3 padding)
+  int* level;
+  int* order;
+  int* root;        // [1]
+  int* child_off;   // [npad + 1] CSR of children
+  int* child_idx;   // [npad]
+  double* X0;       // edge vectors of the step start (3 planes)
+  double* V0;
+  double* A0;       // relative accelerations a_v - a_parent(v) at the step start
+  // per slot: slots 0..K-1 are the divisions (n_k = 2(k+1)), slot K is the step start
+  double* sX;       // slots x 3 planes
+  double* sV;
+  double* sr;
+  double* sv;
+  double* sa;
+  double* P;        // pair partials: slots x NT x 4 x npad
+  double* Ublk;     // slots x nblk
+  double* Tblk;     // slots x nblk
+  double* comblk;   // slots x nblk x 3
+  double* sc;       // slots x kScal scalars
+  double* Tkk;      // extrapolated (X 3 planes, V 3 planes, t)
+  double* epsblk;   // nblk
+  double* res;      // small results read by the host: [0] eps, [1] t, [2] U0, [3] T0
+  double* mom;      // nblk x 8 block partials of T, P, L
+};
+
+}  // namespace mstar
+
+struct mstar_prof_rec {
+  cudaEvent_t a, b;
+  int nsl;
+};
+
+struct mstar_ctx {
+  int n = 0, npad = 0, K = 0, nslots = 0;
+  int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
+  int nblk = 0;
+  mstar_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  mstar::Dev d{};
+  double* host_res = nullptr;  // pinned mirror of d.res (8 doubles)
+  double* host_buf = nullptr;  // pinned staging (nblk * 8 doubles)
+  // host-side scalar state (the step control of Sec. 2.3-2.4 runs on the host)
+  double t = 0.0, B = 0.0, H = 0.0, Mtot = 0.0;
+  bool mst_valid = false;  // the MST/edge buffers describe the current state
+  long long launches = 0;
+  long long force_evals = 0;
+  // profiling of the tiled pair kernel: event pairs recorded around each launch, read
+  // back after the next host synchronisation
+  bool prof = false;
+  std::vector<mstar_prof_rec> prof_pool;
+  size_t prof_used = 0;
+  long long prof_launches = 0, prof_evals = 0;
+  double prof_ms = 0.0, prof_pairs = 0.0;
+};
+
+namespace mstar {
+
+// Layout helpers
+size_t workspace_bytes(int n, const mstar_params& p, int* npad_out = nullptr, int* W_out = nullptr);
+int choose_tile_warps(int n);
+
+// prim.cu
+cudaError_t launch_prim(mstar_ctx* c);      // MST of d.r -> parent, level, order, root
+cudaError_t launch_tree(mstar_ctx* c);      // grandparents and children CSR
+
+// pair.cu: slots [slot_lo, slot_hi) -> sa, Ublk. n_d as in params (0 = all Cartesian).
+cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d);
+
+// step.cu
+cudaError_t launch_prepare(mstar_ctx* c);   // X0, V0, slot K copies, T0 partials
+cudaError_t launch_start_derivs(mstar_ctx* c);  // A0 and U0, T0 into d.res
+cudaError_t launch_init_drift(mstar_ctx* c, double H);
+cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi, double H);
+cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, double H, int tau);
+cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stride, int nsl,
+                           int want_T, double* Tblk_base, double* comblk_base);
+cudaError_t launch_extrapolate(mstar_ctx* c, double H);
+cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom
+// w (3 planes of the state) -= centre of mass; optionally T partials into Tblk slot 0
+cudaError_t launch_com_shift(mstar_ctx* c, double* w, double* Tblk);
+
+// api.cu
+void prof_begin(mstar_ctx* c);
+void prof_end(mstar_ctx* c, int nsl);
+
+}  // namespace mstar
+
+#define MSTAR_LAUNCHED(c) ((c)->launches++)

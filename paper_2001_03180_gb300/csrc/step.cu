@@ -1,0 +1,435 @@
+// The O(N) parts of a GBS step: MST coordinates, LogH drift and kick, rebuilding the
+// Cartesian state, and the Neville-Aitken extrapolation with its error norm.
+//
+// All k_fix leapfrog divisions of a step advance together: "slot" k (0-based) holds
+// division k+1 with n = 2(k+1) substeps (Deuflhard sequence, Eq. seq-deuflhard); slot
+// k_fix holds the step-start state used for the error norm's derivatives. Each kernel
+// takes a contiguous slot range in blockIdx.y, so one launch serves every division that
+// is active at a given substep level (Sec. 4.2: the divisions are independent).
+//
+// The drift/kick/rebuild arithmetic uses explicitly rounded FP64 operations (no
+// contraction), the same operation order as the CPU reference.
+#include "device.cuh"
+#include "internal.h"
+
+namespace mstar {
+namespace {
+
+__constant__ double c_fac[kMaxKfix][kMaxKfix];  // 1 / ((n_k / n_{k-j})^2 - 1)
+
+__device__ __forceinline__ double madd(double a, double f, double b) {  // a + f*b, two roundings
+  return __dadd_rn(a, __dmul_rn(f, b));
+}
+
+// Edge vectors of the step start: X_v = r_v - r_parent(v), V_v likewise (0 at the root and
+// in the padding); copies r and X0 into the step-start slot; block sums of m v^2.
+__global__ void __launch_bounds__(kBlock)
+k_prepare(int n, int npad, int K, const double* __restrict__ m, const int* __restrict__ parent,
+          const double* __restrict__ r, const double* __restrict__ v, double* __restrict__ X0,
+          double* __restrict__ V0, double* __restrict__ sr, double* __restrict__ sX, double* __restrict__ Tblk,
+          int nblk) {
+  __shared__ double scratch[32];
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  double t2 = 0.0;
+  if (w < npad) {
+    const int p = w < n ? parent[w] : -1;
+    double* srK = sr + (size_t)K * 3 * npad;
+    double* sXK = sX + (size_t)K * 3 * npad;
+    double vv[3];
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad;
+      const double rw = r[o + w], vw = v[o + w];
+      const double x = p >= 0 ? __dsub_rn(rw, r[o + p]) : 0.0;
+      const double u = p >= 0 ? __dsub_rn(vw, v[o + p]) : 0.0;
+      X0[o + w] = x;
+      V0[o + w] = u;
+      srK[o + w] = rw;
+      sXK[o + w] = x;
+      vv[c] = vw;
+    }
+    if (w < n) t2 = __dmul_rn(m[w], __dadd_rn(__dadd_rn(__dmul_rn(vv[0], vv[0]), __dmul_rn(vv[1], vv[1])),
+                                               __dmul_rn(vv[2], vv[2])));
+  }
+  const double s = block_sum(t2, scratch);
+  if (threadIdx.x == 0) Tblk[(size_t)K * nblk + blockIdx.x] = s;
+}
+
+// A0_v = a0_v - a0_parent(v) from the step-start slot; block 0 also stores U0 and T0.
+__global__ void __launch_bounds__(kBlock)
+k_start_derivs(int n, int npad, int K, const int* __restrict__ parent, const double* __restrict__ sa,
+               double* __restrict__ A0, const double* __restrict__ Ublk, const double* __restrict__ Tblk,
+               int nblk, double* __restrict__ sc, double* __restrict__ res) {
+  __shared__ double sU, sT;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const double* aK = sa + (size_t)K * 3 * npad;
+  if (w < npad) {
+    const int p = w < n ? parent[w] : -1;
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad;
+      A0[o + w] = p >= 0 ? __dsub_rn(aK[o + w], aK[o + p]) : 0.0;
+    }
+  }
+  if (blockIdx.x == 0) {
+    sum_partials(Ublk + (size_t)K * nblk, nblk, 1, &sU);
+    sum_partials(Tblk + (size_t)K * nblk, nblk, 1, &sT);
+    if (threadIdx.x == 0) {
+      const double T0 = 0.5 * sT;
+      res[2] = sU;
+      res[3] = T0;
+      sc[K * kScal + SC_U] = sU;
+      sc[K * kScal + SC_T_KIN] = T0;
+    }
+  }
+}
+
+// First half drift D(h/2n) of every division from the step start (Sec. 2.3):
+// X = X0 + f V0, V = V0, t = t0 + f with f = (delta/2) / (T0 + B), delta = H / n_k.
+__global__ void __launch_bounds__(kBlock)
+k_init_drift(int n, int npad, int K, double H, double B, double t0, const double* __restrict__ X0,
+             const double* __restrict__ V0, double* __restrict__ sX, double* __restrict__ sV,
+             double* __restrict__ sc) {
+  const int slot = blockIdx.y;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  const double T0 = sc[K * kScal + SC_T_KIN];
+  const double delta = H / (double)(2 * (slot + 1));
+  const double f = (0.5 * delta) / (T0 + B);
+  if (w < npad) {
+    double* X = sX + (size_t)slot * 3 * npad;
+    double* V = sV + (size_t)slot * 3 * npad;
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad;
+      X[o + w] = madd(X0[o + w], f, V0[o + w]);
+      V[o + w] = V0[o + w];
+    }
+  }
+  if (w == 0) {
+    sc[slot * kScal + SC_T_PHYS] = t0 + f;
+    sc[slot * kScal + SC_T_KIN] = T0;
+  }
+}
+
+// K(delta): V_v += (delta / U) (a_v - a_parent(v)), delta = H / n_k (Sec. 2.2).
+__global__ void __launch_bounds__(kBlock)
+k_kick(int n, int npad, int slot_lo, double H, const int* __restrict__ parent, const double* __restrict__ sa,
+       double* __restrict__ sV, const double* __restrict__ Ublk, int nblk, double* __restrict__ sc) {
+  __shared__ double sU;
+  const int slot = slot_lo + blockIdx.y;
+  sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &sU);
+  const double U = sU;
+  const double f = (H / (double)(2 * (slot + 1))) / U;
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < n) {
+    const int p = parent[w];
+    if (p >= 0) {
+      const double* a = sa + (size_t)slot * 3 * npad;
+      double* V = sV + (size_t)slot * 3 * npad;
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = (size_t)c * npad;
+        V[o + w] = madd(V[o + w], f, __dsub_rn(a[o + w], a[o + p]));
+      }
+    }
+  }
+  if (w == 0) sc[slot * kScal + SC_U] = U;
+}
+
+// D(h): X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift.
+__global__ void __launch_bounds__(kBlock)
+k_drift(int npad, int slot_lo, double H, double B, int tau, double* __restrict__ sX,
+        const double* __restrict__ sV, const double* __restrict__ Tblk, int nblk, double* __restrict__ sc) {
+  __shared__ double sT;
+  const int slot = slot_lo + blockIdx.y;
+  sum_partials(Tblk + (size_t)slot * nblk, nblk, 1, &sT);
+  const double T = 0.5 * sT;
+  const int nk = 2 * (slot + 1);
+  const double delta = H / (double)nk;
+  const double h = (tau == nk) ? 0.5 * delta : delta;
+  const double f = h / (T + B);
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w < npad) {
+    double* X = sX + (size_t)slot * 3 * npad;
+    const double* V = sV + (size_t)slot * 3 * npad;
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad;
+      X[o + w] = madd(X[o + w], f, V[o + w]);
+    }
+  }
+  if (w == 0) {
+    sc[slot * kScal + SC_T_PHYS] += f;
+    sc[slot * kScal + SC_T_KIN] = T;
+  }
+}
+
+// Cartesian vector of every body from edge vectors: the path sum w_v = W_v + W_parent(v)
+// + ... up to the root (root: 0), plus block sums of m w for the centre of mass.
+__global__ void __launch_bounds__(kBlock)
+k_rebuild(int n, int npad, size_t stride, const int* __restrict__ parent, const double* __restrict__ Wb,
+          double* __restrict__ wb, const double* __restrict__ m, double* __restrict__ comblk, int nblk) {
+  __shared__ double scratch[32];
+  const int slot = blockIdx.y;
+  const double* W = Wb + slot * stride;
+  double* wv = wb + slot * stride;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double s[3] = {0.0, 0.0, 0.0};
+  if (v < n) {
+    for (int u = v; parent[u] >= 0; u = parent[u]) {
+      s[0] = __dadd_rn(s[0], W[u]);
+      s[1] = __dadd_rn(s[1], W[(size_t)npad + u]);
+      s[2] = __dadd_rn(s[2], W[2 * (size_t)npad + u]);
+    }
+    wv[v] = s[0];
+    wv[(size_t)npad + v] = s[1];
+    wv[2 * (size_t)npad + v] = s[2];
+  }
+  const double mv = v < n ? m[v] : 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double b = block_sum(__dmul_rn(mv, s[c]), scratch);
+    if (threadIdx.x == 0) comblk[((size_t)slot * nblk + blockIdx.x) * 3 + c] = b;
+  }
+}
+
+// Shift to the centre-of-mass frame: w -= (sum m w) / M; optionally block sums of m w^2.
+__global__ void __launch_bounds__(kBlock)
+k_shift(int n, int npad, size_t stride, double Mtot, double* __restrict__ wb, const double* __restrict__ m,
+        const double* __restrict__ comblk, double* __restrict__ Tblk, int nblk) {
+  __shared__ double scratch[32];
+  __shared__ double sc3[3];
+  const int slot = blockIdx.y;
+  for (int c = 0; c < 3; ++c) sum_partials(comblk + (size_t)slot * nblk * 3 + c, nblk, 3, &sc3[c]);
+  double* wv = wb + slot * stride;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  double t2 = 0.0;
+  if (v < n) {
+    double q[3];
+    for (int c = 0; c < 3; ++c) {
+      q[c] = __dsub_rn(wv[(size_t)c * npad + v], sc3[c] / Mtot);
+      wv[(size_t)c * npad + v] = q[c];
+    }
+    t2 = __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
+  }
+  if (Tblk) {
+    const double s = block_sum(t2, scratch);
+    if (threadIdx.x == 0) Tblk[(size_t)slot * nblk + blockIdx.x] = s;
+  }
+}
+
+__device__ __forceinline__ void neville(const double* S, int K, double& tkk, double& tprev) {
+  double prev[kMaxKfix], cur[kMaxKfix];
+#pragma unroll
+  for (int k = 0; k < kMaxKfix; ++k) {
+    if (k < K) {
+      cur[0] = S[k];
+#pragma unroll
+      for (int j = 1; j < kMaxKfix; ++j)
+        if (j <= k) cur[j] = fma(__dsub_rn(cur[j - 1], prev[j - 1]), c_fac[k][j], cur[j - 1]);
+      if (k == K - 2) tprev = cur[k];
+#pragma unroll
+      for (int j = 0; j < kMaxKfix; ++j) prev[j] = cur[j];
+    }
+  }
+  tkk = prev[K - 1];
+}
+
+__device__ __forceinline__ double norm3(double x, double y, double z) {
+  return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+}
+
+// Neville-Aitken extrapolation of every edge vector component and t over the K divisions
+// (Sec. 4.2), and the error of Eq. gbs-criterion:
+// eps = max_q |T_KK - T_{K-1,K-1}|_q / |S_q(s0) + delta_K S'_q(s0)| over X_v, V_v, t with
+// S' = V / (T0 + B) for X, A0 / U0 for V, 1 / (T0 + B) for t, delta_K = H / n_K.
+__global__ void __launch_bounds__(kBlock)
+k_extrapolate(int n, int npad, int K, double H, double B, double t0, const int* __restrict__ parent,
+              const double* __restrict__ sX, const double* __restrict__ sV, const double* __restrict__ X0,
+              const double* __restrict__ V0, const double* __restrict__ A0, const double* __restrict__ sc,
+              double* __restrict__ Tkk, double* __restrict__ epsblk) {
+  __shared__ double scratch[32];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const double T0 = sc[K * kScal + SC_T_KIN], U0 = sc[K * kScal + SC_U];
+  const double rate = 1.0 / (T0 + B);
+  const double delta = H / (double)(2 * K);
+  const size_t slot_stride = (size_t)3 * npad;
+  double e = 0.0;
+  if (v < n) {
+    double S[kMaxKfix];
+    double dX[3], dV[3];
+    for (int c = 0; c < 3; ++c) {
+      double tkk, tp = 0.0;
+      for (int k = 0; k < K; ++k) S[k] = sX[k * slot_stride + (size_t)c * npad + v];
+      neville(S, K, tkk, tp);
+      Tkk[(size_t)c * npad + v] = tkk;
+      dX[c] = __dsub_rn(tkk, tp);
+      for (int k = 0; k < K; ++k) S[k] = sV[k * slot_stride + (size_t)c * npad + v];
+      neville(S, K, tkk, tp);
+      Tkk[(size_t)(3 + c) * npad + v] = tkk;
+      dV[c] = __dsub_rn(tkk, tp);
+    }
+    if (parent[v] >= 0) {
+      double q[3], g[3];
+      for (int c = 0; c < 3; ++c) {
+        const size_t o = (size_t)c * npad + v;
+        q[c] = madd(X0[o], delta, __dmul_rn(V0[o], rate));
+        g[c] = madd(V0[o], delta, A0[o] / U0);
+      }
+      const double rx = norm3(dX[0], dX[1], dX[2]) / fmax(norm3(q[0], q[1], q[2]), 1e-300);
+      const double rv = norm3(dV[0], dV[1], dV[2]) / fmax(norm3(g[0], g[1], g[2]), 1e-300);
+      e = nanmax(rx, rv);
+    }
+  }
+  if (v == 0) {
+    double S[kMaxKfix];
+    for (int k = 0; k < K; ++k) S[k] = sc[k * kScal + SC_T_PHYS];
+    double tkk, tp = 0.0;
+    neville(S, K, tkk, tp);
+    Tkk[(size_t)6 * npad] = tkk;
+    const double rt = fabs(__dsub_rn(tkk, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300);
+    e = nanmax(e, rt);
+  }
+  const double b = block_nanmax(e, scratch);
+  if (threadIdx.x == 0) epsblk[blockIdx.x] = b;
+}
+
+__global__ void k_eps_final(int npad, const double* __restrict__ epsblk, int nblk, const double* __restrict__ Tkk,
+                            double* __restrict__ res) {
+  __shared__ double scratch[32];
+  double e = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) e = nanmax(e, epsblk[b]);
+  e = block_nanmax(e, scratch);
+  if (threadIdx.x == 0) {
+    res[0] = e;
+    res[1] = Tkk[(size_t)6 * npad];
+  }
+}
+
+// Block partials of T = sum m v^2 / 2 (stored as sum m v^2), P = sum m v, L = sum m r x v.
+__global__ void __launch_bounds__(kBlock)
+k_moments(int n, int npad, const double* __restrict__ m, const double* __restrict__ r, const double* __restrict__ v,
+          double* __restrict__ mom) {
+  __shared__ double scratch[32];
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  double q[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (w < n) {
+    const double mw = m[w];
+    const double x = r[w], y = r[npad + w], z = r[2 * (size_t)npad + w];
+    const double vx = v[w], vy = v[npad + w], vz = v[2 * (size_t)npad + w];
+    q[0] = mw * ((vx * vx + vy * vy) + vz * vz);
+    q[1] = mw * vx;
+    q[2] = mw * vy;
+    q[3] = mw * vz;
+    q[4] = mw * (y * vz - z * vy);
+    q[5] = mw * (z * vx - x * vz);
+    q[6] = mw * (x * vy - y * vx);
+  }
+  for (int c = 0; c < 7; ++c) {
+    const double s = block_sum(q[c], scratch);
+    if (threadIdx.x == 0) mom[(size_t)blockIdx.x * 8 + c] = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prepare(mstar_ctx* c) {
+  k_prepare<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.m, c->d.parent, c->d.r, c->d.v, c->d.X0,
+                                              c->d.V0, c->d.sr, c->d.sX, c->d.Tblk, c->nblk);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_start_derivs(mstar_ctx* c) {
+  k_start_derivs<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.parent, c->d.sa, c->d.A0, c->d.Ublk,
+                                                   c->d.Tblk, c->nblk, c->d.sc, c->d.res);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_drift(mstar_ctx* c, double H) {
+  double fac[kMaxKfix][kMaxKfix] = {};
+  for (int k = 0; k < c->K; ++k)
+    for (int j = 1; j <= k; ++j) {
+      const double ratio = (double)(2 * (k + 1)) / (double)(2 * (k - j + 1));
+      fac[k][j] = 1.0 / (ratio * ratio - 1.0);
+    }
+  cudaError_t e = cudaMemcpyToSymbolAsync(c_fac, fac, sizeof(fac), 0, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return e;
+  dim3 grid(c->nblk, c->K);
+  k_init_drift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, H, c->B, c->t, c->d.X0, c->d.V0, c->d.sX,
+                                              c->d.sV, c->d.sc);
+  MSTAR_LAUNCHED(c);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t st = (size_t)3 * c->npad;
+  return launch_rebuild(c, c->d.sX, c->d.sr, st, c->K, 0, nullptr, c->d.comblk);
+}
+
+cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi, double H) {
+  dim3 grid(c->nblk, slot_hi - slot_lo);
+  k_kick<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, slot_lo, H, c->d.parent, c->d.sa, c->d.sV, c->d.Ublk,
+                                        c->nblk, c->d.sc);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, double H, int tau) {
+  dim3 grid(c->nblk, slot_hi - slot_lo);
+  k_drift<<<grid, kBlock, 0, c->stream>>>(c->npad, slot_lo, H, c->B, tau, c->d.sX, c->d.sV, c->d.Tblk, c->nblk,
+                                         c->d.sc);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stride, int nsl, int want_T,
+                           double* Tblk_base, double* comblk_base) {
+  if (nsl <= 0) return cudaSuccess;
+  dim3 grid(c->nblk, nsl);
+  k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, W, w, c->d.m, comblk_base, c->nblk);
+  MSTAR_LAUNCHED(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_shift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->Mtot, w, c->d.m, comblk_base,
+                                         want_T ? Tblk_base : nullptr, c->nblk);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extrapolate(mstar_ctx* c, double H) {
+  k_extrapolate<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, H, c->B, c->t, c->d.parent, c->d.sX,
+                                                  c->d.sV, c->d.X0, c->d.V0, c->d.A0, c->d.sc, c->d.Tkk,
+                                                  c->d.epsblk);
+  MSTAR_LAUNCHED(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_eps_final<<<1, kBlock, 0, c->stream>>>(c->npad, c->d.epsblk, c->nblk, c->d.Tkk, c->d.res);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// block sums of m w (slot 0 of comblk)
+__global__ void __launch_bounds__(kBlock)
+k_mw(int n, int npad, const double* __restrict__ m, const double* __restrict__ w, double* __restrict__ comblk) {
+  __shared__ double scratch[32];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const double mv = v < n ? m[v] : 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double x = v < n ? w[(size_t)c * npad + v] : 0.0;
+    const double b = block_sum(__dmul_rn(mv, x), scratch);
+    if (threadIdx.x == 0) comblk[(size_t)blockIdx.x * 3 + c] = b;
+  }
+}
+
+cudaError_t launch_com_shift(mstar_ctx* c, double* w, double* Tblk) {
+  k_mw<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->d.m, w, c->d.comblk);
+  MSTAR_LAUNCHED(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_shift<<<dim3(c->nblk, 1), kBlock, 0, c->stream>>>(c->n, c->npad, 0, c->Mtot, w, c->d.m, c->d.comblk, Tblk,
+                                                     c->nblk);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(mstar_ctx* c) {
+  k_moments<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->d.m, c->d.r, c->d.v, c->d.mom);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+}  // namespace mstar

@@ -1,0 +1,279 @@
+"""Thin Python binding of libmstar (include/mstar.h): argument marshalling only.
+
+Every function keeps the C name. Arrays may be numpy arrays (host) or CUDA torch
+tensors (device); device memory and streams come from PyTorch. There is no CPU
+fallback: if libmstar.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmstar.so")
+
+MSTAR_OK = 0
+MSTAR_ERR_INVALID_ARG = -1
+MSTAR_ERR_NONFINITE = -2
+MSTAR_ERR_NO_CONVERGENCE = -3
+MSTAR_ERR_TIMEOUT = -4
+MSTAR_ERR_CUDA = -5
+MSTAR_ERR_UNSUPPORTED = -6
+MSTAR_ERR_NOMEM = -7
+MSTAR_MAX_N = 10240
+
+# Names the header declares (checked by the tests against the library's exports).
+EXPORTS = [
+    "mstar_default_params", "mstar_workspace_bytes", "mstar_init", "mstar_step", "mstar_attempt",
+    "mstar_energy", "mstar_get_state", "mstar_set_state", "mstar_set_H", "mstar_get_mst",
+    "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
+    "mstar_profile_enable", "mstar_profile_read",
+]
+
+
+class mstar_params(C.Structure):
+    _fields_ = [("eta_gbs", C.c_double), ("a_gbs", C.c_double), ("fac_min", C.c_double),
+                ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
+                ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int), ("max_halvings", C.c_int),
+                ("max_time_iter", C.c_int)]
+
+
+class mstar_stats(C.Structure):
+    _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("force_evals", C.c_longlong),
+                ("time_iters", C.c_longlong), ("eps_last", C.c_double), ("H", C.c_double),
+                ("t", C.c_double)]
+
+
+class mstar_profile(C.Structure):
+    _fields_ = [("pair_launches", C.c_longlong), ("pair_ms", C.c_double),
+                ("pair_interactions", C.c_double), ("force_evals", C.c_longlong)]
+
+
+_lib = None
+
+
+class MstarError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {mstar_strerror(code)} ({code})")
+        self.code = code
+
+
+def load():
+    """Load libmstar.so (no fallback of any kind)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmstar.so not built ({LIB_PATH}); run paper_2001_03180_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.c_void_p, C.c_void_p
+    L.mstar_default_params.argtypes = [C.POINTER(mstar_params)]
+    L.mstar_default_params.restype = None
+    L.mstar_workspace_bytes.argtypes = [C.c_int, C.POINTER(mstar_params)]
+    L.mstar_workspace_bytes.restype = C.c_size_t
+    L.mstar_init.argtypes = [C.POINTER(vp), C.c_int, dp, dp, dp, C.POINTER(mstar_params), vp, C.c_size_t, vp]
+    L.mstar_step.argtypes = [vp, C.c_double, C.c_int, C.POINTER(mstar_stats)]
+    L.mstar_attempt.argtypes = [vp, C.c_double, C.POINTER(C.c_double), dp, dp, C.POINTER(C.c_double)]
+    L.mstar_energy.argtypes = [vp] + [C.POINTER(C.c_double)] * 3 + [dp, dp]
+    L.mstar_get_state.argtypes = [vp, C.POINTER(C.c_double), dp, dp]
+    L.mstar_set_state.argtypes = [vp, C.c_double, dp, dp]
+    L.mstar_set_H.argtypes = [vp, C.c_double]
+    L.mstar_get_mst.argtypes = [vp, ip, ip, ip, ip]
+    L.mstar_accelerations.argtypes = [vp, dp, C.POINTER(C.c_double)]
+    L.mstar_free.argtypes = [vp]
+    L.mstar_free.restype = None
+    L.mstar_strerror.argtypes = [C.c_int]
+    L.mstar_strerror.restype = C.c_char_p
+    L.mstar_launch_count.argtypes = [vp]
+    L.mstar_launch_count.restype = C.c_longlong
+    L.mstar_profile_enable.argtypes = [vp, C.c_int]
+    L.mstar_profile_read.argtypes = [vp, C.POINTER(mstar_profile)]
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or a torch tensor (host or device); None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _check(rc, where):
+    if rc != MSTAR_OK:
+        raise MstarError(rc, where)
+
+
+def mstar_strerror(code: int) -> str:
+    return load().mstar_strerror(int(code)).decode()
+
+
+def mstar_default_params(**overrides) -> mstar_params:
+    p = mstar_params()
+    load().mstar_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def mstar_workspace_bytes(n: int, p: mstar_params | None = None) -> int:
+    return load().mstar_workspace_bytes(int(n), C.byref(p) if p is not None else None)
+
+
+def mstar_init(n, m, r, v, p=None, workspace=None, workspace_bytes=0, cuda_stream=None):
+    ctx = C.c_void_p()
+    rc = load().mstar_init(C.byref(ctx), int(n), _ptr(m), _ptr(r), _ptr(v), C.byref(p) if p is not None else None,
+                           _ptr(workspace), int(workspace_bytes), cuda_stream)
+    _check(rc, "mstar_init")
+    return ctx
+
+
+def mstar_step(ctx, t_end, max_gbs_steps):
+    st = mstar_stats()
+    rc = load().mstar_step(ctx, float(t_end), int(max_gbs_steps), C.byref(st))
+    return rc, st
+
+
+def mstar_attempt(ctx, H, r_out=None, v_out=None):
+    eps = C.c_double()
+    t = C.c_double()
+    rc = load().mstar_attempt(ctx, float(H), C.byref(eps), _ptr(r_out), _ptr(v_out), C.byref(t))
+    _check(rc, "mstar_attempt")
+    return eps.value, t.value
+
+
+def mstar_energy(ctx, P=None, L=None):
+    E, T, U = C.c_double(), C.c_double(), C.c_double()
+    rc = load().mstar_energy(ctx, C.byref(E), C.byref(T), C.byref(U), _ptr(P), _ptr(L))
+    _check(rc, "mstar_energy")
+    return E.value, T.value, U.value
+
+
+def mstar_get_state(ctx, r=None, v=None):
+    t = C.c_double()
+    _check(load().mstar_get_state(ctx, C.byref(t), _ptr(r), _ptr(v)), "mstar_get_state")
+    return t.value
+
+
+def mstar_set_state(ctx, t, r, v):
+    _check(load().mstar_set_state(ctx, float(t), _ptr(r), _ptr(v)), "mstar_set_state")
+
+
+def mstar_set_H(ctx, H):
+    _check(load().mstar_set_H(ctx, float(H)), "mstar_set_H")
+
+
+def mstar_get_mst(ctx, root=None, parent=None, level=None, order=None):
+    _check(load().mstar_get_mst(ctx, _ptr(root), _ptr(parent), _ptr(level), _ptr(order)), "mstar_get_mst")
+
+
+def mstar_accelerations(ctx, a=None):
+    U = C.c_double()
+    _check(load().mstar_accelerations(ctx, _ptr(a), C.byref(U)), "mstar_accelerations")
+    return U.value
+
+
+def mstar_free(ctx):
+    if ctx:
+        load().mstar_free(ctx)
+
+
+def mstar_launch_count(ctx) -> int:
+    return load().mstar_launch_count(ctx)
+
+
+def mstar_profile_enable(ctx, on: bool):
+    _check(load().mstar_profile_enable(ctx, int(bool(on))), "mstar_profile_enable")
+
+
+def mstar_profile_read(ctx) -> mstar_profile:
+    pr = mstar_profile()
+    _check(load().mstar_profile_read(ctx, C.byref(pr)), "mstar_profile_read")
+    return pr
+
+
+class Integrator:
+    """One N-body system on the GPU. Device memory (the context workspace) is a torch
+    tensor; all GPU work runs on the torch stream current at construction."""
+
+    def __init__(self, m, r, v, device=None, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmstar needs a CUDA GPU")
+        load()
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.p = mstar_default_params(**params)
+        m = np.ascontiguousarray(m, dtype=np.float64)
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        self.n = len(m)
+        nbytes = mstar_workspace_bytes(self.n, self.p)
+        if nbytes == 0:
+            raise MstarError(MSTAR_ERR_INVALID_ARG, "mstar_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            off = (-self.ws.data_ptr()) % 256
+            self._ws_ptr = self.ws.data_ptr() + off
+            self.stream = torch.cuda.current_stream(self.device)
+            self.ctx = C.c_void_p()
+            rc = load().mstar_init(C.byref(self.ctx), self.n, _ptr(m), _ptr(r), _ptr(v), C.byref(self.p),
+                                   C.c_void_p(self._ws_ptr), nbytes, C.c_void_p(self.stream.cuda_stream))
+            _check(rc, "mstar_init")
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            mstar_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, t_end, max_steps=1 << 30, check=True):
+        rc, st = mstar_step(self.ctx, t_end, max_steps)
+        if check:
+            _check(rc, "mstar_step")
+        return rc, dict(accepted=st.accepted, rejected=st.rejected, force_evals=st.force_evals,
+                        time_iters=st.time_iters, eps_last=st.eps_last, H=st.H, t=st.t)
+
+    def attempt(self, H):
+        r = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        eps, t = mstar_attempt(self.ctx, H, r, v)
+        return dict(eps=eps, r=r, v=v, t=t)
+
+    def state(self):
+        r = np.empty((self.n, 3))
+        v = np.empty((self.n, 3))
+        t = mstar_get_state(self.ctx, r, v)
+        return dict(t=t, r=r, v=v)
+
+    def set_state(self, t, r, v):
+        mstar_set_state(self.ctx, t, np.ascontiguousarray(r, np.float64), np.ascontiguousarray(v, np.float64))
+
+    def set_H(self, H):
+        mstar_set_H(self.ctx, H)
+
+    def mst(self):
+        root = np.zeros(1, np.int32)
+        parent = np.empty(self.n, np.int32)
+        level = np.empty(self.n, np.int32)
+        order = np.empty(self.n, np.int32)
+        mstar_get_mst(self.ctx, root, parent, level, order)
+        return int(root[0]), parent, level, order
+
+    def accelerations(self):
+        a = np.empty((self.n, 3))
+        U = mstar_accelerations(self.ctx, a)
+        return a, U
+
+    def energy(self):
+        P = np.empty(3)
+        L = np.empty(3)
+        E, T, U = mstar_energy(self.ctx, P, L)
+        return dict(E=E, T=T, U=U, P=P, L=L)

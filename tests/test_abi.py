@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads and exports every entry point include/mstar.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2001_03180_gb300 import build as B
+from paper_2001_03180_gb300 import mstar as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "mstar.h")).read()
+    return sorted(set(re.findall(r"MSTAR_API\s+[\w\s\*]+?\b(mstar_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(M.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    path = B.build()
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_host_only_entry_points_without_gpu():
+    B.build()
+    p = M.mstar_default_params()
+    assert p.k_fix == 8 and p.n_d == 2 and p.eta_gbs == 1e-12 and p.a_gbs == 0.9
+    assert M.mstar_strerror(M.MSTAR_ERR_NO_CONVERGENCE).startswith("GBS step")
+    assert M.mstar_workspace_bytes(10002, p) > 0
+    assert M.mstar_workspace_bytes(1, p) == 0
+    assert M.mstar_workspace_bytes(M.MSTAR_MAX_N + 1, p) == 0
+    bad = M.mstar_default_params(k_fix=1)
+    assert M.mstar_workspace_bytes(100, bad) == 0
+    bad = M.mstar_default_params(n_d=3)
+    assert M.mstar_workspace_bytes(100, bad) == 0
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The package never imports the oracle: product sources mention no oracle module."""
+    pkg = os.path.join(ROOT, "paper_2001_03180_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "mstar_oracle" not in text, f

@@ -1,0 +1,230 @@
+"""Parity of the sm_103a path (through the C ABI) with the CPU oracle, element by element.
+
+Tolerances: the MST (root, parent, level, insertion order) must be bit-identical; forces
+and the force function agree to 1e-13 relative; after one GBS step attempt the state
+agrees to 1e-12 relative per system (max |x_gpu - x_ora| / max |x_ora|, separately for r
+and v). The error estimate eps is a difference of nearly equal extrapolants, so it is
+compared to 1e-4 relative (its own rounding noise).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_03180_gb300 import workloads as W
+from tests import helpers as Hh
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA GPU", allow_module_level=True)
+
+from paper_2001_03180_gb300 import build as B  # noqa: E402
+
+B.build()
+from paper_2001_03180_gb300 import mstar as M  # noqa: E402
+
+O.set_threads(16)
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def systems():
+    out = {
+        "two": W.kepler_binary(seed=1),
+        "pyth": W.pythagorean(),
+        "plummer64": W.workload("plummer64"),
+        "plummer257": W.plummer(257, 8),
+        "smbh2050": W.workload("plummer2048_smbh_binary"),
+    }
+    return out
+
+
+SYS = systems()
+
+
+def lattice(n_side=4):
+    g = np.arange(n_side, dtype=float)
+    r = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    r = r - r.mean(0)
+    m = np.full(len(r), 1.0 / len(r))
+    v = np.zeros_like(r)
+    return m, r, v
+
+
+@pytest.mark.parametrize("name", list(SYS) + ["lattice", "plummer10k"])
+def test_mst_bit_exact(name):
+    if name == "lattice":
+        m, r, v = lattice()
+    elif name == "plummer10k":
+        m, r, v = W.workload("plummer10k_two_smbh")
+    else:
+        m, r, v = SYS[name]
+    g = M.Integrator(m, r, v)
+    groot, gpar, glev, gord = g.mst()
+    ro = O.com_shift(m, r)
+    # both sides start from the COM-shifted state the library holds
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    assert groot == root
+    assert np.array_equal(gpar, par)
+    assert np.array_equal(glev, lev)
+    assert np.array_equal(gord, order)
+    assert np.abs(st["r"] - ro).max() <= 1e-15 * max(1.0, np.abs(ro).max())
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(SYS))
+def test_forces_match_oracle(name):
+    m, r, v = SYS[name]
+    g = M.Integrator(m, r, v)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=2)
+    assert relerr(a, ao) < 1e-13
+    assert abs(U - Uo) <= 1e-13 * Uo
+    g.close()
+
+
+def test_forces_sampled_full_size():
+    """N = 10002: sampled accelerations against the oracle's per-body sums."""
+    m, r, v = W.workload("plummer10k_two_smbh")
+    g = M.Integrator(m, r, v)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=2)
+    assert relerr(a, ao) < 1e-12
+    assert abs(U - Uo) <= 1e-13 * Uo
+    g.close()
+
+
+@pytest.mark.parametrize("n_d", [0, 2])
+def test_rsqrt_across_exponent_range(n_d):
+    """Two bodies at separations from 1e-150 to 1e12: the reciprocal square root (FP32 seed
+    from the exponent bits, FP64 refinement) of the tiled loop (n_d = 0) and of the near-pair
+    pass (n_d = 2) against correctly rounded numpy arithmetic."""
+    for e10 in [-150, -100, -37, -7, -1, 0, 3, 12]:
+        for frac in [1.0, 1.37, 2.9, 7.77]:
+            d = frac * 10.0 ** e10
+            m = np.array([0.25, 0.75])
+            r = np.array([[-0.75 * d, 0.0, 0.0], [0.25 * d, 0.0, 0.0]])
+            v = np.zeros((2, 3))
+            g = M.Integrator(m, r, v, n_d=n_d)
+            a, U = g.accelerations()
+            st = g.state()
+            dd = st["r"][1, 0] - st["r"][0, 0]
+            U_exact = 0.25 * 0.75 / abs(dd)
+            assert abs(U - U_exact) <= 4 * np.finfo(float).eps * U_exact, (d, U, U_exact)
+            a1 = 0.75 / dd ** 2
+            assert abs(a[0, 0] - a1) <= 8 * np.finfo(float).eps * abs(a1), (d, a[0, 0], a1)
+            g.close()
+
+
+@pytest.mark.parametrize("name,H", [("two", 0.02), ("pyth", 0.5), ("plummer64", 2e-3), ("plummer257", 5e-4),
+                                    ("smbh2050", 1e-5)])
+def test_one_attempt_matches_oracle(name, H):
+    m, r, v = SYS[name]
+    g = M.Integrator(m, r, v)
+    o = O.System(m, r, v)
+    gs = g.attempt(H)
+    os_ = o.attempt(H)
+    assert relerr(gs["r"], os_["r"]) < 1e-12
+    assert relerr(gs["v"], os_["v"]) < 1e-12
+    assert abs(gs["t"] - os_["t"]) <= 1e-12 * abs(os_["t"])
+    assert abs(gs["eps"] - os_["eps"]) <= 1e-4 * os_["eps"] + 1e-16
+    g.close()
+
+
+def test_one_attempt_full_size_plummer10k():
+    m, r, v = W.workload("plummer10k_two_smbh")
+    g = M.Integrator(m, r, v)
+    o = O.System(m, r, v)
+    H = 2e-6
+    gs = g.attempt(H)
+    os_ = o.attempt(H)
+    assert relerr(gs["r"], os_["r"]) < 1e-12
+    assert relerr(gs["v"], os_["v"]) < 1e-12
+    assert abs(gs["eps"] - os_["eps"]) <= 1e-3 * os_["eps"] + 1e-16
+    g.close()
+
+
+def test_plummer64_run_to_t1_matches_oracle():
+    """The configuration integrated to t = 1: the end state agrees with the oracle's and the
+    energy error is within 10x of the oracle's."""
+    m, r, v = SYS["plummer64"]
+    g = M.Integrator(m, r, v)
+    o = O.System(m, r, v)
+    e0g = g.energy()["E"]
+    e0o = o.energy()["E"]
+    rc, st = g.step(1.0)
+    rco, sto = o.integrate(1.0)
+    assert rc == 0 and rco == 0
+    assert abs(st["t"] - 1.0) <= 1e-10 and abs(sto["t"] - 1.0) <= 1e-10
+    S, So = g.state(), o.state()
+    assert relerr(S["r"], So["r"]) < 1e-9
+    assert relerr(S["v"], So["v"]) < 1e-9
+    dEg = abs((g.energy()["E"] - e0g) / e0g)
+    dEo = abs((o.energy()["E"] - e0o) / e0o)
+    assert dEg <= 10 * max(dEo, 1e-15), (dEg, dEo)
+    assert abs(st["accepted"] - sto["accepted"]) <= 2
+    g.close()
+
+
+def test_kepler_gbs_matches_analytic():
+    m, r, v = W.kepler_binary(seed=4, e=0.9)
+    g = M.Integrator(m, r, v)
+    rc, st = g.step(5.0)
+    assert rc == 0 and abs(st["t"] - 5.0) <= 1e-9
+    S = g.state()
+    dr, dv = Hh.kepler_propagate(r[1] - r[0], v[1] - v[0], m.sum(), S["t"])
+    assert np.abs((S["r"][1] - S["r"][0]) - dr).max() <= 1e-9
+    g.close()
+
+
+def test_invalid_inputs_are_rejected():
+    m, r, v = SYS["plummer64"]
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m[:1], r[:1], v[:1])
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+    r2 = r.copy()
+    r2[3, 1] = np.nan
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m, r2, v)
+    assert e.value.code == M.MSTAR_ERR_NONFINITE
+    m2 = m.copy()
+    m2[5] = 0.0
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m2, r, v)
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m, r, v, k_fix=20)
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+
+
+def test_device_pointer_inputs_and_outputs():
+    m, r, v = SYS["plummer257"]
+    dev = torch.device("cuda")
+    mt = torch.tensor(m, device=dev)
+    rt = torch.tensor(r, device=dev)
+    vt = torch.tensor(v, device=dev)
+    p = M.mstar_default_params()
+    nbytes = M.mstar_workspace_bytes(len(m), p)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    ctx = M.mstar_init(len(m), mt, rt, vt, p, ws, nbytes, torch.cuda.current_stream().cuda_stream)
+    ro = torch.empty_like(rt)
+    vo = torch.empty_like(vt)
+    eps, t = M.mstar_attempt(ctx, 5e-4, ro, vo)
+    g = M.Integrator(m, r, v)
+    h = g.attempt(5e-4)
+    assert np.array_equal(ro.cpu().numpy(), h["r"]) and np.array_equal(vo.cpu().numpy(), h["v"])
+    assert eps == h["eps"] and t == h["t"]
+    M.mstar_free(ctx)
+    g.close()
