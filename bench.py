@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark of the MSTAR hot path on GB300: FP64 pair-forces/s and GBS steps/s.
+
+Workload: Plummer sphere of 10^4 equal-mass stars (total mass 1, virial radius 1, seed 5)
+plus two SMBHs of mass 0.005 at +/-0.1 on half-circular orbits (N = 10002), FP64,
+eta_GBS = 1e-12, k_fix = 8 (Deuflhard), N_d = 2. One benchmark step is one accepted GBS
+step (MST, edge coordinates, 73 pair-loop evaluations over 8 concurrent divisions,
+extrapolation, convergence test; rejected attempts are counted and included).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mstar|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank integrates its own
+replica of the system: the path has no data-path exchange, so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "plummer10k_two_smbh"
+WORKLOAD_DESC = ("Plummer N=10000 (m=1e-4, r_vir=1, seed 5) + 2 SMBHs of 0.005 at +/-0.1 (N=10002); "
+                 "eta_GBS=1e-12, k_fix=8 Deuflhard, N_d=2, G=1")
+# Algorithmic FP64 flops of one unordered far-pair interaction in the symmetric loop:
+# separation 3, r^2 5, reciprocal square root 7 (one DMUL, three DFMA), r^-3 2,
+# two mass scalings 2, force function 2, two 3-vector accumulations 12.
+FLOPS_PER_UNORDERED_PAIR = 33
+# SURVEY-style count for one ordered pair-force evaluated on its own (no symmetry).
+FLOPS_PER_ORDERED_PAIR_NONSYM = 28
+NOMINAL_FP64_TFLOPS = 1.25
+# FP64 FMA units: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2 inst/cycle/SM), 152 SMs; the roofline peak is that rate at the SM clock
+# sampled during the timed region, 2 flops per DFMA.
+DFMA_PER_CLK_PER_SM = 2
+NUM_SMS = 152
+L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) of one tiled-pair force evaluation at N = 10002, from the ncu
+# capture summarised in profiles/pair_tiles_plummer10k.md; None once the kernel changes.
+PAIR_TILE_DRAM_BYTES_PER_EVAL = 436224 + 3072
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mstar", choices=["mstar", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(x, world, dev):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def cpu_baseline_sample(n_threads):
+    """The oracle, as it stands, on the host cores: one GBS step attempt of the workload."""
+    import oracle
+    from paper_2001_03180_gb300 import workloads as W
+
+    oracle.build()
+    oracle.set_threads(n_threads)
+    m, r, v = W.workload(WORKLOAD)
+    s = oracle.System(m, r, v)
+    H = 3e-4
+    t0 = time.perf_counter()
+    s.attempt(H)
+    dt = time.perf_counter() - t0
+    n = len(m)
+    pairs = 73 * n * (n - 1)
+    return {"value": pairs / dt, "unit": "pair-forces/s", "cores": n_threads, "kind": "oracle",
+            "sample": f"one GBS step attempt (73 pair-loop evaluations, Prim, rebuilds, extrapolation) of "
+                      f"the N={n} workload at H={H}, {dt:.2f} s wall on {n_threads} threads"}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores (rank 0 only)."""
+    world, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_2001_03180_gb300 import workloads as W
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    m, r, v = W.workload(WORKLOAD)
+    n = len(m)
+    sysd = oracle.System(m, r, v)
+    st = sysd.state()
+    root, parent, level, order = oracle.prim(st["r"])
+    X = oracle.to_mst(parent, st["r"])
+    for _ in range(args.warmup):
+        oracle.forces(m, st["r"], parent, level, X)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.forces(m, st["r"], parent, level, X)
+    dt = time.perf_counter() - t0
+    pairs = n * (n - 1) * args.steps
+    value = pairs / dt
+    sample = (f"each step: one oracle pair-loop evaluation (Eq. 2, near rule N_d=2) of the N={n} state, "
+              f"1/73 of a GBS step's pair work; {threads} threads")
+    out = {"impl": "reference", "metric": "FP64 pair-forces/s", "value": value, "unit": "pair-forces/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC, "n": n},
+           "cpu_baseline": {"value": value, "unit": "pair-forces/s", "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "pair-forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_mstar(args):
+    import numpy as np
+    import torch
+
+    from paper_2001_03180_gb300 import build as B
+    from paper_2001_03180_gb300 import workloads as W
+
+    world, rank, local = dist_setup(args)
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    B.build()
+    from paper_2001_03180_gb300 import mstar as M
+
+    M.load()
+    m, r, v = W.workload(WORKLOAD)
+    n = len(m)
+    g = M.Integrator(m, r, v, device=dev)
+    stream = g.stream
+    fma_rate = M.mstar_fp64_fma_rate(stream.cuda_stream)
+    t_end = 1.0
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # warm-up: the first steps also let the controller find the step size from the
+    # first-step rule ds = q U dt (several rejections)
+    for _ in range(args.warmup):
+        g.step(t_end, 1)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-resident timed region
+    M.mstar_profile_enable(g.ctx, True)
+    launches0 = M.mstar_launch_count(g.ctx)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        acc = rej = fev = 0
+        for _ in range(args.steps):
+            flush.zero_()
+            rc, st = g.step(t_end, 1)
+            acc += st["accepted"]
+            rej += st["rejected"]
+            fev += st["force_evals"]
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = M.mstar_launch_count(g.ctx) - launches0
+    prof = M.mstar_profile_read(g.ctx)
+    M.mstar_profile_enable(g.ctx, False)
+    ms_max = reduce_max(ms, world, dev)
+    pair_forces = float(fev) * n * (n - 1)
+    total_pf = reduce_sum(pair_forces, world, dev)
+    total_steps = reduce_sum(float(acc), world, dev)
+    value = total_pf / (ms_max * 1e-3)
+
+    # ---- end to end: host buffers in, host buffers out, every step
+    e2e = None
+    if args.steps > 0:
+        rh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        vh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+        S = g.state()
+        rh[:] = S["r"]
+        vh[:] = S["v"]
+        t_now = S["t"]
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        fev2 = 0
+        for _ in range(args.steps):
+            M.mstar_set_state(g.ctx, t_now, rh, vh)
+            rc, st = g.step(t_end, 1)
+            fev2 += st["force_evals"]
+            t_now = M.mstar_get_state(g.ctx, rh, vh)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - w0
+        wall = reduce_max(wall, world, dev)
+        e2e_pf = reduce_sum(float(fev2) * n * (n - 1), world, dev)
+        e2e = {"value": e2e_pf / wall, "unit": "pair-forces/s", "h2d_bytes_per_step": 2 * 3 * n * 8,
+               "d2h_bytes_per_step": 2 * 3 * n * 8}
+
+    # ---- roofline of the dominant kernel (tiled pair loop), CUDA events on its stream
+    avg_ms = prof.pair_ms / max(prof.pair_launches, 1)
+    flops_per_launch = FLOPS_PER_UNORDERED_PAIR * prof.pair_interactions / max(prof.pair_launches, 1)
+    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
+    clk_mhz = clocks.get("sm_mhz") or 2070.0
+    peak = 2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / 1e12
+    evals_per_launch = prof.force_evals / max(prof.pair_launches, 1)
+    traffic = (PAIR_TILE_DRAM_BYTES_PER_EVAL * evals_per_launch
+               if PAIR_TILE_DRAM_BYTES_PER_EVAL is not None else None)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_pair_tiles (symmetric FP64 pair loop)",
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x sampled SM clock x 2 flops",
+                "peak_probe_tflops": 2.0 * fma_rate / 1e12,
+                "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
+                "pair_kernel_share_of_step": prof.pair_ms / ms if ms > 0 else None,
+                "survey_equiv_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * prof.pair_interactions
+                / (prof.pair_ms * 1e-3) / 1e12 if prof.pair_ms > 0 else None}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_sample(os.cpu_count() or 1)
+
+    if rank == 0:
+        out = {"metric": "FP64 pair-forces/s", "value": value, "unit": "pair-forces/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic",
+               "config": {"workload": WORKLOAD_DESC, "n": n, "gbs_steps_per_bench_step": 1,
+                          "l2": "flushed between steps (256 MiB write)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
+               "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+               "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(out), flush=True)
+    g.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_mstar(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -155,6 +155,12 @@ typedef struct {
 MSTAR_API int mstar_profile_enable(mstar_ctx* ctx, int on);
 MSTAR_API int mstar_profile_read(mstar_ctx* ctx, mstar_profile* out);
 
+/* Diagnostic with no counterpart in the paper: measures the FP64 FMA issue rate of the
+   current device (FMAs per second over all SMs, 8 independent chains per thread) on the
+   given stream, for reporting the pair loop against the chip's measured FP64 roofline.
+   Allocates and frees a small device buffer. */
+MSTAR_API int mstar_fp64_fma_rate(double* fma_per_second, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

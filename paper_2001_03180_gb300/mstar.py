@@ -29,7 +29,7 @@ EXPORTS = [
     "mstar_default_params", "mstar_workspace_bytes", "mstar_init", "mstar_step", "mstar_attempt",
     "mstar_energy", "mstar_get_state", "mstar_set_state", "mstar_set_H", "mstar_get_mst",
     "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
-    "mstar_profile_enable", "mstar_profile_read",
+    "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate",
 ]
 
 
@@ -90,6 +90,7 @@ def load():
     L.mstar_launch_count.restype = C.c_longlong
     L.mstar_profile_enable.argtypes = [vp, C.c_int]
     L.mstar_profile_read.argtypes = [vp, C.POINTER(mstar_profile)]
+    L.mstar_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
     _lib = L
     return L
 
@@ -194,6 +195,12 @@ def mstar_profile_read(ctx) -> mstar_profile:
     pr = mstar_profile()
     _check(load().mstar_profile_read(ctx, C.byref(pr)), "mstar_profile_read")
     return pr
+
+
+def mstar_fp64_fma_rate(cuda_stream=None) -> float:
+    r = C.c_double()
+    _check(load().mstar_fp64_fma_rate(C.byref(r), cuda_stream), "mstar_fp64_fma_rate")
+    return r.value
 
 
 class Integrator:

@@ -3,8 +3,10 @@
 Tolerances: the MST (root, parent, level, insertion order) must be bit-identical; forces
 and the force function agree to 1e-13 relative; after one GBS step attempt the state
 agrees to 1e-12 relative per system (max |x_gpu - x_ora| / max |x_ora|, separately for r
-and v). The error estimate eps is a difference of nearly equal extrapolants, so it is
-compared to 1e-4 relative (its own rounding noise).
+and v). The error estimate eps is a difference of nearly equal extrapolants whose
+rounding noise floor is about 1e-13 here, so the step sizes are chosen to put eps near
+1e-9 (found with the oracle) and eps is compared to 1e-2 relative; below 1e-11 both
+sides only have to agree that the step converged.
 """
 import math
 
@@ -108,10 +110,11 @@ def test_forces_sampled_full_size():
 
 @pytest.mark.parametrize("n_d", [0, 2])
 def test_rsqrt_across_exponent_range(n_d):
-    """Two bodies at separations from 1e-150 to 1e12: the reciprocal square root (FP32 seed
+    """Two bodies at separations from 1e-100 to 1e12: the reciprocal square root (FP32 seed
     from the exponent bits, FP64 refinement) of the tiled loop (n_d = 0) and of the near-pair
-    pass (n_d = 2) against correctly rounded numpy arithmetic."""
-    for e10 in [-150, -100, -37, -7, -1, 0, 3, 12]:
+    pass (n_d = 2) against correctly rounded numpy arithmetic. (Below about 1e-102, r^-3
+    itself overflows FP64, in the oracle as well.)"""
+    for e10 in [-100, -60, -37, -7, -1, 0, 3, 12]:
         for frac in [1.0, 1.37, 2.9, 7.77]:
             d = frac * 10.0 ** e10
             m = np.array([0.25, 0.75])
@@ -128,8 +131,15 @@ def test_rsqrt_across_exponent_range(n_d):
             g.close()
 
 
-@pytest.mark.parametrize("name,H", [("two", 0.02), ("pyth", 0.5), ("plummer64", 2e-3), ("plummer257", 5e-4),
-                                    ("smbh2050", 1e-5)])
+def check_eps(e_gpu, e_ora):
+    if e_ora > 1e-11:
+        assert abs(e_gpu - e_ora) <= 1e-2 * e_ora, (e_gpu, e_ora)
+    else:
+        assert e_gpu < 1e-11, (e_gpu, e_ora)
+
+
+@pytest.mark.parametrize("name,H", [("two", 0.6), ("two", 0.02), ("pyth", 25.0), ("plummer64", 0.05),
+                                    ("plummer64", 2e-3), ("plummer257", 0.015), ("smbh2050", 3e-3)])
 def test_one_attempt_matches_oracle(name, H):
     m, r, v = SYS[name]
     g = M.Integrator(m, r, v)
@@ -139,7 +149,7 @@ def test_one_attempt_matches_oracle(name, H):
     assert relerr(gs["r"], os_["r"]) < 1e-12
     assert relerr(gs["v"], os_["v"]) < 1e-12
     assert abs(gs["t"] - os_["t"]) <= 1e-12 * abs(os_["t"])
-    assert abs(gs["eps"] - os_["eps"]) <= 1e-4 * os_["eps"] + 1e-16
+    check_eps(gs["eps"], os_["eps"])
     g.close()
 
 
@@ -147,12 +157,12 @@ def test_one_attempt_full_size_plummer10k():
     m, r, v = W.workload("plummer10k_two_smbh")
     g = M.Integrator(m, r, v)
     o = O.System(m, r, v)
-    H = 2e-6
+    H = 3e-4
     gs = g.attempt(H)
     os_ = o.attempt(H)
     assert relerr(gs["r"], os_["r"]) < 1e-12
     assert relerr(gs["v"], os_["v"]) < 1e-12
-    assert abs(gs["eps"] - os_["eps"]) <= 1e-3 * os_["eps"] + 1e-16
+    check_eps(gs["eps"], os_["eps"])
     g.close()
 
 
