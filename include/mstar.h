@@ -161,6 +161,32 @@ MSTAR_API int mstar_profile_read(mstar_ctx* ctx, mstar_profile* out);
    Allocates and frees a small device buffer. */
 MSTAR_API int mstar_fp64_fma_rate(double* fma_per_second, void* cuda_stream);
 
+/* Largest n that mstar_accelerations_noalloc accepts. Its scratch is a fixed static device
+   array of about 1.1 MB (positions, masses and the per-tile partial sums for 2048 bodies). */
+#define MSTAR_NOALLOC_MAX_N 2048
+
+/* No counterpart in the paper: an allocation-free form of the pair loop, for callers that
+   may not allocate device memory - for example a sub-integrator living inside a larger code
+   whose memory manager owns the whole device heap, or a host loop that cannot afford the
+   device synchronisation cudaMalloc implies. It needs no context and calls no allocating
+   routine (no cudaMalloc/cudaFree, no allocating library call).
+   Computes, with every pair taken as far (Cartesian separations, as n_d = 0), the
+   accelerations a_i = G sum_j m_j (r_j - r_i)/|r_j - r_i|^3 (Eq. 2) and the force function
+   U = G sum_{i<j} m_i m_j / |r_j - r_i| (Eq. 1), with the same symmetric tiled loop and
+   reduction order as mstar_accelerations on a context created with n_d = 0.
+   Arguments: n in [2, MSTAR_NOALLOC_MAX_N] (larger n: MSTAR_ERR_UNSUPPORTED); m[n] and
+   r[n x 3] (row-major) inputs, a[n x 3] and U[1] outputs - all four DEVICE (or managed)
+   pointers owned by the caller (host pointers: MSTAR_ERR_INVALID_ARG); G > 0. The work is
+   queued on cuda_stream and the call returns without waiting for it.
+   Scratch: one file-scope static __device__ array that every GPU loading the library holds
+   until the process exits. Every call uses the same array and overwrites what the previous
+   call left there (each call rewrites all it reads), so calls that overlap on the GPU - on
+   different streams or from different threads - race and must be serialised by the caller.
+   The first call on each device looks up the array's device address (cudaGetSymbolAddress);
+   make that first call before capturing a stream into a graph. */
+MSTAR_API int mstar_accelerations_noalloc(int n, const double* m, const double* r, double G, double* a,
+                                          double* U, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

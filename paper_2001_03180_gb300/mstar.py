@@ -29,8 +29,9 @@ EXPORTS = [
     "mstar_default_params", "mstar_workspace_bytes", "mstar_init", "mstar_step", "mstar_attempt",
     "mstar_energy", "mstar_get_state", "mstar_set_state", "mstar_set_H", "mstar_get_mst",
     "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
-    "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate",
+    "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate", "mstar_accelerations_noalloc",
 ]
+MSTAR_NOALLOC_MAX_N = 2048
 
 
 class mstar_params(C.Structure):
@@ -91,6 +92,7 @@ def load():
     L.mstar_profile_enable.argtypes = [vp, C.c_int]
     L.mstar_profile_read.argtypes = [vp, C.POINTER(mstar_profile)]
     L.mstar_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
+    L.mstar_accelerations_noalloc.argtypes = [C.c_int, dp, dp, C.c_double, dp, dp, vp]
     _lib = L
     return L
 
@@ -201,6 +203,12 @@ def mstar_fp64_fma_rate(cuda_stream=None) -> float:
     r = C.c_double()
     _check(load().mstar_fp64_fma_rate(C.byref(r), cuda_stream), "mstar_fp64_fma_rate")
     return r.value
+
+
+def mstar_accelerations_noalloc(n, m, r, G, a, U, cuda_stream=None) -> int:
+    """Allocation-free pair loop; m, r, a, U are device tensors. Returns the status code."""
+    return load().mstar_accelerations_noalloc(int(n), _ptr(m), _ptr(r), float(G), _ptr(a), _ptr(U),
+                                              cuda_stream)
 
 
 class Integrator:
