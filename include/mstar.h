@@ -128,7 +128,10 @@ MSTAR_API int mstar_set_H(mstar_ctx* ctx, double H);
 /* Prim's MST of the current positions (Sec. 3.2) and its indexing (Sec. 3.4): root
    (closest to the centre of mass, lowest index on ties), parent[n] (-1 at the root),
    level[n], order[n] (insertion order). Ties: argmin takes the lowest index, keys are
-   replaced only by strictly smaller squared distances. Any output may be NULL. */
+   replaced only by strictly smaller squared distances. Any output may be NULL.
+   With order == NULL the tree comes from the builder the GBS step uses (Boruvka rounds for
+   n >= 512, which yield Prim's tree whenever no two deciding distances are equal, and
+   Prim's kernel otherwise); with order != NULL Prim's kernel runs and reports the order. */
 MSTAR_API int mstar_get_mst(mstar_ctx* ctx, int* root, int* parent, int* level, int* order);
 
 /* One pair-loop evaluation on the current state (Eq. 2 with the near/far separation rule

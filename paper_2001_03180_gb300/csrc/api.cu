@@ -203,7 +203,9 @@ void prof_flush(mstar_ctx* c) {
 // step start (one force evaluation); reads U0 and T0 back.
 int prepare_step(mstar_ctx* c, double* U0, double* T0) {
   if (!c->mst_valid) {
-    CK(launch_prim(c));
+    bool tied = true;
+    if (c->n >= kBoruvkaMinN) CK(launch_mst_boruvka(c, &tied));
+    if (tied) CK(launch_prim(c));
     CK(launch_tree(c));
     c->mst_valid = true;
   }
@@ -507,8 +509,16 @@ int mstar_set_state(mstar_ctx* c, double t, const double* r, const double* v) {
 
 int mstar_get_mst(mstar_ctx* c, int* root, int* parent, int* level, int* order) {
   if (!c) return MSTAR_ERR_INVALID_ARG;
-  if (!c->mst_valid) {
+  if (order) {
+    // Prim's kernel records the insertion order; it builds the same tree as the step's
+    // MST builder, so the step buffers stay valid.
     CK(launch_prim(c));
+    CK(launch_tree(c));
+    c->mst_valid = true;
+  } else if (!c->mst_valid) {
+    bool tied = true;
+    if (c->n >= kBoruvkaMinN) CK(launch_mst_boruvka(c, &tied));
+    if (tied) CK(launch_prim(c));
     CK(launch_tree(c));
     c->mst_valid = true;
   }

@@ -1,0 +1,386 @@
+// Exact MST for the GBS step by Boruvka rounds over the whole GPU.
+//
+// Sec. 3.2 builds the MST with Prim's algorithm; its N sequential iterations keep a GPU on
+// one SM. When all squared distances that decide the tree are distinct, the MST is unique
+// (Sec. 3.1), so any exact MST algorithm yields Prim's tree. Boruvka's rounds are
+// parallel: every vertex finds its nearest vertex outside its component (exact FP64
+// comparisons, filtered by rigorous float lower bounds), every component takes its
+// cheapest outgoing edge, and components merge along those edges. If two different
+// candidates ever compare exactly equal in FP64, the tree could depend on tie-breaking
+// rules, and the caller falls back to the Prim kernel, which applies the paper's rule.
+// The tree is then oriented from Prim's root (the body closest to the centre of mass) by a
+// breadth-first walk, which gives the same parent and level as Prim's indexing.
+//
+// Distances are computed exactly as the CPU definition does: ((dx*dx)+(dy*dy))+(dz*dz)
+// with dx = x_u - x_v, each operation rounded separately.
+#include <climits>
+#include <cstring>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace mstar {
+namespace {
+
+constexpr int kBT = 128;  // vertices per CTA in the nearest-foreign-neighbour search
+
+__device__ __forceinline__ double d2_exact(const double* X, const double* Y, const double* Z, int u, int v) {
+  const double dx = __dsub_rn(X[u], X[v]), dy = __dsub_rn(Y[u], Y[v]), dz = __dsub_rn(Z[u], Z[v]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Nearest foreign neighbour (smallest exact squared distance to a vertex of another
+// component) of every vertex whose cached neighbour is missing or has become internal;
+// CTA (tile, part) scans the part-th slice of the candidates. Writes per (vertex, part)
+// the exact distance bits and the neighbour; exact equal distances to two different
+// candidates set *tie.
+__global__ void __launch_bounds__(kBT)
+k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* __restrict__ Y,
+      const double* __restrict__ Z, const float* __restrict__ f4, const int* __restrict__ comp,
+      const int* __restrict__ nbr, unsigned long long* __restrict__ partD, int* __restrict__ partJ,
+      int* __restrict__ tie) {
+  __shared__ float sx[kBT], sy[kBT], sz[kBT], se[kBT];
+  __shared__ int sc[kBT];
+  __shared__ int any;
+  const int i = blockIdx.x * kBT + threadIdx.x;
+  const int part = blockIdx.y;
+  bool need = false;
+  int ci = -1;
+  if (i < n) {
+    ci = comp[i];
+    const int b = nbr[i];
+    need = (b < 0) || (comp[b] == ci);
+  }
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  if (need) any = 1;
+  __syncthreads();
+  if (!any) return;
+  const float xi = i < n ? f4[4 * i] : 0.0f, yi = i < n ? f4[4 * i + 1] : 0.0f, zi = i < n ? f4[4 * i + 2] : 0.0f;
+  const float ei = i < n ? f4[4 * i + 3] : 0.0f;
+  // running best: exact distance bits, index, and a float upper bound (with margin)
+  unsigned long long bD = ~0ull;
+  int bj = -1;
+  float bhi = __int_as_float(0x7f800000);
+  int mytie = 0;
+  const int per = (n + nparts - 1) / nparts;
+  const int j_lo = part * per, j_hi = min(n, j_lo + per);
+  for (int t0 = j_lo; t0 < j_hi; t0 += kBT) {
+    __syncthreads();
+    const int j = t0 + threadIdx.x;
+    if (j < j_hi) {
+      sx[threadIdx.x] = f4[4 * j];
+      sy[threadIdx.x] = f4[4 * j + 1];
+      sz[threadIdx.x] = f4[4 * j + 2];
+      se[threadIdx.x] = f4[4 * j + 3];
+      sc[threadIdx.x] = comp[j];
+    }
+    __syncthreads();
+    if (!need) continue;
+    const int cnt = min(kBT, j_hi - t0);
+    for (int q = 0; q < cnt; ++q) {
+      // a lower bound of |r_i - r_j|^2 from the float copies: each coordinate difference
+      // errs by at most (|x_i| + |x_j| + |dx|) 2^-24; ei, ej hold max|coordinate| 2^-23.
+      const float dx = fabsf(xi - sx[q]), dy = fabsf(yi - sy[q]), dz = fabsf(zi - sz[q]);
+      const float e = ei + se[q];
+      const float lx = fmaxf(fmaf(dx, -0x1p-22f, dx) - e, 0.0f);
+      const float ly = fmaxf(fmaf(dy, -0x1p-22f, dy) - e, 0.0f);
+      const float lz = fmaxf(fmaf(dz, -0x1p-22f, dz) - e, 0.0f);
+      const float lo = ((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f);
+      if (lo <= bhi && sc[q] != ci) {
+        const int jj = t0 + q;
+        const double d = d2_exact(X, Y, Z, i, jj);
+        const unsigned long long db = key_bits(d);
+        if (db < bD) {
+          bD = db;
+          bj = jj;
+          bhi = __double2float_ru(d) * (1.0f + 0x1p-20f);
+        } else if (db == bD && jj != bj) {
+          mytie = 1;
+        }
+      }
+    }
+  }
+  if (need) {
+    partD[(size_t)part * npad + i] = bD;
+    partJ[(size_t)part * npad + i] = bj;
+    if (mytie) atomicOr(tie, 1);
+  }
+}
+
+// Merge the parts: exact minimum, ties flagged; cache the neighbour.
+__global__ void k_nfn_merge(int n, int npad, int nparts, const int* __restrict__ comp, int* __restrict__ nbr,
+                            unsigned long long* __restrict__ nbrD, const unsigned long long* __restrict__ partD,
+                            const int* __restrict__ partJ, int* __restrict__ tie) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int b = nbr[i];
+  if (b >= 0 && comp[b] != comp[i]) return;
+  unsigned long long bD = ~0ull;
+  int bj = -1;
+  for (int p = 0; p < nparts; ++p) {
+    const unsigned long long d = partD[(size_t)p * npad + i];
+    const int j = partJ[(size_t)p * npad + i];
+    if (j < 0) continue;
+    if (d < bD) {
+      bD = d;
+      bj = j;
+    } else if (d == bD && j != bj) {
+      atomicOr(tie, 1);
+    }
+  }
+  nbr[i] = bj;
+  nbrD[i] = bD;
+}
+
+__global__ void k_comp_min(int n, const int* __restrict__ comp, const unsigned long long* __restrict__ nbrD,
+                           unsigned long long* __restrict__ cmin) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) atomicMin(&cmin[comp[i]], nbrD[i]);
+}
+
+__global__ void k_comp_edge(int n, const int* __restrict__ comp, const unsigned long long* __restrict__ nbrD,
+                            const unsigned long long* __restrict__ cmin, int* __restrict__ cidx,
+                            int* __restrict__ ccnt, int* __restrict__ tie) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = comp[i];
+  if (nbrD[i] == cmin[c]) {
+    if (atomicAdd(&ccnt[c], 1) > 0) atomicOr(tie, 1);  // two cheapest edges of equal weight
+    cidx[c] = i;
+  }
+}
+
+// Hook every component onto the component at the far end of its cheapest edge. Two
+// components that chose each other chose the same edge (weights distinct); the smaller
+// label becomes the root and records the edge once.
+__global__ void k_hook(int n, const int* __restrict__ comp, const int* __restrict__ nbr, const int* __restrict__ cidx,
+                       int* __restrict__ nxt, int* __restrict__ eu, int* __restrict__ ev, int* __restrict__ ecount) {
+  const int C = blockIdx.x * blockDim.x + threadIdx.x;
+  if (C >= n || comp[C] != C) return;
+  const int i = cidx[C];
+  const int j = nbr[i];
+  const int T = comp[j];
+  const int jT = nbr[cidx[T]];
+  const bool mutual = comp[jT] == C;
+  if (mutual && C < T) {
+    nxt[C] = C;
+  } else {
+    nxt[C] = T;
+  }
+  if (!mutual || C < T) {
+    const int e = atomicAdd(ecount, 1);
+    if (e < n - 1) {
+      eu[e] = i;
+      ev[e] = j;
+    }
+  }
+}
+
+__global__ void k_relabel(int n, int* __restrict__ comp, const int* __restrict__ nxt,
+                          unsigned long long* __restrict__ cmin, int* __restrict__ ccnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c = comp[i];
+  for (int guard = 0; guard < n && nxt[c] != c; ++guard) c = nxt[c];
+  comp[i] = c;
+  cmin[i] = ~0ull;
+  ccnt[i] = 0;
+}
+
+__global__ void k_boruvka_init(int n, const double* __restrict__ X, const double* __restrict__ Y,
+                               const double* __restrict__ Z, float* __restrict__ f4, int* __restrict__ comp,
+                               int* __restrict__ nbr, unsigned long long* __restrict__ cmin, int* __restrict__ ccnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float x = __double2float_rn(X[i]), y = __double2float_rn(Y[i]), z = __double2float_rn(Z[i]);
+  f4[4 * i] = x;
+  f4[4 * i + 1] = y;
+  f4[4 * i + 2] = z;
+  f4[4 * i + 3] = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))) * 0x1p-23f + 1e-37f;
+  comp[i] = i;
+  nbr[i] = -1;
+  cmin[i] = ~0ull;
+  ccnt[i] = 0;
+}
+
+// Orient the tree from Prim's root: adjacency from the edge list, then a breadth-first
+// walk in one CTA (levels are tree depths, independent of the visiting order).
+__global__ void __launch_bounds__(1024, 1)
+k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, const double* __restrict__ Z,
+         const int* __restrict__ eu, const int* __restrict__ ev, int* __restrict__ adj_off, int* __restrict__ adj,
+         int* __restrict__ parent, int* __restrict__ level, int* __restrict__ root_out, int* __restrict__ queue) {
+  extern __shared__ int smi[];
+  int* deg = smi;       // n
+  int* fill = deg + n;  // n
+  __shared__ unsigned long long rk[32];
+  __shared__ int ri[32];
+  __shared__ int qhead, qtail, lvl_end;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int v = tid; v < n; v += nt) {
+    deg[v] = 0;
+    fill[v] = 0;
+    parent[v] = -2;
+    level[v] = 0;
+  }
+  // root: closest to the origin (COM frame), lowest index on ties
+  unsigned long long bk = ~0ull;
+  int bi = INT_MAX;
+  for (int w = tid; w < n; w += nt) {
+    const double x = X[w], y = Y[w], z = Z[w];
+    const unsigned long long k =
+        key_bits(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+    if (k < bk || (k == bk && w < bi)) {
+      bk = k;
+      bi = w;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_down_sync(0xffffffffu, bk, o);
+    const int i2 = __shfl_down_sync(0xffffffffu, bi, o);
+    if (k2 < bk || (k2 == bk && i2 < bi)) {
+      bk = k2;
+      bi = i2;
+    }
+  }
+  if ((tid & 31) == 0) {
+    rk[tid >> 5] = bk;
+    ri[tid >> 5] = bi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int w = 1; w < (nt >> 5); ++w)
+      if (rk[w] < rk[0] || (rk[w] == rk[0] && ri[w] < ri[0])) {
+        rk[0] = rk[w];
+        ri[0] = ri[w];
+      }
+  }
+  for (int e = tid; e < n - 1; e += nt) {
+    atomicAdd(&deg[eu[e]], 1);
+    atomicAdd(&deg[ev[e]], 1);
+  }
+  __syncthreads();
+  const int root = ri[0];
+  if (tid == 0) {
+    int acc = 0;
+    for (int v = 0; v < n; ++v) {
+      adj_off[v] = acc;
+      acc += deg[v];
+    }
+    adj_off[n] = acc;
+    root_out[0] = root;
+    parent[root] = -1;
+    level[root] = 0;
+    queue[0] = root;
+    qhead = 0;
+    qtail = 1;
+  }
+  __syncthreads();
+  for (int e = tid; e < n - 1; e += nt) {
+    const int a = eu[e], b = ev[e];
+    adj[adj_off[a] + atomicAdd(&fill[a], 1)] = b;
+    adj[adj_off[b] + atomicAdd(&fill[b], 1)] = a;
+  }
+  __syncthreads();
+  while (true) {
+    const int h = qhead, t = qtail;
+    if (h >= t) break;
+    __syncthreads();
+    if (tid == 0) lvl_end = t;
+    for (int q = h + tid; q < t; q += nt) {
+      const int u = queue[q];
+      for (int a = adj_off[u]; a < adj_off[u + 1]; ++a) {
+        const int w = adj[a];
+        if (parent[w] == -2) {
+          parent[w] = u;
+          level[w] = level[u] + 1;
+          queue[atomicAdd(&qtail, 1)] = w;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid == 0) qhead = lvl_end;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// Boruvka MST of d.r into parent/level/root; returns cudaSuccess and sets *tied when a
+// tie was seen (the caller then runs the Prim kernel). Scratch lives in the pair partial
+// buffer, which is free while the tree is being built.
+cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
+  const int n = c->n, npad = c->npad;
+  const int nparts = n >= 4096 ? 8 : (n >= 1024 ? 4 : 1);
+  char* base = reinterpret_cast<char*>(c->d.P);
+  auto take = [&](size_t bytes) {
+    char* p = base;
+    base += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  float* f4 = reinterpret_cast<float*>(take(sizeof(float) * 4 * npad));
+  int* comp = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* nbr = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  unsigned long long* nbrD = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npad));
+  unsigned long long* cmin = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npad));
+  int* cidx = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* ccnt = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* nxt = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* eu = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* ev = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  int* adj_off = reinterpret_cast<int*>(take(sizeof(int) * (npad + 1)));
+  int* adj = reinterpret_cast<int*>(take(sizeof(int) * 2 * npad));
+  int* queue = reinterpret_cast<int*>(take(sizeof(int) * npad));
+  unsigned long long* partD = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npad * nparts));
+  int* partJ = reinterpret_cast<int*>(take(sizeof(int) * (size_t)npad * nparts));
+  int* flags = reinterpret_cast<int*>(take(sizeof(int) * 4));  // [0] tie, [1] edge count
+  const size_t p_bytes = (size_t)c->nslots * c->NT * 4 * npad * sizeof(double);
+  if ((size_t)(base - reinterpret_cast<char*>(c->d.P)) > p_bytes) {  // scratch does not fit: use Prim
+    *tied = true;
+    return cudaSuccess;
+  }
+  const double* X = c->d.r;
+  const double* Y = X + npad;
+  const double* Z = Y + npad;
+  const int nb = (n + 255) / 256;
+  cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) return e;
+  k_boruvka_init<<<nb, 256, 0, c->stream>>>(n, X, Y, Z, f4, comp, nbr, cmin, ccnt);
+  MSTAR_LAUNCHED(c);
+  int edges = 0;
+  *tied = false;
+  for (int round = 0; round < 64 && edges < n - 1; ++round) {
+    k_nfn<<<dim3((n + kBT - 1) / kBT, nparts), kBT, 0, c->stream>>>(n, npad, nparts, X, Y, Z, f4, comp, nbr, partD,
+                                                                     partJ, flags);
+    k_nfn_merge<<<nb, 256, 0, c->stream>>>(n, npad, nparts, comp, nbr, nbrD, partD, partJ, flags);
+    k_comp_min<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin);
+    k_comp_edge<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, cidx, ccnt, flags);
+    k_hook<<<nb, 256, 0, c->stream>>>(n, comp, nbr, cidx, nxt, eu, ev, flags + 1);
+    k_relabel<<<nb, 256, 0, c->stream>>>(n, comp, nxt, cmin, ccnt);
+    c->launches += 6;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c->host_buf, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+      return e;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
+    int fl[2];
+    std::memcpy(fl, c->host_buf, sizeof(fl));
+    if (fl[0]) {
+      *tied = true;
+      return cudaSuccess;
+    }
+    edges = fl[1];
+  }
+  if (edges != n - 1) {  // cannot happen without ties; be safe
+    *tied = true;
+    return cudaSuccess;
+  }
+  const size_t smem = sizeof(int) * 2 * (size_t)n;
+  if ((e = cudaFuncSetAttribute(k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  k_orient<<<1, 1024, smem, c->stream>>>(n, X, Y, Z, eu, ev, adj_off, adj, c->d.parent, c->d.level, c->d.root,
+                                         queue);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+}  // namespace mstar

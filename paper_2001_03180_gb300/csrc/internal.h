@@ -93,6 +93,9 @@ int choose_tile_warps(int n);
 // prim.cu
 cudaError_t launch_prim(mstar_ctx* c);      // MST of d.r -> parent, level, order, root
 cudaError_t launch_tree(mstar_ctx* c);      // grandparents and children CSR
+// boruvka.cu: exact MST by Boruvka rounds; *tied = true asks for the Prim kernel instead
+cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied);
+constexpr int kBoruvkaMinN = 512;           // below this Prim in one CTA is as fast
 
 // pair.cu: slots [slot_lo, slot_hi) -> sa, Ublk. n_d as in params (0 = all Cartesian).
 cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d);

@@ -2,17 +2,17 @@
 //
 // One CTA builds the whole tree: Prim's N iterations are sequential, and keeping the tree
 // inside one SM turns every iteration's global argmin into a block reduction with two
-// barriers. Each thread owns up to VPT vertices and keeps their exact FP64 keys (squared
-// distance to the tree) in registers; parents, levels and FP32 copies of the positions
-// live in shared memory.
+// barriers. Each thread owns up to VPT vertices and keeps their keys (squared distance to
+// the tree, as float intervals) in registers together with a summary of its smallest
+// bounds, rebuilt only when one of its keys changed; parents, levels, FP32 copies of the
+// positions and their rounding radii live in shared memory.
 //
-// Keys must be bit-identical to the CPU definition, so every distance that can change a
-// key is computed in FP64 exactly as ((dx*dx)+(dy*dy))+(dz*dz) without contraction. One
-// SM issues only ~1.6 FP64 instructions per clock, so an FP32 lower bound of the distance,
-// with a rigorous rounding-error allowance, first decides whether the new tree vertex can
-// possibly lower a key; only then is the FP64 distance evaluated. The skip test never
-// rejects a vertex whose FP64 distance would be strictly below its key (derivation beside
-// the code), so the tree, order and levels are those of the plain algorithm.
+// Keys must decide exactly as the CPU definition does, where every distance is computed in
+// FP64 as ((dx*dx)+(dy*dy))+(dz*dz) without contraction. One SM issues only ~1.6 FP64
+// instructions per clock and Prim's ~50 key decreases per iteration would each cost a
+// divergent FP64 sequence, so keys are carried as rigorous float intervals and FP64
+// distances are evaluated only when an interval comparison cannot decide (derivation beside
+// the code). The tree, order and levels are those of the plain algorithm.
 #include <climits>
 
 #include "device.cuh"
@@ -62,6 +62,58 @@ __device__ __forceinline__ void block_argmin(unsigned long long& k, int& i, unsi
   i = *wi;
 }
 
+// Per-thread summary for the argmin: the smallest upper bound (with its index) and the two
+// smallest lower bounds (index of the smallest). Non-negative float bit patterns order like
+// the values, and 0xffffffff sorts after every real key (+inf included).
+struct Cand {
+  unsigned hk;
+  int hidx;
+  unsigned l1;
+  int l1idx;
+  unsigned l2;
+};
+
+__device__ __forceinline__ Cand cand_identity() { return Cand{0xffffffffu, INT_MAX, 0xffffffffu, INT_MAX, 0xffffffffu}; }
+
+__device__ __forceinline__ void cand_combine(Cand& a, const Cand& b) {
+  if (b.hk < a.hk || (b.hk == a.hk && b.hidx < a.hidx)) {
+    a.hk = b.hk;
+    a.hidx = b.hidx;
+  }
+  if (b.l1 < a.l1 || (b.l1 == a.l1 && b.l1idx < a.l1idx)) {
+    a.l2 = min(a.l1, b.l2);
+    a.l1 = b.l1;
+    a.l1idx = b.l1idx;
+  } else {
+    a.l2 = min(a.l2, b.l1);
+  }
+}
+
+__device__ __forceinline__ Cand cand_shfl_down(const Cand& c, int o) {
+  Cand r;
+  r.hk = __shfl_down_sync(0xffffffffu, c.hk, o);
+  r.hidx = __shfl_down_sync(0xffffffffu, c.hidx, o);
+  r.l1 = __shfl_down_sync(0xffffffffu, c.l1, o);
+  r.l1idx = __shfl_down_sync(0xffffffffu, c.l1idx, o);
+  r.l2 = __shfl_down_sync(0xffffffffu, c.l2, o);
+  return r;
+}
+
+__device__ __forceinline__ double exact_d2(double xa, double ya, double za, double xb, double yb, double zb) {
+  const double dx = __dsub_rn(xa, xb), dy = __dsub_rn(ya, yb), dz = __dsub_rn(za, zb);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// Keys are kept as float intervals [klo, khi] that provably contain the exact FP64 key
+// (the squared distance to the tree, computed as the CPU definition does), plus
+// skey >= sqrt(khi) with margin. For a new tree vertex u and a non-tree vertex w:
+//  - if some coordinate's lower bound |dx| - err >= skey, then d(u,w)^2 > key: no update;
+//  - else with the interval [lo, hi] of d(u,w)^2: hi < klo -> certain update; lo >= khi ->
+//    certain no update; otherwise the FP64 distances are compared exactly.
+// The argmin is certain when the vertex with the smallest upper bound also has the
+// smallest lower bound and the second-smallest lower bound lies above that upper bound;
+// otherwise the exact keys of all vertices whose interval reaches down to it decide.
+// Every decision therefore equals the one the exact FP64 comparison makes.
 template <int VPT>
 __global__ void __launch_bounds__(1024, 1)
 k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_out,
@@ -70,20 +122,26 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
   float* xf = sm_f;
   float* yf = xf + n;
   float* zf = yf + n;
-  int* par = reinterpret_cast<int*>(zf + n);
-  int* lvl = par + n;
+  float* ew = zf + n;  // per-vertex error radius: max|coordinate| * 2^-23 + 1e-37
+  int* par = reinterpret_cast<int*>(ew + n);
+  short* lvl = reinterpret_cast<short*>(par + n);
   __shared__ unsigned long long rk[32], wk;
   __shared__ int ri[32], wi;
+  __shared__ Cand rc[32];
+  __shared__ Cand wc;
 
   const double* X = r;
   const double* Y = r + npad;
   const double* Z = r + 2 * (size_t)npad;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
 
   for (int w = tid; w < n; w += nt) {
-    xf[w] = __double2float_rn(X[w]);
-    yf[w] = __double2float_rn(Y[w]);
-    zf[w] = __double2float_rn(Z[w]);
+    const float x = __double2float_rn(X[w]), y = __double2float_rn(Y[w]), z = __double2float_rn(Z[w]);
+    xf[w] = x;
+    yf[w] = y;
+    zf[w] = z;
+    ew[w] = fmaxf(fabsf(x), fmaxf(fabsf(y), fabsf(z))) * 0x1p-23f + 1e-37f;
     par[w] = -1;
     lvl[w] = 0;
   }
@@ -100,13 +158,14 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
   block_argmin(bk, bi, rk, ri, &wk, &wi);
   const int root = bi;
 
-  unsigned long long key[VPT];
-  float kf[VPT];  // an upper bound (round-up float) of key, for the FP32 skip test
+  const float kInf = __int_as_float(0x7f800000);
+  float klo[VPT], khi[VPT], skey[VPT];
   unsigned intree = 0;
 #pragma unroll
   for (int s = 0; s < VPT; ++s) {
-    key[s] = kInfBits;
-    kf[s] = __int_as_float(0x7f800000);
+    klo[s] = kInf;
+    khi[s] = kInf;
+    skey[s] = kInf;
     int w = tid + s * nt;
     if (w >= n || w == root) intree |= 1u << s;
   }
@@ -115,53 +174,114 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
     root_out[0] = root;
   }
 
+  Cand c = cand_identity();
+  bool dirty = true;  // this thread's summary must be rebuilt from its slots
   int u = root;
   for (int it = 1; it < n; ++it) {
-    const double xu = X[u], yu = Y[u], zu = Z[u];
-    const float xfu = xf[u], yfu = yf[u], zfu = zf[u];
+    const float xfu = xf[u], yfu = yf[u], zfu = zf[u], eu = ew[u];
     const float axu = fabsf(xfu), ayu = fabsf(yfu), azu = fabsf(zfu);
-    bk = ~0ull;
-    bi = INT_MAX;
 #pragma unroll
     for (int s = 0; s < VPT; ++s) {
       if (intree & (1u << s)) continue;
       const int w = tid + s * nt;
-      // Lower bound of |dx| from float copies: |x - fl(x)| <= 2^-24 |fl(x)| and the float
-      // subtraction errs by <= 2^-24 |dxf|; 2^-23 doubles that allowance to cover the
-      // rounding of the bound itself, 1e-37 covers subnormal coordinates.
       const float xw = xf[w], yw = yf[w], zw = zf[w];
       const float dxf = xfu - xw, dyf = yfu - yw, dzf = zfu - zw;
-      const float lx = fmaxf(fabsf(dxf) - (axu + fabsf(xw) + fabsf(dxf)) * 0x1p-23f - 1e-37f, 0.0f);
-      const float ly = fmaxf(fabsf(dyf) - (ayu + fabsf(yw) + fabsf(dyf)) * 0x1p-23f - 1e-37f, 0.0f);
-      const float lz = fmaxf(fabsf(dzf) - (azu + fabsf(zw) + fabsf(dzf)) * 0x1p-23f - 1e-37f, 0.0f);
-      // lx^2+ly^2+lz^2 in float is at most (1+2^-24)^3 too large; scaling by (1-2^-20)
-      // leaves a value below the true squared distance by more than the FP64 distance's
-      // own relative error (< 2^-50). So lbf >= kf >= key implies d_fp64 >= key.
-      const float lbf = ((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f);
-      if (lbf < kf[s]) {
-        const double dx = __dsub_rn(xu, X[w]), dy = __dsub_rn(yu, Y[w]), dz = __dsub_rn(zu, Z[w]);
-        const double d = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        if (d < __longlong_as_double((long long)key[s])) {
-          key[s] = key_bits(d);
-          kf[s] = __double2float_ru(d);
+      const float ax = fabsf(dxf), ay = fabsf(dyf), az = fabsf(dzf);
+      // Quick test on the largest coordinate difference a: |d_true| >= a - (a + max|u| +
+      // max|w|) 2^-24 (float copies round to nearest, the difference rounds once); the test
+      // subtracts a 2^-22 + (max|u| + max|w|) 2^-23, which also covers its own two roundings.
+      // skey >= sqrt(khi (1 + 2^-20)).
+      const float a = fmaxf(ax, fmaxf(ay, az));
+      if (fmaf(a, -0x1p-22f, a) - (eu + ew[w]) >= skey[s]) continue;
+      // Full float interval of d(u,w)^2. |x - fl(x)| <= 2^-24 |fl(x)| and the float
+      // difference errs by <= 2^-24 |dxf|; 2^-23 doubles that allowance, 1e-37 covers
+      // subnormal coordinates.
+      const float ex = (axu + fabsf(xw) + ax) * 0x1p-23f + 1e-37f;
+      const float ey = (ayu + fabsf(yw) + ay) * 0x1p-23f + 1e-37f;
+      const float ez = (azu + fabsf(zw) + az) * 0x1p-23f + 1e-37f;
+      const float lx = fmaxf(ax - ex, 0.0f), ly = fmaxf(ay - ey, 0.0f), lz = fmaxf(az - ez, 0.0f);
+      const float hx = ax + ex, hy = ay + ey, hz = az + ez;
+      // (1 -/+ 2^-20) absorbs the float roundings of the sums of squares and the FP64
+      // distance's own relative error (< 2^-50); hi is trusted only above 1e-30, where no
+      // square that matters can underflow.
+      const float lo = ((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f);
+      const float hi = ((hx * hx + hy * hy) + hz * hz) * (1.0f + 0x1p-20f);
+      if (hi < klo[s] && hi >= 1e-30f) {
+        klo[s] = lo;
+        khi[s] = hi;
+        skey[s] = __fsqrt_ru(__fmul_ru(hi, 1.0f + 0x1p-20f));
+        par[w] = u;
+        dirty = true;
+      } else if (!(lo >= khi[s])) {
+        const double xw64 = X[w], yw64 = Y[w], zw64 = Z[w];
+        const double d = exact_d2(X[u], Y[u], Z[u], xw64, yw64, zw64);
+        const int p = par[w];
+        const double key =
+            p >= 0 ? exact_d2(X[p], Y[p], Z[p], xw64, yw64, zw64) : __longlong_as_double(0x7ff0000000000000LL);
+        if (d < key) {
+          klo[s] = __double2float_rd(d);
+          khi[s] = __double2float_ru(d);
+          skey[s] = __fsqrt_ru(__fmul_ru(khi[s], 1.0f + 0x1p-20f));
           par[w] = u;
+          dirty = true;
         }
       }
-      argmin_combine(bk, bi, key[s], w);
     }
-    block_argmin(bk, bi, rk, ri, &wk, &wi);
-    const int nxt = bi;
+    if (dirty) {
+      c = cand_identity();
+#pragma unroll
+      for (int s = 0; s < VPT; ++s)
+        if (!(intree & (1u << s)))
+          cand_combine(c, Cand{__float_as_uint(khi[s]), tid + s * nt, __float_as_uint(klo[s]), tid + s * nt,
+                               0xffffffffu});
+      dirty = false;
+    }
+    // block reduction of the candidate summaries
+    Cand cw = c;
+    for (int o = 16; o > 0; o >>= 1) cand_combine(cw, cand_shfl_down(cw, o));
+    if (lane == 0) rc[warp] = cw;
+    __syncthreads();
+    if (warp == 0) {
+      cw = lane < nw ? rc[lane] : cand_identity();
+      for (int o = 16; o > 0; o >>= 1) cand_combine(cw, cand_shfl_down(cw, o));
+      if (lane == 0) wc = cw;
+    }
+    __syncthreads();
+    cw = wc;
+    int nxt;
+    if (cw.l1idx == cw.hidx && cw.l2 > cw.hk) {
+      nxt = cw.hidx;
+    } else {
+      // exact argmin over every vertex whose lower bound does not exceed the best upper bound
+      bk = ~0ull;
+      bi = INT_MAX;
+#pragma unroll
+      for (int s = 0; s < VPT; ++s) {
+        if (intree & (1u << s)) continue;
+        const int w = tid + s * nt;
+        if (__float_as_uint(klo[s]) <= cw.hk) {
+          const int p = par[w];
+          const double key = p >= 0 ? exact_d2(X[p], Y[p], Z[p], X[w], Y[w], Z[w])
+                                    : __longlong_as_double(0x7ff0000000000000LL);
+          argmin_combine(bk, bi, key_bits(key), w);
+        }
+      }
+      block_argmin(bk, bi, rk, ri, &wk, &wi);
+      nxt = bi;
+    }
     if (tid == nxt % nt) {
       intree |= 1u << (nxt / nt);
+      dirty = true;
       int p = par[nxt];
       if (p < 0) {  // only with non-finite positions
         p = root;
         par[nxt] = p;
       }
-      lvl[nxt] = lvl[p] + 1;
+      lvl[nxt] = (short)(lvl[p] + 1);
       order_out[it] = nxt;
     }
     u = nxt;
+    __syncthreads();
   }
   __syncthreads();
   for (int w = tid; w < n; w += nt) {
@@ -240,7 +360,7 @@ k_tree(int n, int npad, const int* __restrict__ parent, int* __restrict__ gp, in
 
 template <int VPT>
 cudaError_t run_prim(mstar_ctx* c, int nt) {
-  size_t smem = (size_t)c->n * (3 * sizeof(float) + 2 * sizeof(int));
+  size_t smem = (size_t)c->n * (4 * sizeof(float) + sizeof(int) + sizeof(short));
   cudaError_t e = cudaFuncSetAttribute(k_prim<VPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_prim<VPT><<<1, nt, smem, c->stream>>>(c->n, c->npad, c->d.r, c->d.parent, c->d.level, c->d.order,

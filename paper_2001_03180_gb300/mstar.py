@@ -274,11 +274,13 @@ class Integrator:
     def set_H(self, H):
         mstar_set_H(self.ctx, H)
 
-    def mst(self):
+    def mst(self, with_order=True):
+        """(root, parent, level, order); with_order=False returns the step builder's tree
+        and order None."""
         root = np.zeros(1, np.int32)
         parent = np.empty(self.n, np.int32)
         level = np.empty(self.n, np.int32)
-        order = np.empty(self.n, np.int32)
+        order = np.empty(self.n, np.int32) if with_order else None
         mstar_get_mst(self.ctx, root, parent, level, order)
         return int(root[0]), parent, level, order
 
