@@ -7,6 +7,10 @@
 // GB300. Near pairs are masked out of the tiles with integer compares on parent and
 // grandparent indices and summed in a sparse pass with the edge-vector separations.
 //
+// Per pair the FP64 pipe issues only the separation (3 DADD), the force-function term
+// (1 DFMA) and the two force accumulations (6 DFMA); r^2, 1/r, 1/r^3 and the mass products
+// run on the integer pipe (pair_scalars_int), which the FP64-bound loop leaves idle.
+//
 // Tiles: the N bodies form NT tiles of T = 32*W. CTA (I, J), I <= J, owns the I-tile as
 // "i" bodies (one per thread, accumulators in registers) and stages the J-tile ("j"
 // bodies) in shared memory together with their accumulators. Each warp sweeps the W
@@ -43,7 +47,8 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
              double* __restrict__ P) {
   constexpr int T = 32 * W;
   __shared__ double sx[T], sy[T], sz[T], sm[T], sax[T], say[T], saz[T];
-  __shared__ int sp[T], sg[T];
+  __shared__ unsigned long long smm[T];
+  __shared__ int sp[T], sg[T], sme[T];
 
   const int slot = slot_lo + blockIdx.y;
   int I, J;
@@ -57,13 +62,19 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
   sy[tid] = ry[j0 + tid];
   sz[tid] = rz[j0 + tid];
   sm[tid] = m[j0 + tid];
+  {
+    const MassSplit ms = mass_split(m[j0 + tid]);
+    smm[tid] = ms.m;
+    sme[tid] = ms.e;
+  }
   sp[tid] = parent[j0 + tid];
   sg[tid] = gp[j0 + tid];
   sax[tid] = 0.0;
   say[tid] = 0.0;
   saz[tid] = 0.0;
   const int i = I * T + tid;
-  const double xi = rx[i], yi = ry[i], zi = rz[i], mi = m[i];
+  const double xi = rx[i], yi = ry[i], zi = rz[i];
+  const MassSplit msi = mass_split(m[i]);
   const int pi = parent[i], gpi = gp[i];
   const bool i_pad = i >= n;
   const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
@@ -88,11 +99,11 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
         masked |= nd1 & ((pi == j) | (pj == i));
         masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
         const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
-        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        double rinv = rsqrt_fp64(r2);
+        double rinv, sj, si;
+        pair_scalars_int(dx, dy, dz, MassSplit{smm[jl], sme[jl]}, msi, rinv, sj, si);
         rinv = masked ? 0.0 : rinv;
-        const double rinv3 = (rinv * rinv) * rinv;
-        const double sj = mj * rinv3, si = mi * rinv3;
+        sj = masked ? 0.0 : sj;
+        si = masked ? 0.0 : si;
         axi = fma(sj, dx, axi);
         ayi = fma(sj, dy, ayi);
         azi = fma(sj, dz, azi);

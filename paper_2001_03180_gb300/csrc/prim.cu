@@ -21,8 +21,6 @@
 namespace mstar {
 namespace {
 
-constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-
 __device__ __forceinline__ void argmin_combine(unsigned long long& k, int& i, unsigned long long k2, int i2) {
   if (k2 < k || (k2 == k && i2 < i)) {
     k = k2;
