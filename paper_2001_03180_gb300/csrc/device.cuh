@@ -105,15 +105,20 @@ __device__ __forceinline__ unsigned long long sq_top(unsigned long long m, int s
   return sh < 64 ? (T >> sh) : 0ull;
 }
 
+// Significand (with the hidden bit; 0 for zero/subnormal) and biased exponent of |x|, built
+// from the two 32-bit halves so that no FP64 instruction is involved.
+__device__ __forceinline__ unsigned long long sig_of(double x, int& e) {
+  const unsigned hi = (unsigned)__double2hiint(x) & 0x7FFFFFFFu;
+  const unsigned lo = (unsigned)__double2loint(x);
+  e = (int)(hi >> 20);
+  const unsigned long long m = ((unsigned long long)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+  return e ? m : 0ull;
+}
+
 __device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz, const MassSplit& mj,
                                                  const MassSplit& mi, double& rinv, double& sj, double& si) {
-  const unsigned long long bx = (unsigned long long)__double_as_longlong(dx) & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long by = (unsigned long long)__double_as_longlong(dy) & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long bz = (unsigned long long)__double_as_longlong(dz) & 0x7FFFFFFFFFFFFFFFull;
-  const int ex = (int)(bx >> 52), ey = (int)(by >> 52), ez = (int)(bz >> 52);
-  const unsigned long long mx = ex ? ((bx & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-  const unsigned long long my = ey ? ((by & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
-  const unsigned long long mz = ez ? ((bz & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+  int ex, ey, ez;
+  const unsigned long long mx = sig_of(dx, ex), my = sig_of(dy, ey), mz = sig_of(dz, ez);
   const int E = max(ex, max(ey, ez));
   // r^2 = F * 2^(2E - 2106); each aligned square is below 2^62, so F < 2^64
   const unsigned long long F = sq_top(mx, 2 + 2 * (E - ex)) + sq_top(my, 2 + 2 * (E - ey)) + sq_top(mz, 2 + 2 * (E - ez));

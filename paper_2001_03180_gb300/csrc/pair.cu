@@ -98,19 +98,24 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
         bool masked = i_pad | (j >= n) | (self & (k == 16) & (lane >= 16));
         masked |= nd1 & ((pi == j) | (pj == i));
         masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
-        const double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+        double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+        // keep the separations in registers: recomputing them for the accumulations would
+        // cost three more FP64 instructions per pair
+        asm volatile("" : "+d"(dx), "+d"(dy), "+d"(dz));
         double rinv, sj, si;
         pair_scalars_int(dx, dy, dz, MassSplit{smm[jl], sme[jl]}, msi, rinv, sj, si);
-        rinv = masked ? 0.0 : rinv;
-        sj = masked ? 0.0 : sj;
-        si = masked ? 0.0 : si;
+        // masked pairs contribute nothing (integer selects on the bit patterns)
+        rinv = __longlong_as_double(masked ? 0ll : __double_as_longlong(rinv));
+        sj = __longlong_as_double(masked ? 0ll : __double_as_longlong(sj));
+        si = __longlong_as_double(masked ? 0ll : __double_as_longlong(si));
         axi = fma(sj, dx, axi);
         ayi = fma(sj, dy, ayi);
         azi = fma(sj, dz, azi);
         ui = fma(mj, rinv, ui);
-        sax[jl] = fma(-si, dx, sax[jl]);
-        say[jl] = fma(-si, dy, say[jl]);
-        saz[jl] = fma(-si, dz, saz[jl]);
+        // j-side sums are kept with the opposite sign and negated once when written
+        sax[jl] = fma(si, dx, sax[jl]);
+        say[jl] = fma(si, dy, say[jl]);
+        saz[jl] = fma(si, dz, saz[jl]);
         __syncwarp();
       }
     }
@@ -120,9 +125,9 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
   double* Ps = P + (size_t)slot * NT * 4 * npad;
   if (diag) {
     double* q = Ps + (size_t)I * 4 * npad + i;
-    q[0] = axi + sax[tid];
-    q[(size_t)npad] = ayi + say[tid];
-    q[2 * (size_t)npad] = azi + saz[tid];
+    q[0] = axi - sax[tid];
+    q[(size_t)npad] = ayi - say[tid];
+    q[2 * (size_t)npad] = azi - saz[tid];
     q[3 * (size_t)npad] = ui;
   } else {
     double* q = Ps + (size_t)J * 4 * npad + i;
@@ -131,9 +136,9 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
     q[2 * (size_t)npad] = azi;
     q[3 * (size_t)npad] = ui;
     double* qj = Ps + (size_t)I * 4 * npad + j0 + tid;
-    qj[0] = sax[tid];
-    qj[(size_t)npad] = say[tid];
-    qj[2 * (size_t)npad] = saz[tid];
+    qj[0] = -sax[tid];
+    qj[(size_t)npad] = -say[tid];
+    qj[2 * (size_t)npad] = -saz[tid];
     qj[3 * (size_t)npad] = 0.0;
   }
 }
