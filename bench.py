@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mstar", choices=["mstar", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     return ap.parse_args()
 
 
@@ -212,6 +213,54 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+BATCH_DESC = ("4096 independent systems (seed 3): even indices hierarchical triples (masses 1, 1, 0.1; inner a=1, "
+              "e~U[0,0.9]; outer a~U[10,50]; inclination~U[40,140] deg), odd indices Plummer clusters of "
+              "N~round(exp U[ln 3, ln 200]) bodies with a central mass of 0.1 of the cluster; eta_GBS=1e-12, k_fix=8")
+
+
+def run_batched(args, dev, M, W, torch):
+    """Batched subsystems: each launch gives every system one GBS step attempt (one CTA per
+    system). Throughput = accepted system steps per second over the timed launches; the
+    plain one-context-per-system path is timed beside it on a sample of the same systems."""
+    systems = W.batched_systems(4096, 3)
+    t_end = 1000.0  # no system gets there within the launches below: each launch is an attempt for all
+    b = M.Batch([(s.m, s.r, s.v) for s in systems], device=dev)
+    b.step(t_end, 40)  # step-size controllers settle from the first-step rule (halvings)
+    launches = 5 * max(args.steps, 1)
+    st0 = b.step(t_end, 0)
+    l0 = M.mstar_batch_launch_count(b.b)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(b.stream)
+    st1 = b.step(t_end, launches)
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    nl = M.mstar_batch_launch_count(b.b) - l0
+    b.close()
+    acc = st1["accepted"] - st0["accepted"]
+    att = acc + st1["rejected"] - st0["rejected"]
+    out = {"workload": BATCH_DESC, "systems": len(systems), "bodies": sum(len(s.m) for s in systems),
+           "launches": nl, "ms_per_launch": ms / launches, "system_steps_per_s": acc / (ms * 1e-3),
+           "system_attempts_per_s": att / (ms * 1e-3), "failed": st1["failed"]}
+    # the single-system path, one context per system, on every 128th system
+    secs = 0.0
+    steps = 0
+    for s in systems[::128]:
+        g = M.Integrator(s.m, s.r, s.v, device=dev)
+        g.step(t_end, 3)
+        torch.cuda.synchronize(dev)
+        w0 = time.perf_counter()
+        _, st = g.step(t_end, 5)
+        secs += time.perf_counter() - w0
+        steps += st["accepted"]
+        g.close()
+    out["single_context_system_steps_per_s"] = steps / secs
+    out["single_context_sample"] = "every 128th system (%d), 5 steps each, sequential" % len(systems[::128])
+    return out
+
+
 def run_mstar(args):
     import numpy as np
     import torch
@@ -335,6 +384,10 @@ def run_mstar(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(os.cpu_count() or 1)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        with torch.cuda.stream(stream):
+            batched = run_batched(args, dev, M, W, torch)
 
     if rank == 0:
         out = {"metric": "FP64 pair-forces/s", "value": value, "unit": "pair-forces/s", "n_gpus": world,
@@ -346,7 +399,7 @@ def run_mstar(args):
                           "parallelism": "replicas" if world > 1 else "single"},
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches, "clocks": clocks}
+               "gpu_launches": launches, "clocks": clocks, "batched": batched}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:

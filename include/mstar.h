@@ -164,6 +164,56 @@ MSTAR_API int mstar_profile_read(mstar_ctx* ctx, mstar_profile* out);
    Allocates and frees a small device buffer. */
 MSTAR_API int mstar_fp64_fma_rate(double* fma_per_second, void* cuda_stream);
 
+/* ---- Batched independent systems (Sec. 4.2: the parallel method extends to many
+   independent N-body systems integrated simultaneously). */
+
+/* Largest system of a batch (one CTA of 128 threads builds its MST in registers). */
+#define MSTAR_BATCH_MAX_N 512
+
+typedef struct mstar_batch mstar_batch;
+
+typedef struct {
+  long long accepted;    /* accepted GBS steps, summed over the systems */
+  long long rejected;    /* rejected attempts (each halved that system's H) */
+  long long force_evals; /* pair-loop evaluations */
+  int finished;          /* systems that reached t_end or stopped (status != 0) */
+  int failed;            /* systems stopped by an error (status < 0) */
+} mstar_batch_stats;
+
+/* Device bytes a batch needs (0 if the sizes or parameters are invalid). */
+MSTAR_API size_t mstar_batch_workspace_bytes(int nsys, const int* offsets, const mstar_params* p);
+
+/* Create a batch of nsys independent systems. offsets[nsys + 1] (host) is a CSR over the
+   concatenated bodies: system s owns bodies offsets[s] .. offsets[s+1]-1, each system has
+   2 .. MSTAR_BATCH_MAX_N bodies. m[nbody], r[nbody x 3], v[nbody x 3] (host or device) are
+   copied; each system is shifted to its own centre-of-mass frame and gets its own B = U - T,
+   time 0 and unset step. Workspace as for mstar_init (NULL: allocated by the library).
+   Errors: INVALID_ARG, NONFINITE, UNSUPPORTED (a system above MSTAR_BATCH_MAX_N or a
+   coordinate >= 1e15), NOMEM, CUDA. */
+MSTAR_API int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const double* m, const double* r,
+                               const double* v, const mstar_params* p, void* workspace, size_t workspace_bytes,
+                               void* cuda_stream);
+
+/* `launches` kernel launches; each advances every unfinished system by one GBS step
+   attempt towards t_end (accepted: the state and time advance and H grows by Eq. hnext;
+   rejected: H halves for the next launch; Sec. 2.3-2.4 as in mstar_step, per system).
+   A system stops at |t - t_end| <= t_tol |t_end|, after max_time_iter end-time-clamped
+   steps, or (status -3) after more than max_halvings successive rejections. Within a
+   launch each system is one CTA; its k_fix divisions are assigned to four warps by the
+   greedy longest-first recipe of Sec. 4.2. Synchronises the stream; out may be NULL. */
+MSTAR_API int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out);
+
+/* Per-system time t[nsys], state r, v (nbody x 3, host or device), last error eps[nsys]
+   and status[nsys] (0 running, 1 at t_end, 2 time-iteration limit, -3 no convergence). Any
+   output may be NULL. */
+MSTAR_API int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double* v, double* eps, int* status);
+
+/* Set every system's next fictitious step (host array H[nsys]; 0 = unset). */
+MSTAR_API int mstar_batch_set_H(mstar_batch* b, const double* H);
+
+MSTAR_API long long mstar_batch_launch_count(const mstar_batch* b);
+MSTAR_API void mstar_batch_free(mstar_batch* b);
+
 /* Largest n that mstar_accelerations_noalloc accepts. Its scratch is a fixed static device
    array of about 1.1 MB (positions, masses and the per-tile partial sums for 2048 bodies). */
 #define MSTAR_NOALLOC_MAX_N 2048

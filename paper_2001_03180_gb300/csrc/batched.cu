@@ -1,0 +1,917 @@
+// Batched GBS steps for many independent small systems (Sec. 4.2 notes the method extends to
+// integrating multiple independent N-body systems simultaneously).
+//
+// One launch advances every unfinished system by one GBS step attempt. Each system is one
+// CTA of four warps:
+//  - the whole CTA builds the system's MST (Prim, exact FP64 keys, Sec. 3.2 / 3.4), the
+//    edge coordinates and the derivative information of the step start;
+//  - the k_fix leapfrog divisions are spread over the warps with the paper's greedy recipe
+//    (largest n_k first, to the least-loaded group, lowest index on ties; Sec. 4.2), and
+//    each warp runs its divisions with warp-level synchronisation only;
+//  - the whole CTA then extrapolates (Aitken-Neville), evaluates the error of Eq.
+//    gbs-criterion and applies the step control of Sec. 2.3-2.4 for its system.
+// CTAs are issued largest system first so that the longest runs start early.
+//
+// The pair loop inside a warp uses the same symmetric rotation as the large-N kernel: lane
+// l owns body i of a 32-block and pairs with body (l + k) mod 32 of the partner block at
+// step k, so every unordered pair is visited once and the 32 partner accumulators are
+// updated by distinct lanes. Near pairs (N_d <= 2) are masked out and summed from edge
+// vectors afterwards, exactly as in the large-N path.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace mstar {
+namespace {
+
+constexpr int kBW = 4;            // warps per system CTA
+constexpr int kBThreads = 32 * kBW;
+constexpr int kBMaxN = 512;       // largest system of a batch
+constexpr int kBVpt = kBMaxN / kBThreads;
+
+// Per-system scalars in device memory.
+struct SysScalars {
+  double t, B, H, M, U0, T0, eps, t_end_reached;
+  long long accepted, rejected, force_evals;
+  int status;      // 0 running, 1 reached t_end, 2 time-iteration limit, -3 no convergence
+  int halvings, time_iters, pad;
+};
+
+// Per-body storage (doubles), offsets in units of bodies.
+enum : int {
+  B_R = 0, B_V = 3, B_X0 = 6, B_V0 = 9, B_A0 = 12, B_TKK = 15,
+  B_WARP = 21,                      // 4 warps x (X 3, V 3, r 3, v 3, a 3)
+  B_END = B_WARP + kBW * 15,        // k_fix division end states x (X 3, V 3)
+};
+constexpr int kBodyDoublesBase = B_END;  // + 6 * k_fix
+
+__constant__ double c_bfac[kMaxKfix][kMaxKfix];  // 1 / ((n_k / n_{k-j})^2 - 1)
+
+struct BatchParams {
+  double eta, a_gbs, fac_min, fac_max, q_first, t_tol, G;
+  int k_fix, n_d, max_halvings, max_time_iter;
+  int body_doubles;
+};
+
+struct WarpBuf {
+  double *X, *V, *r, *v, *a;  // 3-vectors per body, stride 3 (xyz)
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__device__ __forceinline__ double madd(double a, double f, double b) { return __dadd_rn(a, __dmul_rn(f, b)); }
+
+// Path sums from edge vectors (w_v = W_v + W_parent(v) + ...), then the COM shift; returns
+// sum m |w|^2 after the shift when want_T. Warp-level.
+__device__ double warp_rebuild(int n, const double* __restrict__ m, const int* __restrict__ parent,
+                               const double* W, double* w, double Mtot, bool want_T, int lane) {
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int u = v; parent[u] >= 0; u = parent[u]) {
+      s0 = __dadd_rn(s0, W[3 * u]);
+      s1 = __dadd_rn(s1, W[3 * u + 1]);
+      s2 = __dadd_rn(s2, W[3 * u + 2]);
+    }
+    w[3 * v] = s0;
+    w[3 * v + 1] = s1;
+    w[3 * v + 2] = s2;
+    c0 += __dmul_rn(m[v], s0);
+    c1 += __dmul_rn(m[v], s1);
+    c2 += __dmul_rn(m[v], s2);
+  }
+  c0 = warp_sum(c0) / Mtot;
+  c1 = warp_sum(c1) / Mtot;
+  c2 = warp_sum(c2) / Mtot;
+  double t2 = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    const double q0 = __dsub_rn(w[3 * v], c0), q1 = __dsub_rn(w[3 * v + 1], c1), q2 = __dsub_rn(w[3 * v + 2], c2);
+    w[3 * v] = q0;
+    w[3 * v + 1] = q1;
+    w[3 * v + 2] = q2;
+    if (want_T) t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+  }
+  __syncwarp();
+  return want_T ? warp_sum(t2) : 0.0;
+}
+
+// Pair loop of one system by one warp: a (3-vectors, times G) and U. sj_* in shared memory
+// hold one 32-block of partners and their accumulators.
+struct WarpShared {
+  double x[32], y[32], z[32], mm[32], ax[32], ay[32], az[32];
+  unsigned long long ms[32];
+  int me[32], p[32], g[32];
+};
+
+__device__ double warp_forces(int n, int n_d, double G, const double* __restrict__ m, const int* __restrict__ parent,
+                              const int* __restrict__ gp, const int* __restrict__ coff, const int* __restrict__ cidx,
+                              const double* r, const double* X, double* a, WarpShared& sh, int lane) {
+  for (int v = lane; v < n; v += 32) {
+    a[3 * v] = 0.0;
+    a[3 * v + 1] = 0.0;
+    a[3 * v + 2] = 0.0;
+  }
+  __syncwarp();
+  const int nb = (n + 31) >> 5;
+  const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
+  double usum = 0.0;
+  for (int I = 0; I < nb; ++I) {
+    const int i = I * 32 + lane;
+    const bool ipad = i >= n;
+    const double xi = ipad ? 0.0 : r[3 * i], yi = ipad ? 0.0 : r[3 * i + 1], zi = ipad ? 0.0 : r[3 * i + 2];
+    const MassSplit msi = mass_split(ipad ? 1.0 : m[i]);
+    const double mi = ipad ? 0.0 : m[i];
+    const int pi = ipad ? -3 : parent[i], gpi = ipad ? -3 : gp[i];
+    double axi = 0.0, ayi = 0.0, azi = 0.0, ui = 0.0;
+    for (int J = I; J < nb; ++J) {
+      const int jb = J * 32 + lane;
+      const bool jpad = jb >= n;
+      sh.x[lane] = jpad ? 0.0 : r[3 * jb];
+      sh.y[lane] = jpad ? 0.0 : r[3 * jb + 1];
+      sh.z[lane] = jpad ? 0.0 : r[3 * jb + 2];
+      sh.mm[lane] = jpad ? 0.0 : m[jb];
+      const MassSplit ms = mass_split(jpad ? 1.0 : m[jb]);
+      sh.ms[lane] = ms.m;
+      sh.me[lane] = ms.e;
+      sh.p[lane] = jpad ? -3 : parent[jb];
+      sh.g[lane] = jpad ? -3 : gp[jb];
+      sh.ax[lane] = 0.0;
+      sh.ay[lane] = 0.0;
+      sh.az[lane] = 0.0;
+      __syncwarp();
+      const bool self = (I == J);
+      const int kbeg = self ? 1 : 0, kend = self ? 17 : 32;
+      for (int k = kbeg; k < kend; ++k) {
+        const int jl = (lane + k) & 31;
+        const int j = J * 32 + jl;
+        bool masked = ipad | (j >= n) | (self & (k == 16) & (lane >= 16));
+        const int pj = sh.p[jl], gj = sh.g[jl];
+        masked |= nd1 & ((pi == j) | (pj == i));
+        masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
+        double dx = sh.x[jl] - xi, dy = sh.y[jl] - yi, dz = sh.z[jl] - zi;
+        asm volatile("" : "+d"(dx), "+d"(dy), "+d"(dz));
+        double rinv, sj, si;
+        if (!masked) {
+          pair_scalars_int(dx, dy, dz, MassSplit{sh.ms[jl], sh.me[jl]}, msi, rinv, sj, si);
+        } else {
+          rinv = sj = si = 0.0;
+        }
+        axi = fma(sj, dx, axi);
+        ayi = fma(sj, dy, ayi);
+        azi = fma(sj, dz, azi);
+        ui = fma(sh.mm[jl], rinv, ui);
+        sh.ax[jl] = fma(si, dx, sh.ax[jl]);
+        sh.ay[jl] = fma(si, dy, sh.ay[jl]);
+        sh.az[jl] = fma(si, dz, sh.az[jl]);
+        __syncwarp();
+      }
+      if (!jpad) {  // partner sums were kept with the opposite sign
+        a[3 * jb] -= sh.ax[lane];
+        a[3 * jb + 1] -= sh.ay[lane];
+        a[3 * jb + 2] -= sh.az[lane];
+      }
+      __syncwarp();
+    }
+    if (!ipad) {
+      a[3 * i] += axi;
+      a[3 * i + 1] += ayi;
+      a[3 * i + 2] += azi;
+    }
+    usum += mi * ui;
+    __syncwarp();
+  }
+  // near pairs from edge vectors: parent, children, grandparent, grandchildren, siblings
+  if (n_d >= 1) {
+    for (int p = lane; p < n; p += 32) {
+      double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
+      auto add = [&](int q, double dx, double dy, double dz) {
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        const double ri = rsqrt_fp64(r2);
+        const double s = m[q] * ((ri * ri) * ri);
+        ax = fma(s, dx, ax);
+        ay = fma(s, dy, ay);
+        az = fma(s, dz, az);
+        if (q > p) u = fma(m[q], ri, u);
+      };
+      const int pp = parent[p];
+      const double xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2];
+      if (pp >= 0) add(pp, -xp, -yp, -zp);
+      for (int c = coff[p]; c < coff[p + 1]; ++c) {
+        const int ch = cidx[c];
+        add(ch, X[3 * ch], X[3 * ch + 1], X[3 * ch + 2]);
+      }
+      if (n_d >= 2) {
+        const int g = gp[p];
+        if (g >= 0) add(g, -(xp + X[3 * pp]), -(yp + X[3 * pp + 1]), -(zp + X[3 * pp + 2]));
+        for (int c = coff[p]; c < coff[p + 1]; ++c) {
+          const int ch = cidx[c];
+          for (int e = coff[ch]; e < coff[ch + 1]; ++e) {
+            const int gc = cidx[e];
+            add(gc, X[3 * gc] + X[3 * ch], X[3 * gc + 1] + X[3 * ch + 1], X[3 * gc + 2] + X[3 * ch + 2]);
+          }
+        }
+        if (pp >= 0) {
+          for (int c = coff[pp]; c < coff[pp + 1]; ++c) {
+            const int sb = cidx[c];
+            if (sb != p) add(sb, X[3 * sb] - xp, X[3 * sb + 1] - yp, X[3 * sb + 2] - zp);
+          }
+        }
+      }
+      a[3 * p] += ax;
+      a[3 * p + 1] += ay;
+      a[3 * p + 2] += az;
+      usum += m[p] * u;
+    }
+  }
+  __syncwarp();
+  for (int v = lane; v < n; v += 32) {
+    a[3 * v] *= G;
+    a[3 * v + 1] *= G;
+    a[3 * v + 2] *= G;
+  }
+  __syncwarp();
+  return G * warp_sum(usum);
+}
+
+__device__ __forceinline__ void block_argmin(unsigned long long& k, int& i, unsigned long long* rk, int* ri) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_down_sync(0xffffffffu, k, o);
+    const int i2 = __shfl_down_sync(0xffffffffu, i, o);
+    if (k2 < k || (k2 == k && i2 < i)) {
+      k = k2;
+      i = i2;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    rk[warp] = k;
+    ri[warp] = i;
+  }
+  __syncthreads();
+  k = rk[0];
+  i = ri[0];
+  for (int w = 1; w < kBW; ++w)
+    if (rk[w] < k || (rk[w] == k && ri[w] < i)) {
+      k = rk[w];
+      i = ri[w];
+    }
+}
+
+__device__ __forceinline__ double d2x(const double* r, int u, int v) {
+  const double dx = __dsub_rn(r[3 * u], r[3 * v]), dy = __dsub_rn(r[3 * u + 1], r[3 * v + 1]),
+               dz = __dsub_rn(r[3 * u + 2], r[3 * v + 2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+__global__ void __launch_bounds__(kBThreads)
+k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ off, BatchParams P, double t_end,
+               const double* __restrict__ mass, double* __restrict__ body, int* __restrict__ ibody,
+               SysScalars* __restrict__ sys, double* __restrict__ tdiv) {
+  __shared__ WarpShared wsh[kBW];
+  __shared__ unsigned long long rk[kBW];
+  __shared__ int ri[kBW];
+  __shared__ int s_cnt[kBMaxN + 1];
+  __shared__ int s_lvl[kBMaxN];
+  __shared__ double s_red[kBW];
+  __shared__ double s_scal[4];  // U0, T0, H, abort flag
+  const int s = order[blockIdx.x];
+  SysScalars* S = sys + s;
+  if (S->status != 0) return;
+  const int o = off[s], n = off[s + 1] - o;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = P.k_fix;
+  const double* m = mass + o;
+  double* bd = body + (size_t)o * P.body_doubles;
+  // body-major blocks of 3-vectors: field f of body v at bd[f * 3 * n + 3 v + c]
+  auto F = [&](int field) { return bd + (size_t)field * n; };
+  double* R = F(B_R);
+  double* Vs = F(B_V);
+  double* X0 = F(B_X0);
+  double* V0 = F(B_V0);
+  double* A0 = F(B_A0);
+  double* TKK = F(B_TKK);
+  int* ib = ibody + (size_t)o * 5;
+  int* parent = ib;
+  int* gp = ib + n;
+  int* coff = ib + 2 * n;       // n + 1 entries (uses the level slot's first entry too)
+  int* cidx = ib + 3 * n + 1;   // n - 1 entries
+  const double t0 = S->t, B = S->B, Mtot = S->M;
+
+  // ---- MST (Prim with exact FP64 keys, one CTA) and the children lists
+  unsigned long long key[kBVpt];
+  bool intree[kBVpt];
+  {
+    unsigned long long bk = ~0ull;
+    int bi = INT_MAX;
+    for (int q = 0; q < kBVpt; ++q) {
+      const int v = tid + q * kBThreads;
+      intree[q] = v >= n;
+      key[q] = 0x7ff0000000000000ull;
+      if (v < n) {
+        const double x = R[3 * v], y = R[3 * v + 1], z = R[3 * v + 2];
+        const unsigned long long d = key_bits(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+        if (d < bk) {
+          bk = d;
+          bi = v;
+        }
+        parent[v] = -1;
+        s_lvl[v] = 0;
+      }
+    }
+    block_argmin(bk, bi, rk, ri);
+    const int root = bi;
+    for (int q = 0; q < kBVpt; ++q)
+      if (tid + q * kBThreads == root) intree[q] = true;
+    int u = root;
+    for (int it = 1; it < n; ++it) {
+      bk = ~0ull;
+      bi = INT_MAX;
+      for (int q = 0; q < kBVpt; ++q) {
+        if (intree[q]) continue;
+        const int v = tid + q * kBThreads;
+        const double d = d2x(R, u, v);
+        if (d < __longlong_as_double((long long)key[q])) {
+          key[q] = key_bits(d);
+          parent[v] = u;
+        }
+        if (key[q] < bk) {
+          bk = key[q];
+          bi = v;
+        }
+      }
+      block_argmin(bk, bi, rk, ri);
+      const int nxt = bi;
+      if ((nxt % kBThreads) == tid) {
+        intree[nxt / kBThreads] = true;
+        int p = parent[nxt];
+        if (p < 0) {
+          p = root;
+          parent[nxt] = p;
+        }
+        s_lvl[nxt] = s_lvl[p] + 1;
+      }
+      u = nxt;
+    }
+    __syncthreads();
+    // grandparents and children CSR (ascending child index)
+    for (int v = tid; v <= n; v += kBThreads) s_cnt[v] = 0;
+    __syncthreads();
+    for (int v = tid; v < n; v += kBThreads) {
+      const int p = parent[v];
+      gp[v] = p >= 0 ? parent[p] : -1;
+      if (p >= 0) atomicAdd(&s_cnt[p], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int v = 0; v < n; ++v) {
+        const int c = s_cnt[v];
+        coff[v] = acc;
+        s_cnt[v] = acc;
+        acc += c;
+      }
+      coff[n] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {  // n <= 512: a sequential fill keeps every list in ascending order
+      for (int v = 0; v < n; ++v) {
+        const int p = parent[v];
+        if (p >= 0) cidx[s_cnt[p]++] = v;
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- edge coordinates of the step start, T0, and the derivative information (warp 0)
+  for (int v = tid; v < n; v += kBThreads) {
+    const int p = parent[v];
+    for (int c = 0; c < 3; ++c) {
+      X0[3 * v + c] = p >= 0 ? __dsub_rn(R[3 * v + c], R[3 * p + c]) : 0.0;
+      V0[3 * v + c] = p >= 0 ? __dsub_rn(Vs[3 * v + c], Vs[3 * p + c]) : 0.0;
+    }
+  }
+  __syncthreads();
+  {
+    WarpBuf wb{F(B_WARP + warp * 15), F(B_WARP + warp * 15 + 3), F(B_WARP + warp * 15 + 6),
+               F(B_WARP + warp * 15 + 9), F(B_WARP + warp * 15 + 12)};
+    if (warp == 0) {
+      const double U0 = warp_forces(n, P.n_d, P.G, m, parent, gp, coff, cidx, R, X0, wb.a, wsh[0], lane);
+      double t2 = 0.0;
+      for (int v = lane; v < n; v += 32) {
+        const double q0 = Vs[3 * v], q1 = Vs[3 * v + 1], q2 = Vs[3 * v + 2];
+        t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+        const int p = parent[v];
+        for (int c = 0; c < 3; ++c) A0[3 * v + c] = p >= 0 ? __dsub_rn(wb.a[3 * v + c], wb.a[3 * p + c]) : 0.0;
+      }
+      const double T0 = 0.5 * warp_sum(t2);
+      if (lane == 0) {
+        // Sec. 2.4: first step ds = q U dt; then the controller's step, clamped to t_end
+        const double dt = t_end - t0;
+        double abort_ = 0.0;
+        double Hs = 0.0;
+        if (fabs(dt) <= P.t_tol * fabs(t_end)) {
+          S->status = 1;
+          abort_ = 1.0;
+        } else {
+          Hs = (S->H == 0.0) ? P.q_first * U0 * dt : fabs(S->H) * (dt < 0 ? -1.0 : 1.0);
+          if (fabs(Hs / U0) >= fabs(dt)) {
+            Hs = U0 * dt;
+            if (S->halvings == 0) {
+              if (S->time_iters >= P.max_time_iter) {
+                S->status = 2;
+                abort_ = 1.0;
+              } else {
+                S->time_iters++;
+              }
+            }
+          }
+        }
+        s_scal[0] = U0;
+        s_scal[1] = T0;
+        s_scal[2] = Hs;
+        s_scal[3] = abort_;
+        S->U0 = U0;
+        S->T0 = T0;
+      }
+    }
+    __syncthreads();
+    if (s_scal[3] != 0.0) return;
+    const double T0 = s_scal[1], H = s_scal[2];
+
+    // ---- this warp's divisions (greedy longest-first assignment to kBW groups)
+    int load[kBW] = {0, 0, 0, 0};
+    for (int k = K; k >= 1; --k) {
+      int gsel = 0;
+      for (int w = 1; w < kBW; ++w)
+        if (load[w] < load[gsel]) gsel = w;
+      load[gsel] += 2 * k;
+      if (gsel != warp) continue;
+      const int nk = 2 * k;
+      const double delta = H / (double)nk;
+      double f = (0.5 * delta) / (T0 + B);
+      for (int v = lane; v < n; v += 32)
+        for (int c = 0; c < 3; ++c) {
+          wb.X[3 * v + c] = madd(X0[3 * v + c], f, V0[3 * v + c]);
+          wb.V[3 * v + c] = V0[3 * v + c];
+        }
+      double t = t0 + f;
+      __syncwarp();
+      warp_rebuild(n, m, parent, wb.X, wb.r, Mtot, false, lane);
+      for (int tau = 1; tau <= nk; ++tau) {
+        const double U = warp_forces(n, P.n_d, P.G, m, parent, gp, coff, cidx, wb.r, wb.X, wb.a, wsh[warp], lane);
+        const double fk = delta / U;
+        for (int v = lane; v < n; v += 32) {
+          const int p = parent[v];
+          if (p >= 0)
+            for (int c = 0; c < 3; ++c) wb.V[3 * v + c] = madd(wb.V[3 * v + c], fk, __dsub_rn(wb.a[3 * v + c], wb.a[3 * p + c]));
+        }
+        __syncwarp();
+        const double T = 0.5 * warp_rebuild(n, m, parent, wb.V, wb.v, Mtot, true, lane);
+        f = ((tau == nk) ? 0.5 * delta : delta) / (T + B);
+        for (int v = lane; v < n; v += 32)
+          for (int c = 0; c < 3; ++c) wb.X[3 * v + c] = madd(wb.X[3 * v + c], f, wb.V[3 * v + c]);
+        t += f;
+        __syncwarp();
+        if (tau < nk) warp_rebuild(n, m, parent, wb.X, wb.r, Mtot, false, lane);
+      }
+      double* E = F(B_END + 6 * (k - 1));
+      for (int v = lane; v < n; v += 32)
+        for (int c = 0; c < 3; ++c) {
+          E[3 * v + c] = wb.X[3 * v + c];
+          E[3 * n + 3 * v + c] = wb.V[3 * v + c];
+        }
+      if (lane == 0) tdiv[(size_t)s * kMaxKfix + (k - 1)] = t;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+
+  // ---- Aitken-Neville extrapolation and the error of Eq. gbs-criterion
+  const double H = s_scal[2], T0 = s_scal[1], U0 = s_scal[0];
+  const double rate = 1.0 / (T0 + B), delta = H / (double)(2 * K);
+  auto neville = [&](const double* Sv, double& tkk, double& tprev) {
+    double prev[kMaxKfix], cur[kMaxKfix];
+    for (int k = 0; k < K; ++k) {
+      cur[0] = Sv[k];
+      for (int j = 1; j <= k; ++j) cur[j] = fma(__dsub_rn(cur[j - 1], prev[j - 1]), c_bfac[k][j], cur[j - 1]);
+      if (k == K - 2) tprev = cur[k];
+      for (int j = 0; j <= k; ++j) prev[j] = cur[j];
+    }
+    tkk = prev[K - 1];
+  };
+  double e = 0.0;
+  for (int v = tid; v < n; v += kBThreads) {
+    double Sv[kMaxKfix], dX[3], dV[3];
+    for (int c = 0; c < 3; ++c) {
+      double tkk, tp = 0.0;
+      for (int k = 0; k < K; ++k) Sv[k] = F(B_END + 6 * k)[3 * v + c];
+      neville(Sv, tkk, tp);
+      TKK[3 * v + c] = tkk;
+      dX[c] = __dsub_rn(tkk, tp);
+      for (int k = 0; k < K; ++k) Sv[k] = F(B_END + 6 * k)[3 * n + 3 * v + c];
+      neville(Sv, tkk, tp);
+      TKK[3 * n + 3 * v + c] = tkk;
+      dV[c] = __dsub_rn(tkk, tp);
+    }
+    if (parent[v] >= 0) {
+      double q[3], g[3];
+      for (int c = 0; c < 3; ++c) {
+        q[c] = madd(X0[3 * v + c], delta, __dmul_rn(V0[3 * v + c], rate));
+        g[c] = madd(V0[3 * v + c], delta, A0[3 * v + c] / U0);
+      }
+      auto nrm = [](const double* w) {
+        return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(w[0], w[0]), __dmul_rn(w[1], w[1])), __dmul_rn(w[2], w[2])));
+      };
+      e = nanmax(e, nanmax(nrm(dX) / fmax(nrm(q), 1e-300), nrm(dV) / fmax(nrm(g), 1e-300)));
+    }
+  }
+  double tkk_t = 0.0;
+  if (tid == 0) {
+    double Sv[kMaxKfix], tp = 0.0;
+    for (int k = 0; k < K; ++k) Sv[k] = tdiv[(size_t)s * kMaxKfix + k];
+    neville(Sv, tkk_t, tp);
+    e = nanmax(e, fabs(__dsub_rn(tkk_t, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300));
+  }
+  for (int o2 = 16; o2 > 0; o2 >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o2));
+  if (lane == 0) s_red[warp] = e;
+  __syncthreads();
+  if (tid == 0) {
+    double eps = s_red[0];
+    for (int w = 1; w < kBW; ++w) eps = nanmax(eps, s_red[w]);
+    S->eps = eps;
+    S->force_evals += 2 * K * (K + 1) / 2 + 1;
+    if (eps <= P.eta) {
+      double fc = (eps > 0.0) ? P.a_gbs * pow(P.eta / eps, 1.0 / (2 * K - 1)) : P.fac_max;
+      fc = fmin(fmax(fc, P.fac_min), P.fac_max);
+      S->H = fc * H;
+      S->t = tkk_t;
+      S->accepted++;
+      S->halvings = 0;
+      s_scal[3] = 1.0;
+    } else {
+      S->rejected++;
+      S->H = 0.5 * H;
+      if (++S->halvings > P.max_halvings) S->status = -3;
+      s_scal[3] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (s_scal[3] == 0.0) return;
+  // ---- accept: deconstruct the extrapolated edge vectors into the Cartesian state
+  if (warp < 2) {
+    double* dst = warp == 0 ? R : Vs;
+    const double* src = warp == 0 ? TKK : TKK + 3 * n;
+    warp_rebuild(n, m, parent, src, dst, Mtot, false, lane);
+  }
+}
+
+// Initial COM shift, B = U - T and M per system (one CTA each).
+__global__ void __launch_bounds__(kBThreads)
+k_batched_init(int nsys, const int* __restrict__ off, BatchParams P, const double* __restrict__ mass,
+               double* __restrict__ body, int* __restrict__ ibody, SysScalars* __restrict__ sys) {
+  __shared__ WarpShared wsh;
+  const int s = blockIdx.x;
+  const int o = off[s], n = off[s + 1] - o;
+  const int tid = threadIdx.x;
+  const double* m = mass + o;
+  double* bd = body + (size_t)o * P.body_doubles;
+  double* R = bd + (size_t)B_R * n;
+  double* Vs = bd + (size_t)B_V * n;
+  if (tid >= 32) return;
+  const int lane = tid;
+  double M = 0.0;
+  if (lane == 0)
+    for (int v = 0; v < n; ++v) M += m[v];
+  M = __shfl_sync(0xffffffffu, M, 0);
+  for (int w = 0; w < 2; ++w) {
+    double* q = w == 0 ? R : Vs;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+    for (int v = lane; v < n; v += 32) {
+      c0 += __dmul_rn(m[v], q[3 * v]);
+      c1 += __dmul_rn(m[v], q[3 * v + 1]);
+      c2 += __dmul_rn(m[v], q[3 * v + 2]);
+    }
+    c0 = warp_sum(c0) / M;
+    c1 = warp_sum(c1) / M;
+    c2 = warp_sum(c2) / M;
+    for (int v = lane; v < n; v += 32) {
+      q[3 * v] = __dsub_rn(q[3 * v], c0);
+      q[3 * v + 1] = __dsub_rn(q[3 * v + 1], c1);
+      q[3 * v + 2] = __dsub_rn(q[3 * v + 2], c2);
+    }
+    __syncwarp();
+  }
+  // U with every pair Cartesian (Eq. 1), T
+  int* ib = ibody + (size_t)o * 5;
+  double* a = bd + (size_t)B_WARP * n;
+  const double U = warp_forces(n, 0, P.G, m, ib, ib + n, ib + 2 * n, ib + 3 * n + 1, R, R, a, wsh, lane);
+  double t2 = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    const double q0 = Vs[3 * v], q1 = Vs[3 * v + 1], q2 = Vs[3 * v + 2];
+    t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+  }
+  const double T = 0.5 * warp_sum(t2);
+  if (lane == 0) {
+    SysScalars& S = sys[s];
+    S.M = M;
+    S.B = U - T;
+  }
+}
+
+}  // namespace
+}  // namespace mstar
+
+using mstar::SysScalars;
+using mstar::BatchParams;
+using mstar::kBodyDoublesBase;
+using mstar::kMaxKfix;
+using mstar::kBMaxN;
+using mstar::kBThreads;
+using mstar::B_R;
+using mstar::B_V;
+
+struct mstar_batch {
+  int nsys = 0, nbody = 0;
+  mstar_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_ws = false;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int *off = nullptr, *order = nullptr, *ibody = nullptr;
+  double *mass = nullptr, *body = nullptr, *tdiv = nullptr, *stage = nullptr;
+  SysScalars* sys = nullptr;
+  BatchParams bp{};
+  std::vector<int> off_h;
+  long long launches = 0;
+};
+
+namespace mstar_batch_detail {
+
+struct BCarve {
+  char* base;
+  size_t off = 0;
+  explicit BCarve(void* b) : base(static_cast<char*>(b)) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+size_t bcarve(int nsys, int nbody, int K, void* base, mstar_batch* b) {
+  BCarve c(base);
+  const int bdbl = kBodyDoublesBase + 6 * K;
+  int* off = c.take<int>(nsys + 1);
+  int* order = c.take<int>(nsys);
+  int* ibody = c.take<int>((size_t)nbody * 5);
+  double* mass = c.take<double>(nbody);
+  double* body = c.take<double>((size_t)nbody * bdbl);
+  double* tdiv = c.take<double>((size_t)nsys * kMaxKfix);
+  double* stage = c.take<double>((size_t)nbody * 3);
+  SysScalars* sys = c.take<SysScalars>(nsys);
+  if (b) {
+    b->off = off;
+    b->order = order;
+    b->ibody = ibody;
+    b->mass = mass;
+    b->body = body;
+    b->tdiv = tdiv;
+    b->stage = stage;
+    b->sys = sys;
+  }
+  return (c.off + 255) & ~size_t(255);
+}
+
+bool batch_sizes_ok(int nsys, const int* off, int* nbody) {
+  if (nsys < 1 || !off || off[0] != 0) return false;
+  for (int s = 0; s < nsys; ++s) {
+    const int n = off[s + 1] - off[s];
+    if (n < 2 || n > kBMaxN) return false;
+  }
+  *nbody = off[nsys];
+  return true;
+}
+
+__global__ void k_scatter_vec(int nbody, const int* __restrict__ off, int nsys, int bdbl, int field,
+                              const double* __restrict__ src, double* __restrict__ body, int to_body) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nbody) return;
+  int lo = 0, hi = nsys;  // system of body i
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid;
+  }
+  const int o = off[lo], n = off[lo + 1] - o, v = i - o;
+  double* dst = body + (size_t)o * bdbl + (size_t)field * n + 3 * v;
+  for (int c = 0; c < 3; ++c) {
+    if (to_body) dst[c] = src[3 * (size_t)i + c];
+    else const_cast<double*>(src)[3 * (size_t)i + c] = dst[c];
+  }
+}
+
+}  // namespace mstar_batch_detail
+
+using namespace mstar_batch_detail;
+
+extern "C" {
+
+size_t mstar_batch_workspace_bytes(int nsys, const int* offsets, const mstar_params* p) {
+  mstar_params d;
+  if (!p) {
+    mstar_default_params(&d);
+    p = &d;
+  }
+  int nbody = 0;
+  if (!batch_sizes_ok(nsys, offsets, &nbody) || p->k_fix < 2 || p->k_fix > kMaxKfix) return 0;
+  return bcarve(nsys, nbody, p->k_fix, nullptr, nullptr);
+}
+
+void mstar_batch_free(mstar_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->own_ws && b->ws) cudaFree(b->ws);
+  delete b;
+}
+
+int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const double* m, const double* r,
+                     const double* v, const mstar_params* p, void* workspace, size_t workspace_bytes,
+                     void* cuda_stream) {
+  if (!out) return MSTAR_ERR_INVALID_ARG;
+  *out = nullptr;
+  mstar_params pd;
+  if (!p) {
+    mstar_default_params(&pd);
+    p = &pd;
+  }
+  int nbody = 0;
+  if (!offsets || !m || !r || !v) return MSTAR_ERR_INVALID_ARG;
+  if (nsys < 1 || offsets[0] != 0) return MSTAR_ERR_INVALID_ARG;
+  for (int s = 0; s < nsys; ++s)
+    if (offsets[s + 1] - offsets[s] > kBMaxN) return MSTAR_ERR_UNSUPPORTED;
+  if (!batch_sizes_ok(nsys, offsets, &nbody)) return MSTAR_ERR_INVALID_ARG;
+  if (p->k_fix < 2 || p->k_fix > kMaxKfix || p->n_d < 0 || p->n_d > 2 || !(p->eta_gbs > 0.0) ||
+      !(p->G > 0.0) || !(p->a_gbs > 0.0 && p->a_gbs <= 1.0) || !(p->fac_min > 0.0 && p->fac_min <= p->fac_max))
+    return MSTAR_ERR_INVALID_ARG;
+  mstar_batch* b = new (std::nothrow) mstar_batch();
+  if (!b) return MSTAR_ERR_NOMEM;
+  b->nsys = nsys;
+  b->nbody = nbody;
+  b->p = *p;
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  const size_t need = bcarve(nsys, nbody, p->k_fix, nullptr, nullptr);
+  if (workspace) {
+    if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+      delete b;
+      return MSTAR_ERR_NOMEM;
+    }
+    b->ws = workspace;
+  } else {
+    if (cudaMalloc(&b->ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete b;
+      return MSTAR_ERR_NOMEM;
+    }
+    b->own_ws = true;
+  }
+  b->ws_bytes = need;
+  bcarve(nsys, nbody, p->k_fix, b->ws, b);
+  b->bp = BatchParams{p->eta_gbs, p->a_gbs, p->fac_min, p->fac_max, p->q_first, p->t_tol, p->G,
+                      p->k_fix, p->n_d, p->max_halvings, p->max_time_iter, kBodyDoublesBase + 6 * p->k_fix};
+  b->off_h.assign(offsets, offsets + nsys + 1);
+  // systems in decreasing order of pair work, so the longest CTAs start first
+  std::vector<int> ord(nsys);
+  for (int s = 0; s < nsys; ++s) ord[s] = s;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
+    const long long na = offsets[a + 1] - offsets[a], nc = offsets[c + 1] - offsets[c];
+    return na * na > nc * nc;
+  });
+  // host-side validation of the inputs (copied to the host when they live on the device)
+  std::vector<double> mh(nbody), rh(3 * (size_t)nbody), vh(3 * (size_t)nbody);
+  auto fetch = [&](double* dst, const double* src, size_t count) {
+    return cudaMemcpy(dst, src, sizeof(double) * count, cudaMemcpyDefault) == cudaSuccess;
+  };
+  if (!fetch(mh.data(), m, nbody) || !fetch(rh.data(), r, 3 * (size_t)nbody) || !fetch(vh.data(), v, 3 * (size_t)nbody)) {
+    mstar_batch_free(b);
+    return MSTAR_ERR_CUDA;
+  }
+  for (int i = 0; i < nbody; ++i) {
+    if (!std::isfinite(mh[i])) { mstar_batch_free(b); return MSTAR_ERR_NONFINITE; }
+    if (!(mh[i] > 0.0)) { mstar_batch_free(b); return MSTAR_ERR_INVALID_ARG; }
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(rh[3 * i + c]) || !std::isfinite(vh[3 * i + c])) { mstar_batch_free(b); return MSTAR_ERR_NONFINITE; }
+      if (std::fabs(rh[3 * i + c]) >= 1e15) { mstar_batch_free(b); return MSTAR_ERR_UNSUPPORTED; }
+    }
+  }
+  cudaStream_t st = b->stream;
+  double fac[kMaxKfix][kMaxKfix] = {};
+  for (int k = 0; k < p->k_fix; ++k)
+    for (int j = 1; j <= k; ++j) {
+      const double ratio = (double)(2 * (k + 1)) / (double)(2 * (k - j + 1));
+      fac[k][j] = 1.0 / (ratio * ratio - 1.0);
+    }
+  bool ok = cudaMemcpyToSymbol(mstar::c_bfac, fac, sizeof(fac)) == cudaSuccess &&
+            cudaMemsetAsync(b->ws, 0, need, st) == cudaSuccess &&
+            cudaMemcpyAsync(b->off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(b->mass, mh.data(), sizeof(double) * nbody, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+            cudaMemcpyAsync(b->stage, rh.data(), sizeof(double) * 3 * nbody, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  const int nb = (nbody + 255) / 256;
+  if (ok) {
+    k_scatter_vec<<<nb, 256, 0, st>>>(nbody, b->off, nsys, b->bp.body_doubles, B_R, b->stage, b->body, 1);
+    ok = cudaMemcpyAsync(b->stage, vh.data(), sizeof(double) * 3 * nbody, cudaMemcpyHostToDevice, st) == cudaSuccess;
+  }
+  if (ok) {
+    k_scatter_vec<<<nb, 256, 0, st>>>(nbody, b->off, nsys, b->bp.body_doubles, B_V, b->stage, b->body, 1);
+    mstar::k_batched_init<<<nsys, kBThreads, 0, st>>>(nsys, b->off, b->bp, b->mass, b->body, b->ibody, b->sys);
+    b->launches += 3;
+    ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+  }
+  if (!ok) {
+    mstar_batch_free(b);
+    return MSTAR_ERR_CUDA;
+  }
+  *out = b;
+  return MSTAR_OK;
+}
+
+int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out) {
+  if (!b || !std::isfinite(t_end) || launches < 0) return MSTAR_ERR_INVALID_ARG;
+  for (int l = 0; l < launches; ++l) {
+    mstar::k_batched_step<<<b->nsys, kBThreads, 0, b->stream>>>(b->nsys, b->order, b->off, b->bp, t_end, b->mass, b->body,
+                                                          b->ibody, b->sys, b->tdiv);
+    b->launches++;
+  }
+  if (cudaGetLastError() != cudaSuccess) return MSTAR_ERR_CUDA;
+  if (out) {
+    std::vector<SysScalars> h(b->nsys);
+    if (cudaMemcpyAsync(h.data(), b->sys, sizeof(SysScalars) * b->nsys, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+      return MSTAR_ERR_CUDA;
+    mstar_batch_stats st{};
+    for (const auto& s : h) {
+      st.accepted += s.accepted;
+      st.rejected += s.rejected;
+      st.force_evals += s.force_evals;
+      if (s.status != 0) st.finished++;
+      if (s.status < 0) st.failed++;
+    }
+    *out = st;
+  } else if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    return MSTAR_ERR_CUDA;
+  }
+  return MSTAR_OK;
+}
+
+int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double* v, double* eps, int* status) {
+  if (!b) return MSTAR_ERR_INVALID_ARG;
+  std::vector<SysScalars> h(b->nsys);
+  if (cudaMemcpyAsync(h.data(), b->sys, sizeof(SysScalars) * b->nsys, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
+    return MSTAR_ERR_CUDA;
+  const int nb = (b->nbody + 255) / 256;
+  std::vector<double> tmp(3 * (size_t)b->nbody);
+  for (int w = 0; w < 2; ++w) {
+    double* dst = w == 0 ? r : v;
+    if (!dst) continue;
+    k_scatter_vec<<<nb, 256, 0, b->stream>>>(b->nbody, b->off, b->nsys, b->bp.body_doubles, w == 0 ? B_R : B_V,
+                                             b->stage, b->body, 0);
+    b->launches++;
+    if (cudaMemcpyAsync(dst, b->stage, sizeof(double) * 3 * b->nbody, cudaMemcpyDefault, b->stream) != cudaSuccess)
+      return MSTAR_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  for (int s = 0; s < b->nsys; ++s) {
+    if (t) t[s] = h[s].t;
+    if (eps) eps[s] = h[s].eps;
+    if (status) status[s] = h[s].status;
+  }
+  return MSTAR_OK;
+}
+
+int mstar_batch_set_H(mstar_batch* b, const double* H) {
+  if (!b || !H) return MSTAR_ERR_INVALID_ARG;
+  std::vector<SysScalars> h(b->nsys);
+  if (cudaMemcpyAsync(h.data(), b->sys, sizeof(SysScalars) * b->nsys, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return MSTAR_ERR_CUDA;
+  for (int s = 0; s < b->nsys; ++s) h[s].H = H[s];
+  if (cudaMemcpyAsync(b->sys, h.data(), sizeof(SysScalars) * b->nsys, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return MSTAR_ERR_CUDA;
+  return MSTAR_OK;
+}
+
+long long mstar_batch_launch_count(const mstar_batch* b) { return b ? b->launches : 0; }
+
+}  // extern "C"

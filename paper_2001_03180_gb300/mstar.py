@@ -30,7 +30,10 @@ EXPORTS = [
     "mstar_energy", "mstar_get_state", "mstar_set_state", "mstar_set_H", "mstar_get_mst",
     "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
     "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate", "mstar_accelerations_noalloc",
+    "mstar_batch_workspace_bytes", "mstar_batch_init", "mstar_step_batched", "mstar_batch_get_state",
+    "mstar_batch_set_H", "mstar_batch_launch_count", "mstar_batch_free",
 ]
+MSTAR_BATCH_MAX_N = 512
 MSTAR_NOALLOC_MAX_N = 2048
 
 
@@ -45,6 +48,11 @@ class mstar_stats(C.Structure):
     _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("force_evals", C.c_longlong),
                 ("time_iters", C.c_longlong), ("eps_last", C.c_double), ("H", C.c_double),
                 ("t", C.c_double)]
+
+
+class mstar_batch_stats(C.Structure):
+    _fields_ = [("accepted", C.c_longlong), ("rejected", C.c_longlong), ("force_evals", C.c_longlong),
+                ("finished", C.c_int), ("failed", C.c_int)]
 
 
 class mstar_profile(C.Structure):
@@ -93,6 +101,16 @@ def load():
     L.mstar_profile_read.argtypes = [vp, C.POINTER(mstar_profile)]
     L.mstar_fp64_fma_rate.argtypes = [C.POINTER(C.c_double), vp]
     L.mstar_accelerations_noalloc.argtypes = [C.c_int, dp, dp, C.c_double, dp, dp, vp]
+    L.mstar_batch_workspace_bytes.argtypes = [C.c_int, ip, C.POINTER(mstar_params)]
+    L.mstar_batch_workspace_bytes.restype = C.c_size_t
+    L.mstar_batch_init.argtypes = [C.POINTER(vp), C.c_int, ip, dp, dp, dp, C.POINTER(mstar_params), vp, C.c_size_t, vp]
+    L.mstar_step_batched.argtypes = [vp, C.c_double, C.c_int, C.POINTER(mstar_batch_stats)]
+    L.mstar_batch_get_state.argtypes = [vp, dp, dp, dp, dp, ip]
+    L.mstar_batch_set_H.argtypes = [vp, dp]
+    L.mstar_batch_launch_count.argtypes = [vp]
+    L.mstar_batch_launch_count.restype = C.c_longlong
+    L.mstar_batch_free.argtypes = [vp]
+    L.mstar_batch_free.restype = None
     _lib = L
     return L
 
@@ -103,6 +121,10 @@ def _ptr(x):
         return None
     if isinstance(x, np.ndarray):
         return x.ctypes.data
+    if isinstance(x, C.c_void_p):
+        return x.value
+    if isinstance(x, int):
+        return x
     return x.data_ptr()
 
 
@@ -294,3 +316,102 @@ class Integrator:
         L = np.empty(3)
         E, T, U = mstar_energy(self.ctx, P, L)
         return dict(E=E, T=T, U=U, P=P, L=L)
+
+
+def mstar_batch_workspace_bytes(nsys, offsets, p=None) -> int:
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    return load().mstar_batch_workspace_bytes(int(nsys), _ptr(offsets), C.byref(p) if p is not None else None)
+
+
+def mstar_batch_init(nsys, offsets, m, r, v, p=None, workspace=None, workspace_bytes=0, cuda_stream=None):
+    offsets = np.ascontiguousarray(offsets, dtype=np.int32)
+    b = C.c_void_p()
+    rc = load().mstar_batch_init(C.byref(b), int(nsys), _ptr(offsets), _ptr(m), _ptr(r), _ptr(v),
+                                 C.byref(p) if p is not None else None, _ptr(workspace), int(workspace_bytes),
+                                 cuda_stream)
+    _check(rc, "mstar_batch_init")
+    return b
+
+
+def mstar_step_batched(b, t_end, launches):
+    st = mstar_batch_stats()
+    rc = load().mstar_step_batched(b, float(t_end), int(launches), C.byref(st))
+    return rc, st
+
+
+def mstar_batch_get_state(b, t=None, r=None, v=None, eps=None, status=None):
+    _check(load().mstar_batch_get_state(b, _ptr(t), _ptr(r), _ptr(v), _ptr(eps), _ptr(status)),
+           "mstar_batch_get_state")
+
+
+def mstar_batch_set_H(b, H):
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    _check(load().mstar_batch_set_H(b, _ptr(H)), "mstar_batch_set_H")
+
+
+def mstar_batch_launch_count(b) -> int:
+    return load().mstar_batch_launch_count(b)
+
+
+def mstar_batch_free(b):
+    if b:
+        load().mstar_batch_free(b)
+
+
+class Batch:
+    """Many independent systems integrated together (one CTA per system per launch); device
+    memory from torch, work on the torch stream current at construction."""
+
+    def __init__(self, systems, device=None, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmstar needs a CUDA GPU")
+        load()
+        self.device = torch.device(device or "cuda")
+        self.p = mstar_default_params(**params)
+        sizes = [len(sm[0]) for sm in systems]
+        self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+        self.nsys = len(systems)
+        self.nbody = int(self.offsets[-1])
+        m = np.ascontiguousarray(np.concatenate([np.asarray(s[0], np.float64) for s in systems]))
+        r = np.ascontiguousarray(np.concatenate([np.asarray(s[1], np.float64).reshape(-1, 3) for s in systems]))
+        v = np.ascontiguousarray(np.concatenate([np.asarray(s[2], np.float64).reshape(-1, 3) for s in systems]))
+        nbytes = mstar_batch_workspace_bytes(self.nsys, self.offsets, self.p)
+        if nbytes == 0:  # let the library name the problem (it rejects before allocating)
+            self.b = mstar_batch_init(self.nsys, self.offsets, m, r, v, self.p)
+            raise MstarError(MSTAR_ERR_INVALID_ARG, "mstar_batch_workspace_bytes")
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = self.ws.data_ptr() + (-self.ws.data_ptr()) % 256
+            self.stream = torch.cuda.current_stream(self.device)
+            self.b = mstar_batch_init(self.nsys, self.offsets, m, r, v, self.p, C.c_void_p(ptr), nbytes,
+                                      C.c_void_p(self.stream.cuda_stream))
+
+    def close(self):
+        if getattr(self, "b", None):
+            mstar_batch_free(self.b)
+            self.b = None
+
+    def __del__(self):
+        self.close()
+
+    def step(self, t_end, launches=1):
+        rc, st = mstar_step_batched(self.b, t_end, launches)
+        _check(rc, "mstar_step_batched")
+        return dict(accepted=st.accepted, rejected=st.rejected, force_evals=st.force_evals,
+                    finished=st.finished, failed=st.failed)
+
+    def state(self):
+        t = np.empty(self.nsys)
+        eps = np.empty(self.nsys)
+        status = np.empty(self.nsys, np.int32)
+        r = np.empty((self.nbody, 3))
+        v = np.empty((self.nbody, 3))
+        mstar_batch_get_state(self.b, t, r, v, eps, status)
+        o = self.offsets
+        return dict(t=t, eps=eps, status=status, r=[r[o[s]:o[s + 1]] for s in range(self.nsys)],
+                    v=[v[o[s]:o[s + 1]] for s in range(self.nsys)])
+
+    def set_H(self, H):
+        mstar_batch_set_H(self.b, H)
