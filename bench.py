@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", default="mstar", choices=["mstar", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-subsystems measurement and print its object")
     return ap.parse_args()
 
 
@@ -226,6 +228,7 @@ def run_batched(args, dev, M, W, torch):
     t_end = 1000.0  # no system gets there within the launches below: each launch is an attempt for all
     b = M.Batch([(s.m, s.r, s.v) for s in systems], device=dev)
     b.step(t_end, 40)  # step-size controllers settle from the first-step rule (halvings)
+    sched, tune_ms = b.autotune(t_end, repeats=2)  # setup, state unchanged
     launches = 5 * max(args.steps, 1)
     st0 = b.step(t_end, 0)
     l0 = M.mstar_batch_launch_count(b.b)
@@ -243,7 +246,11 @@ def run_batched(args, dev, M, W, torch):
     att = acc + st1["rejected"] - st0["rejected"]
     out = {"workload": BATCH_DESC, "systems": len(systems), "bodies": sum(len(s.m) for s in systems),
            "launches": nl, "ms_per_launch": ms / launches, "system_steps_per_s": acc / (ms * 1e-3),
-           "system_attempts_per_s": att / (ms * 1e-3), "failed": st1["failed"]}
+           "system_attempts_per_s": att / (ms * 1e-3), "failed": st1["failed"],
+           "schedule": {"warps_per_division_group_by_size_class": sched.tolist(),
+                        "size_classes": "[2,8] [9,16] [17,32] [33,64] [65,128] [129,256] [257,512]",
+                        "autotune_launch_ms": tune_ms},
+           "launch": "one CUDA graph launch per attempt (one kernel node per group width)"}
     # the single-system path, one context per system, on every 128th system
     secs = 0.0
     steps = 0
@@ -280,6 +287,9 @@ def run_mstar(args):
     from paper_2001_03180_gb300 import mstar as M
 
     M.load()
+    if args.batched_only:
+        print(json.dumps(run_batched(args, dev, M, W, torch)), flush=True)
+        return
     m, r, v = W.workload(WORKLOAD)
     n = len(m)
     g = M.Integrator(m, r, v, device=dev)

@@ -167,8 +167,12 @@ MSTAR_API int mstar_fp64_fma_rate(double* fma_per_second, void* cuda_stream);
 /* ---- Batched independent systems (Sec. 4.2: the parallel method extends to many
    independent N-body systems integrated simultaneously). */
 
-/* Largest system of a batch (one CTA of 128 threads builds its MST in registers). */
+/* Largest system of a batch (one CTA builds its MST with at most 4 keys per thread). */
 #define MSTAR_BATCH_MAX_N 512
+
+/* Size classes of the batch schedule: n in [2,8], [9,16], [17,32], [33,64], [65,128],
+   [129,256], [257,512]. */
+#define MSTAR_BATCH_NUM_CLASSES 7
 
 typedef struct mstar_batch mstar_batch;
 
@@ -194,13 +198,15 @@ MSTAR_API int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, 
                                const double* v, const mstar_params* p, void* workspace, size_t workspace_bytes,
                                void* cuda_stream);
 
-/* `launches` kernel launches; each advances every unfinished system by one GBS step
-   attempt towards t_end (accepted: the state and time advance and H grows by Eq. hnext;
-   rejected: H halves for the next launch; Sec. 2.3-2.4 as in mstar_step, per system).
-   A system stops at |t - t_end| <= t_tol |t_end|, after max_time_iter end-time-clamped
-   steps, or (status -3) after more than max_halvings successive rejections. Within a
-   launch each system is one CTA; its k_fix divisions are assigned to four warps by the
-   greedy longest-first recipe of Sec. 4.2. Synchronises the stream; out may be NULL. */
+/* `launches` launches of the batch's CUDA graph; each advances every unfinished system by
+   one GBS step attempt towards t_end (accepted: the state and time advance and H grows by
+   Eq. hnext; rejected: H halves for the next launch; Sec. 2.3-2.4 as in mstar_step, per
+   system). A system stops at |t - t_end| <= t_tol |t_end|, after max_time_iter
+   end-time-clamped steps, or (status -3) after more than max_halvings successive
+   rejections. Each system is one CTA of four division groups of G warps (G from the
+   schedule, by size class); its k_fix divisions go to the groups by the greedy
+   longest-first recipe of Sec. 4.2. The graph holds one independent kernel node per group
+   width in use. Synchronises the stream; out may be NULL. */
 MSTAR_API int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out);
 
 /* Per-system time t[nsys], state r, v (nbody x 3, host or device), last error eps[nsys]
@@ -211,6 +217,25 @@ MSTAR_API int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double
 /* Set every system's next fictitious step (host array H[nsys]; 0 = unset). */
 MSTAR_API int mstar_batch_set_H(mstar_batch* b, const double* H);
 
+/* Schedule of the batch: warps per division group (1, 2 or 4) for each of the
+   MSTAR_BATCH_NUM_CLASSES size classes. A new schedule rebuilds the graph (INVALID_ARG for
+   any other width). The default is 1 up to 64 bodies, 2 up to 128, 4 above. The schedule
+   changes only the work split, not the arithmetic of a system beyond the order in which
+   partial sums are added. */
+MSTAR_API int mstar_batch_set_schedule(mstar_batch* b, const int* schedule);
+MSTAR_API int mstar_batch_get_schedule(const mstar_batch* b, int* schedule);
+
+/* Autotuner with no counterpart in the paper (its GPU analogue of choosing how many
+   processes work on one force loop, Sec. 4.3): one pass of coordinate descent over the
+   size classes present, largest first, timing one graph launch towards t_end (best of
+   `repeats`, after a warm-up) for each group width with the other classes fixed, and
+   keeping the fastest. Trials run on a snapshot of the batch, which is put back: the
+   systems' state, time and step sizes are unchanged. Allocates a temporary device copy of
+   the workspace (NOMEM if that fails). Sets and returns the schedule (schedule_out may be
+   NULL) and the launch time it measured in ms (ms_out may be NULL). */
+MSTAR_API int mstar_batch_autotune(mstar_batch* b, double t_end, int repeats, int* schedule_out, double* ms_out);
+
+/* Kernel launches issued so far (graph kernel nodes count one each per graph launch). */
 MSTAR_API long long mstar_batch_launch_count(const mstar_batch* b);
 MSTAR_API void mstar_batch_free(mstar_batch* b);
 

@@ -1,22 +1,26 @@
 // Batched GBS steps for many independent small systems (Sec. 4.2 notes the method extends to
 // integrating multiple independent N-body systems simultaneously).
 //
-// One launch advances every unfinished system by one GBS step attempt. Each system is one
-// CTA of four warps:
+// One graph launch advances every unfinished system by one GBS step attempt. Each system is
+// one CTA of four division groups of G warps (G = 1, 2 or 4, chosen per size class):
 //  - the whole CTA builds the system's MST (Prim, exact FP64 keys, Sec. 3.2 / 3.4), the
 //    edge coordinates and the derivative information of the step start;
-//  - the k_fix leapfrog divisions are spread over the warps with the paper's greedy recipe
-//    (largest n_k first, to the least-loaded group, lowest index on ties; Sec. 4.2), and
-//    each warp runs its divisions with warp-level synchronisation only;
+//  - the k_fix leapfrog divisions are spread over the four groups with the paper's greedy
+//    recipe (largest n_k first, to the least-loaded group, lowest index on ties; Sec. 4.2);
+//    a group runs its divisions with group-level barriers only, its G warps splitting the
+//    pair loop by 32 x 32 blocks and the O(N) work by body;
 //  - the whole CTA then extrapolates (Aitken-Neville), evaluates the error of Eq.
 //    gbs-criterion and applies the step control of Sec. 2.3-2.4 for its system.
-// CTAs are issued largest system first so that the longest runs start early.
+// Systems of the same G form one kernel node of the graph (largest system first); the
+// nodes are independent, so the schedules run side by side on the GPU.
 //
 // The pair loop inside a warp uses the same symmetric rotation as the large-N kernel: lane
 // l owns body i of a 32-block and pairs with body (l + k) mod 32 of the partner block at
 // step k, so every unordered pair is visited once and the 32 partner accumulators are
-// updated by distinct lanes. Near pairs (N_d <= 2) are masked out and summed from edge
-// vectors afterwards, exactly as in the large-N path.
+// updated by distinct lanes. Each warp accumulates into its own partial acceleration
+// buffer; the group adds the G partials in a fixed order, so results do not depend on
+// timing. Near pairs (N_d <= 2) are masked out and summed from edge vectors afterwards,
+// exactly as in the large-N path.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -30,10 +34,17 @@
 namespace mstar {
 namespace {
 
-constexpr int kBW = 4;            // warps per system CTA
-constexpr int kBThreads = 32 * kBW;
+constexpr int kGroups = 4;        // division groups per system
+constexpr int kMaxG = 4;          // warps per group of the widest schedule
 constexpr int kBMaxN = 512;       // largest system of a batch
-constexpr int kBVpt = kBMaxN / kBThreads;
+constexpr int kNumClasses = 7;    // size classes of the schedule table
+
+// Size class of a system of n bodies: [2,8], [9,16], [17,32], ..., [257,512].
+__host__ __device__ __forceinline__ int size_class(int n) {
+  int c = 0;
+  while (c < kNumClasses - 1 && n > (8 << c)) ++c;
+  return c;
+}
 
 // Per-system scalars in device memory.
 struct SysScalars {
@@ -43,11 +54,12 @@ struct SysScalars {
   int halvings, time_iters, pad;
 };
 
-// Per-body storage (doubles), offsets in units of bodies.
+// Per-body storage (doubles), offsets in units of n doubles (a 3-vector field spans 3).
 enum : int {
   B_R = 0, B_V = 3, B_X0 = 6, B_V0 = 9, B_A0 = 12, B_TKK = 15,
-  B_WARP = 21,                      // 4 warps x (X 3, V 3, r 3, v 3, a 3)
-  B_END = B_WARP + kBW * 15,        // k_fix division end states x (X 3, V 3)
+  B_GRP = 21,                          // per group: X 3, V 3, r 3, v 3, kMaxG partial a x 3
+  kGrpStride = 12 + 3 * kMaxG,
+  B_END = B_GRP + kGroups * kGrpStride,  // k_fix division end states x (X 3, V 3)
 };
 constexpr int kBodyDoublesBase = B_END;  // + 6 * k_fix
 
@@ -59,8 +71,12 @@ struct BatchParams {
   int body_doubles;
 };
 
-struct WarpBuf {
-  double *X, *V, *r, *v, *a;  // 3-vectors per body, stride 3 (xyz)
+// Position of a thread within its division group.
+struct GI {
+  int g;     // group 0..3
+  int w;     // warp within the group
+  int lane;
+  int t;     // thread within the group
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -70,12 +86,48 @@ __device__ __forceinline__ double warp_sum(double x) {
 
 __device__ __forceinline__ double madd(double a, double f, double b) { return __dadd_rn(a, __dmul_rn(f, b)); }
 
+// Barrier over the 32 G threads of group g (named barrier g + 1; 0 is __syncthreads).
+template <int G>
+__device__ __forceinline__ void gsync(int g) {
+  if constexpr (G == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(32 * G) : "memory");
+  }
+}
+
+// Sums of three values over the group, added warp by warp in a fixed order.
+template <int G>
+__device__ __forceinline__ void gsum3(double& a, double& b, double& c, const GI& gi, double (*red)[kMaxG][3]) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  if constexpr (G > 1) {
+    if (gi.lane == 0) {
+      red[gi.g][gi.w][0] = a;
+      red[gi.g][gi.w][1] = b;
+      red[gi.g][gi.w][2] = c;
+    }
+    gsync<G>(gi.g);
+    a = red[gi.g][0][0];
+    b = red[gi.g][0][1];
+    c = red[gi.g][0][2];
+    for (int q = 1; q < G; ++q) {
+      a += red[gi.g][q][0];
+      b += red[gi.g][q][1];
+      c += red[gi.g][q][2];
+    }
+    gsync<G>(gi.g);
+  }
+}
+
 // Path sums from edge vectors (w_v = W_v + W_parent(v) + ...), then the COM shift; returns
-// sum m |w|^2 after the shift when want_T. Warp-level.
-__device__ double warp_rebuild(int n, const double* __restrict__ m, const int* __restrict__ parent,
-                               const double* W, double* w, double Mtot, bool want_T, int lane) {
+// sum m |w|^2 after the shift when want_T. Group-level; ends with the group synchronised.
+template <int G>
+__device__ double grebuild(int n, const double* __restrict__ m, const int* __restrict__ parent, const double* W,
+                           double* w, double Mtot, bool want_T, const GI& gi, double (*red)[kMaxG][3]) {
   double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-  for (int v = lane; v < n; v += 32) {
+  for (int v = gi.t; v < n; v += 32 * G) {
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int u = v; parent[u] >= 0; u = parent[u]) {
       s0 = __dadd_rn(s0, W[3 * u]);
@@ -89,32 +141,42 @@ __device__ double warp_rebuild(int n, const double* __restrict__ m, const int* _
     c1 += __dmul_rn(m[v], s1);
     c2 += __dmul_rn(m[v], s2);
   }
-  c0 = warp_sum(c0) / Mtot;
-  c1 = warp_sum(c1) / Mtot;
-  c2 = warp_sum(c2) / Mtot;
+  gsum3<G>(c0, c1, c2, gi, red);
+  c0 = c0 / Mtot;
+  c1 = c1 / Mtot;
+  c2 = c2 / Mtot;
   double t2 = 0.0;
-  for (int v = lane; v < n; v += 32) {
+  for (int v = gi.t; v < n; v += 32 * G) {
     const double q0 = __dsub_rn(w[3 * v], c0), q1 = __dsub_rn(w[3 * v + 1], c1), q2 = __dsub_rn(w[3 * v + 2], c2);
     w[3 * v] = q0;
     w[3 * v + 1] = q1;
     w[3 * v + 2] = q2;
     if (want_T) t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
   }
-  __syncwarp();
-  return want_T ? warp_sum(t2) : 0.0;
+  gsync<G>(gi.g);
+  if (!want_T) return 0.0;
+  double z1 = 0.0, z2 = 0.0;
+  gsum3<G>(t2, z1, z2, gi, red);
+  return t2;
 }
 
-// Pair loop of one system by one warp: a (3-vectors, times G) and U. sj_* in shared memory
-// hold one 32-block of partners and their accumulators.
+// One 32-block of partners and their accumulators, per warp.
 struct WarpShared {
   double x[32], y[32], z[32], mm[32], ax[32], ay[32], az[32];
   unsigned long long ms[32];
   int me[32], p[32], g[32];
 };
 
-__device__ double warp_forces(int n, int n_d, double G, const double* __restrict__ m, const int* __restrict__ parent,
-                              const int* __restrict__ gp, const int* __restrict__ coff, const int* __restrict__ cidx,
-                              const double* r, const double* X, double* a, WarpShared& sh, int lane) {
+// Pair loop of one system by one group: accelerations (3-vectors, times G) into a0 (the
+// group's first partial buffer; partial w at a0 + 3 n w) and the return value U. Ends with
+// the group synchronised and a0 complete.
+template <int G>
+__device__ double gforces(int n, int n_d, double Gc, const double* __restrict__ m, const int* __restrict__ parent,
+                          const int* __restrict__ gp, const int* __restrict__ coff, const int* __restrict__ cidx,
+                          const double* r, const double* X, double* a0, WarpShared& sh, const GI& gi,
+                          double (*red)[kMaxG][3]) {
+  const int lane = gi.lane;
+  double* a = a0 + (size_t)3 * n * gi.w;
   for (int v = lane; v < n; v += 32) {
     a[3 * v] = 0.0;
     a[3 * v + 1] = 0.0;
@@ -124,15 +186,17 @@ __device__ double warp_forces(int n, int n_d, double G, const double* __restrict
   const int nb = (n + 31) >> 5;
   const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
   double usum = 0.0;
+  int q = 0;
   for (int I = 0; I < nb; ++I) {
-    const int i = I * 32 + lane;
-    const bool ipad = i >= n;
-    const double xi = ipad ? 0.0 : r[3 * i], yi = ipad ? 0.0 : r[3 * i + 1], zi = ipad ? 0.0 : r[3 * i + 2];
-    const MassSplit msi = mass_split(ipad ? 1.0 : m[i]);
-    const double mi = ipad ? 0.0 : m[i];
-    const int pi = ipad ? -3 : parent[i], gpi = ipad ? -3 : gp[i];
-    double axi = 0.0, ayi = 0.0, azi = 0.0, ui = 0.0;
-    for (int J = I; J < nb; ++J) {
+    for (int J = I; J < nb; ++J, ++q) {
+      if ((q & (G - 1)) != gi.w) continue;
+      const int i = I * 32 + lane;
+      const bool ipad = i >= n;
+      const double xi = ipad ? 0.0 : r[3 * i], yi = ipad ? 0.0 : r[3 * i + 1], zi = ipad ? 0.0 : r[3 * i + 2];
+      const MassSplit msi = mass_split(ipad ? 1.0 : m[i]);
+      const double mi = ipad ? 0.0 : m[i];
+      const int pi = ipad ? -3 : parent[i], gpi = ipad ? -3 : gp[i];
+      double axi = 0.0, ayi = 0.0, azi = 0.0, ui = 0.0;
       const int jb = J * 32 + lane;
       const bool jpad = jb >= n;
       sh.x[lane] = jpad ? 0.0 : r[3 * jb];
@@ -174,33 +238,35 @@ __device__ double warp_forces(int n, int n_d, double G, const double* __restrict
         sh.az[jl] = fma(si, dz, sh.az[jl]);
         __syncwarp();
       }
+      // body jb and body i of this item are only ever touched by this lane of this warp
       if (!jpad) {  // partner sums were kept with the opposite sign
         a[3 * jb] -= sh.ax[lane];
         a[3 * jb + 1] -= sh.ay[lane];
         a[3 * jb + 2] -= sh.az[lane];
       }
+      if (!ipad) {
+        a[3 * i] += axi;
+        a[3 * i + 1] += ayi;
+        a[3 * i + 2] += azi;
+      }
+      usum += mi * ui;
       __syncwarp();
     }
-    if (!ipad) {
-      a[3 * i] += axi;
-      a[3 * i + 1] += ayi;
-      a[3 * i + 2] += azi;
-    }
-    usum += mi * ui;
-    __syncwarp();
   }
-  // near pairs from edge vectors: parent, children, grandparent, grandchildren, siblings
+  // near pairs from edge vectors: parent, children, grandparent, grandchildren, siblings.
+  // Body p goes to thread p mod 32G, i.e. lane p mod 32 of this warp: the same lane that
+  // updated it in the loop above.
   if (n_d >= 1) {
-    for (int p = lane; p < n; p += 32) {
+    for (int p = gi.t; p < n; p += 32 * G) {
       double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
-      auto add = [&](int q, double dx, double dy, double dz) {
+      auto add = [&](int q2, double dx, double dy, double dz) {
         const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
         const double ri = rsqrt_fp64(r2);
-        const double s = m[q] * ((ri * ri) * ri);
+        const double s = m[q2] * ((ri * ri) * ri);
         ax = fma(s, dx, ax);
         ay = fma(s, dy, ay);
         az = fma(s, dz, az);
-        if (q > p) u = fma(m[q], ri, u);
+        if (q2 > p) u = fma(m[q2], ri, u);
       };
       const int pp = parent[p];
       const double xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2];
@@ -232,16 +298,22 @@ __device__ double warp_forces(int n, int n_d, double G, const double* __restrict
       usum += m[p] * u;
     }
   }
-  __syncwarp();
-  for (int v = lane; v < n; v += 32) {
-    a[3 * v] *= G;
-    a[3 * v + 1] *= G;
-    a[3 * v + 2] *= G;
+  gsync<G>(gi.g);
+  // a0 = G_const x (partial 0 + partial 1 + ...), fixed order
+  for (int v = gi.t; v < n; v += 32 * G) {
+    for (int c = 0; c < 3; ++c) {
+      double s = a0[3 * v + c];
+      for (int w = 1; w < G; ++w) s += a0[(size_t)3 * n * w + 3 * v + c];
+      a0[3 * v + c] = s * Gc;
+    }
   }
-  __syncwarp();
-  return G * warp_sum(usum);
+  gsync<G>(gi.g);
+  double z1 = 0.0, z2 = 0.0;
+  gsum3<G>(usum, z1, z2, gi, red);
+  return Gc * usum;
 }
 
+template <int NW>
 __device__ __forceinline__ void block_argmin(unsigned long long& k, int& i, unsigned long long* rk, int* ri) {
   for (int o = 16; o > 0; o >>= 1) {
     const unsigned long long k2 = __shfl_down_sync(0xffffffffu, k, o);
@@ -260,7 +332,7 @@ __device__ __forceinline__ void block_argmin(unsigned long long& k, int& i, unsi
   __syncthreads();
   k = rk[0];
   i = ri[0];
-  for (int w = 1; w < kBW; ++w)
+  for (int w = 1; w < NW; ++w)
     if (rk[w] < k || (rk[w] == k && ri[w] < i)) {
       k = rk[w];
       i = ri[w];
@@ -273,26 +345,32 @@ __device__ __forceinline__ double d2x(const double* r, int u, int v) {
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-__global__ void __launch_bounds__(kBThreads)
-k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ off, BatchParams P, double t_end,
-               const double* __restrict__ mass, double* __restrict__ body, int* __restrict__ ibody,
-               SysScalars* __restrict__ sys, double* __restrict__ tdiv) {
-  __shared__ WarpShared wsh[kBW];
-  __shared__ unsigned long long rk[kBW];
-  __shared__ int ri[kBW];
+// One GBS step attempt for each of the `count` systems order[0 .. count-1].
+template <int G>
+__global__ void __launch_bounds__(128 * G)
+k_batched_step(int count, const int* __restrict__ order, const int* __restrict__ off, BatchParams P,
+               const double* __restrict__ tend, const double* __restrict__ mass, double* __restrict__ body,
+               int* __restrict__ ibody, SysScalars* __restrict__ sys, double* __restrict__ tdiv) {
+  constexpr int NT = 128 * G, NW = 4 * G, VPT = kBMaxN / NT;
+  __shared__ WarpShared wsh[NW];
+  __shared__ unsigned long long rk[NW];
+  __shared__ int ri[NW];
   __shared__ int s_cnt[kBMaxN + 1];
-  __shared__ int s_lvl[kBMaxN];
-  __shared__ double s_red[kBW];
+  __shared__ double s_red[NW];
+  __shared__ double s_gred[kGroups][kMaxG][3];
   __shared__ double s_scal[4];  // U0, T0, H, abort flag
+  if ((int)blockIdx.x >= count) return;
   const int s = order[blockIdx.x];
   SysScalars* S = sys + s;
   if (S->status != 0) return;
+  const double t_end = *tend;
   const int o = off[s], n = off[s + 1] - o;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const GI gi{warp / G, warp % G, lane, (warp % G) * 32 + lane};
   const int K = P.k_fix;
   const double* m = mass + o;
   double* bd = body + (size_t)o * P.body_doubles;
-  // body-major blocks of 3-vectors: field f of body v at bd[f * 3 * n + 3 v + c]
+  // body-major blocks of 3-vectors: field f of body v at bd[f * n + 3 v + c]
   auto F = [&](int field) { return bd + (size_t)field * n; };
   double* R = F(B_R);
   double* Vs = F(B_V);
@@ -303,18 +381,18 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
   int* ib = ibody + (size_t)o * 5;
   int* parent = ib;
   int* gp = ib + n;
-  int* coff = ib + 2 * n;       // n + 1 entries (uses the level slot's first entry too)
+  int* coff = ib + 2 * n;       // n + 1 entries
   int* cidx = ib + 3 * n + 1;   // n - 1 entries
   const double t0 = S->t, B = S->B, Mtot = S->M;
 
   // ---- MST (Prim with exact FP64 keys, one CTA) and the children lists
-  unsigned long long key[kBVpt];
-  bool intree[kBVpt];
   {
+    unsigned long long key[VPT];
+    bool intree[VPT];
     unsigned long long bk = ~0ull;
     int bi = INT_MAX;
-    for (int q = 0; q < kBVpt; ++q) {
-      const int v = tid + q * kBThreads;
+    for (int q = 0; q < VPT; ++q) {
+      const int v = tid + q * NT;
       intree[q] = v >= n;
       key[q] = 0x7ff0000000000000ull;
       if (v < n) {
@@ -325,20 +403,19 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
           bi = v;
         }
         parent[v] = -1;
-        s_lvl[v] = 0;
       }
     }
-    block_argmin(bk, bi, rk, ri);
+    block_argmin<NW>(bk, bi, rk, ri);
     const int root = bi;
-    for (int q = 0; q < kBVpt; ++q)
-      if (tid + q * kBThreads == root) intree[q] = true;
+    for (int q = 0; q < VPT; ++q)
+      if (tid + q * NT == root) intree[q] = true;
     int u = root;
     for (int it = 1; it < n; ++it) {
       bk = ~0ull;
       bi = INT_MAX;
-      for (int q = 0; q < kBVpt; ++q) {
+      for (int q = 0; q < VPT; ++q) {
         if (intree[q]) continue;
-        const int v = tid + q * kBThreads;
+        const int v = tid + q * NT;
         const double d = d2x(R, u, v);
         if (d < __longlong_as_double((long long)key[q])) {
           key[q] = key_bits(d);
@@ -349,24 +426,19 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
           bi = v;
         }
       }
-      block_argmin(bk, bi, rk, ri);
+      block_argmin<NW>(bk, bi, rk, ri);
       const int nxt = bi;
-      if ((nxt % kBThreads) == tid) {
-        intree[nxt / kBThreads] = true;
-        int p = parent[nxt];
-        if (p < 0) {
-          p = root;
-          parent[nxt] = p;
-        }
-        s_lvl[nxt] = s_lvl[p] + 1;
+      if ((nxt % NT) == tid) {
+        intree[nxt / NT] = true;
+        if (parent[nxt] < 0) parent[nxt] = root;
       }
       u = nxt;
     }
     __syncthreads();
     // grandparents and children CSR (ascending child index)
-    for (int v = tid; v <= n; v += kBThreads) s_cnt[v] = 0;
+    for (int v = tid; v <= n; v += NT) s_cnt[v] = 0;
     __syncthreads();
-    for (int v = tid; v < n; v += kBThreads) {
+    for (int v = tid; v < n; v += NT) {
       const int p = parent[v];
       gp[v] = p >= 0 ? parent[p] : -1;
       if (p >= 0) atomicAdd(&s_cnt[p], 1);
@@ -381,9 +453,7 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
         acc += c;
       }
       coff[n] = acc;
-    }
-    __syncthreads();
-    if (tid == 0) {  // n <= 512: a sequential fill keeps every list in ascending order
+      // n <= 512: a sequential fill keeps every list in ascending order
       for (int v = 0; v < n; ++v) {
         const int p = parent[v];
         if (p >= 0) cidx[s_cnt[p]++] = v;
@@ -392,8 +462,8 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
     __syncthreads();
   }
 
-  // ---- edge coordinates of the step start, T0, and the derivative information (warp 0)
-  for (int v = tid; v < n; v += kBThreads) {
+  // ---- edge coordinates of the step start
+  for (int v = tid; v < n; v += NT) {
     const int p = parent[v];
     for (int c = 0; c < 3; ++c) {
       X0[3 * v + c] = p >= 0 ? __dsub_rn(R[3 * v + c], R[3 * p + c]) : 0.0;
@@ -401,97 +471,102 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
     }
   }
   __syncthreads();
-  {
-    WarpBuf wb{F(B_WARP + warp * 15), F(B_WARP + warp * 15 + 3), F(B_WARP + warp * 15 + 6),
-               F(B_WARP + warp * 15 + 9), F(B_WARP + warp * 15 + 12)};
-    if (warp == 0) {
-      const double U0 = warp_forces(n, P.n_d, P.G, m, parent, gp, coff, cidx, R, X0, wb.a, wsh[0], lane);
-      double t2 = 0.0;
-      for (int v = lane; v < n; v += 32) {
-        const double q0 = Vs[3 * v], q1 = Vs[3 * v + 1], q2 = Vs[3 * v + 2];
-        t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
-        const int p = parent[v];
-        for (int c = 0; c < 3; ++c) A0[3 * v + c] = p >= 0 ? __dsub_rn(wb.a[3 * v + c], wb.a[3 * p + c]) : 0.0;
-      }
-      const double T0 = 0.5 * warp_sum(t2);
-      if (lane == 0) {
-        // Sec. 2.4: first step ds = q U dt; then the controller's step, clamped to t_end
-        const double dt = t_end - t0;
-        double abort_ = 0.0;
-        double Hs = 0.0;
-        if (fabs(dt) <= P.t_tol * fabs(t_end)) {
-          S->status = 1;
-          abort_ = 1.0;
-        } else {
-          Hs = (S->H == 0.0) ? P.q_first * U0 * dt : fabs(S->H) * (dt < 0 ? -1.0 : 1.0);
-          if (fabs(Hs / U0) >= fabs(dt)) {
-            Hs = U0 * dt;
-            if (S->halvings == 0) {
-              if (S->time_iters >= P.max_time_iter) {
-                S->status = 2;
-                abort_ = 1.0;
-              } else {
-                S->time_iters++;
-              }
+  double* gX = F(B_GRP + gi.g * kGrpStride);
+  double* gV = gX + 3 * n;
+  double* gr = gX + 6 * n;
+  double* gv = gX + 9 * n;
+  double* ga = gX + 12 * n;
+  // ---- derivative information of the step start (group 0) and the step size
+  if (gi.g == 0) {
+    const double U0 = gforces<G>(n, P.n_d, P.G, m, parent, gp, coff, cidx, R, X0, ga, wsh[warp], gi, s_gred);
+    double t2 = 0.0;
+    for (int v = gi.t; v < n; v += 32 * G) {
+      const double q0 = Vs[3 * v], q1 = Vs[3 * v + 1], q2 = Vs[3 * v + 2];
+      t2 += __dmul_rn(m[v], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+      const int p = parent[v];
+      for (int c = 0; c < 3; ++c) A0[3 * v + c] = p >= 0 ? __dsub_rn(ga[3 * v + c], ga[3 * p + c]) : 0.0;
+    }
+    double z1 = 0.0, z2 = 0.0;
+    gsum3<G>(t2, z1, z2, gi, s_gred);
+    const double T0 = 0.5 * t2;
+    if (gi.t == 0) {
+      // Sec. 2.4: first step ds = q U dt; then the controller's step, clamped to t_end
+      const double dt = t_end - t0;
+      double abort_ = 0.0;
+      double Hs = 0.0;
+      if (fabs(dt) <= P.t_tol * fabs(t_end)) {
+        S->status = 1;
+        abort_ = 1.0;
+      } else {
+        Hs = (S->H == 0.0) ? P.q_first * U0 * dt : fabs(S->H) * (dt < 0 ? -1.0 : 1.0);
+        if (fabs(Hs / U0) >= fabs(dt)) {
+          Hs = U0 * dt;
+          if (S->halvings == 0) {
+            if (S->time_iters >= P.max_time_iter) {
+              S->status = 2;
+              abort_ = 1.0;
+            } else {
+              S->time_iters++;
             }
           }
         }
-        s_scal[0] = U0;
-        s_scal[1] = T0;
-        s_scal[2] = Hs;
-        s_scal[3] = abort_;
-        S->U0 = U0;
-        S->T0 = T0;
       }
+      s_scal[0] = U0;
+      s_scal[1] = T0;
+      s_scal[2] = Hs;
+      s_scal[3] = abort_;
+      S->U0 = U0;
+      S->T0 = T0;
     }
-    __syncthreads();
-    if (s_scal[3] != 0.0) return;
+  }
+  __syncthreads();
+  if (s_scal[3] != 0.0) return;
+  {
     const double T0 = s_scal[1], H = s_scal[2];
-
-    // ---- this warp's divisions (greedy longest-first assignment to kBW groups)
-    int load[kBW] = {0, 0, 0, 0};
+    // ---- this group's divisions (greedy longest-first assignment to the four groups)
+    int load[kGroups] = {0, 0, 0, 0};
     for (int k = K; k >= 1; --k) {
       int gsel = 0;
-      for (int w = 1; w < kBW; ++w)
+      for (int w = 1; w < kGroups; ++w)
         if (load[w] < load[gsel]) gsel = w;
       load[gsel] += 2 * k;
-      if (gsel != warp) continue;
+      if (gsel != gi.g) continue;
       const int nk = 2 * k;
       const double delta = H / (double)nk;
       double f = (0.5 * delta) / (T0 + B);
-      for (int v = lane; v < n; v += 32)
+      for (int v = gi.t; v < n; v += 32 * G)
         for (int c = 0; c < 3; ++c) {
-          wb.X[3 * v + c] = madd(X0[3 * v + c], f, V0[3 * v + c]);
-          wb.V[3 * v + c] = V0[3 * v + c];
+          gX[3 * v + c] = madd(X0[3 * v + c], f, V0[3 * v + c]);
+          gV[3 * v + c] = V0[3 * v + c];
         }
       double t = t0 + f;
-      __syncwarp();
-      warp_rebuild(n, m, parent, wb.X, wb.r, Mtot, false, lane);
+      gsync<G>(gi.g);
+      grebuild<G>(n, m, parent, gX, gr, Mtot, false, gi, s_gred);
       for (int tau = 1; tau <= nk; ++tau) {
-        const double U = warp_forces(n, P.n_d, P.G, m, parent, gp, coff, cidx, wb.r, wb.X, wb.a, wsh[warp], lane);
+        const double U = gforces<G>(n, P.n_d, P.G, m, parent, gp, coff, cidx, gr, gX, ga, wsh[warp], gi, s_gred);
         const double fk = delta / U;
-        for (int v = lane; v < n; v += 32) {
+        for (int v = gi.t; v < n; v += 32 * G) {
           const int p = parent[v];
           if (p >= 0)
-            for (int c = 0; c < 3; ++c) wb.V[3 * v + c] = madd(wb.V[3 * v + c], fk, __dsub_rn(wb.a[3 * v + c], wb.a[3 * p + c]));
+            for (int c = 0; c < 3; ++c) gV[3 * v + c] = madd(gV[3 * v + c], fk, __dsub_rn(ga[3 * v + c], ga[3 * p + c]));
         }
-        __syncwarp();
-        const double T = 0.5 * warp_rebuild(n, m, parent, wb.V, wb.v, Mtot, true, lane);
+        gsync<G>(gi.g);
+        const double T = 0.5 * grebuild<G>(n, m, parent, gV, gv, Mtot, true, gi, s_gred);
         f = ((tau == nk) ? 0.5 * delta : delta) / (T + B);
-        for (int v = lane; v < n; v += 32)
-          for (int c = 0; c < 3; ++c) wb.X[3 * v + c] = madd(wb.X[3 * v + c], f, wb.V[3 * v + c]);
+        for (int v = gi.t; v < n; v += 32 * G)
+          for (int c = 0; c < 3; ++c) gX[3 * v + c] = madd(gX[3 * v + c], f, gV[3 * v + c]);
         t += f;
-        __syncwarp();
-        if (tau < nk) warp_rebuild(n, m, parent, wb.X, wb.r, Mtot, false, lane);
+        gsync<G>(gi.g);
+        if (tau < nk) grebuild<G>(n, m, parent, gX, gr, Mtot, false, gi, s_gred);
       }
       double* E = F(B_END + 6 * (k - 1));
-      for (int v = lane; v < n; v += 32)
+      for (int v = gi.t; v < n; v += 32 * G)
         for (int c = 0; c < 3; ++c) {
-          E[3 * v + c] = wb.X[3 * v + c];
-          E[3 * n + 3 * v + c] = wb.V[3 * v + c];
+          E[3 * v + c] = gX[3 * v + c];
+          E[3 * n + 3 * v + c] = gV[3 * v + c];
         }
-      if (lane == 0) tdiv[(size_t)s * kMaxKfix + (k - 1)] = t;
-      __syncwarp();
+      if (gi.t == 0) tdiv[(size_t)s * kMaxKfix + (k - 1)] = t;
+      gsync<G>(gi.g);
     }
   }
   __syncthreads();
@@ -510,7 +585,7 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
     tkk = prev[K - 1];
   };
   double e = 0.0;
-  for (int v = tid; v < n; v += kBThreads) {
+  for (int v = tid; v < n; v += NT) {
     double Sv[kMaxKfix], dX[3], dV[3];
     for (int c = 0; c < 3; ++c) {
       double tkk, tp = 0.0;
@@ -547,7 +622,7 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
   __syncthreads();
   if (tid == 0) {
     double eps = s_red[0];
-    for (int w = 1; w < kBW; ++w) eps = nanmax(eps, s_red[w]);
+    for (int w = 1; w < NW; ++w) eps = nanmax(eps, s_red[w]);
     S->eps = eps;
     S->force_evals += 2 * K * (K + 1) / 2 + 1;
     if (eps <= P.eta) {
@@ -568,27 +643,26 @@ k_batched_step(int nsys, const int* __restrict__ order, const int* __restrict__ 
   __syncthreads();
   if (s_scal[3] == 0.0) return;
   // ---- accept: deconstruct the extrapolated edge vectors into the Cartesian state
-  if (warp < 2) {
-    double* dst = warp == 0 ? R : Vs;
-    const double* src = warp == 0 ? TKK : TKK + 3 * n;
-    warp_rebuild(n, m, parent, src, dst, Mtot, false, lane);
+  if (gi.g < 2) {
+    double* dst = gi.g == 0 ? R : Vs;
+    const double* src = gi.g == 0 ? TKK : TKK + 3 * n;
+    grebuild<G>(n, m, parent, src, dst, Mtot, false, gi, s_gred);
   }
 }
 
-// Initial COM shift, B = U - T and M per system (one CTA each).
-__global__ void __launch_bounds__(kBThreads)
+// Initial COM shift, B = U - T and M per system (one warp each).
+__global__ void __launch_bounds__(32)
 k_batched_init(int nsys, const int* __restrict__ off, BatchParams P, const double* __restrict__ mass,
                double* __restrict__ body, int* __restrict__ ibody, SysScalars* __restrict__ sys) {
   __shared__ WarpShared wsh;
   const int s = blockIdx.x;
   const int o = off[s], n = off[s + 1] - o;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x;
+  const GI gi{0, 0, lane, lane};
   const double* m = mass + o;
   double* bd = body + (size_t)o * P.body_doubles;
   double* R = bd + (size_t)B_R * n;
   double* Vs = bd + (size_t)B_V * n;
-  if (tid >= 32) return;
-  const int lane = tid;
   double M = 0.0;
   if (lane == 0)
     for (int v = 0; v < n; ++v) M += m[v];
@@ -613,8 +687,8 @@ k_batched_init(int nsys, const int* __restrict__ off, BatchParams P, const doubl
   }
   // U with every pair Cartesian (Eq. 1), T
   int* ib = ibody + (size_t)o * 5;
-  double* a = bd + (size_t)B_WARP * n;
-  const double U = warp_forces(n, 0, P.G, m, ib, ib + n, ib + 2 * n, ib + 3 * n + 1, R, R, a, wsh, lane);
+  double* a = bd + (size_t)B_GRP * n + 12 * (size_t)n;
+  const double U = gforces<1>(n, 0, P.G, m, ib, ib + n, ib + 2 * n, ib + 3 * n + 1, R, R, a, wsh, gi, nullptr);
   double t2 = 0.0;
   for (int v = lane; v < n; v += 32) {
     const double q0 = Vs[3 * v], q1 = Vs[3 * v + 1], q2 = Vs[3 * v + 2];
@@ -636,9 +710,12 @@ using mstar::BatchParams;
 using mstar::kBodyDoublesBase;
 using mstar::kMaxKfix;
 using mstar::kBMaxN;
-using mstar::kBThreads;
+using mstar::kNumClasses;
 using mstar::B_R;
 using mstar::B_V;
+
+static_assert(kNumClasses == MSTAR_BATCH_NUM_CLASSES, "size classes of the schedule table");
+static_assert(kBMaxN == MSTAR_BATCH_MAX_N, "largest system of a batch");
 
 struct mstar_batch {
   int nsys = 0, nbody = 0;
@@ -648,11 +725,18 @@ struct mstar_batch {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   int *off = nullptr, *order = nullptr, *ibody = nullptr;
-  double *mass = nullptr, *body = nullptr, *tdiv = nullptr, *stage = nullptr;
+  double *mass = nullptr, *body = nullptr, *tdiv = nullptr, *stage = nullptr, *tend = nullptr;
   SysScalars* sys = nullptr;
   BatchParams bp{};
   std::vector<int> off_h;
   long long launches = 0;
+  // schedule: warps per division group for each size class, the systems of each schedule
+  // (largest first) as consecutive segments of `order`, and the graph of one launch
+  int sched[kNumClasses] = {};
+  int seg_begin[3] = {}, seg_count[3] = {};  // schedules G = 1, 2, 4
+  cudaGraphExec_t exec = nullptr;
+  int graph_nodes = 0;
+  double tend_h = NAN;
 };
 
 namespace mstar_batch_detail {
@@ -681,6 +765,7 @@ size_t bcarve(int nsys, int nbody, int K, void* base, mstar_batch* b) {
   double* tdiv = c.take<double>((size_t)nsys * kMaxKfix);
   double* stage = c.take<double>((size_t)nbody * 3);
   SysScalars* sys = c.take<SysScalars>(nsys);
+  double* tend = c.take<double>(1);
   if (b) {
     b->off = off;
     b->order = order;
@@ -690,6 +775,7 @@ size_t bcarve(int nsys, int nbody, int K, void* base, mstar_batch* b) {
     b->tdiv = tdiv;
     b->stage = stage;
     b->sys = sys;
+    b->tend = tend;
   }
   return (c.off + 255) & ~size_t(255);
 }
@@ -721,6 +807,105 @@ __global__ void k_scatter_vec(int nbody, const int* __restrict__ off, int nsys, 
   }
 }
 
+int sched_index(int G) { return G == 1 ? 0 : (G == 2 ? 1 : (G == 4 ? 2 : -1)); }
+
+// Warps per division group by size class before any tuning: wider groups for larger systems.
+void default_schedule(int* sched) {
+  static const int d[kNumClasses] = {1, 1, 1, 1, 2, 4, 4};
+  for (int c = 0; c < kNumClasses; ++c) sched[c] = d[c];
+}
+
+void destroy_graph(mstar_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_nodes = 0;
+}
+
+// Order the systems by schedule (G = 1, 2, 4 segments), largest pair work first within a
+// segment, upload the order and build the graph: one independent kernel node per nonempty
+// segment, the widest schedule at the highest priority.
+int apply_schedule(mstar_batch* b, const int* sched) {
+  for (int c = 0; c < kNumClasses; ++c)
+    if (sched_index(sched[c]) < 0) return MSTAR_ERR_INVALID_ARG;
+  std::vector<int> ord(b->nsys);
+  for (int s = 0; s < b->nsys; ++s) ord[s] = s;
+  auto n_of = [&](int s) { return b->off_h[s + 1] - b->off_h[s]; };
+  auto g_of = [&](int s) { return sched_index(sched[mstar::size_class(n_of(s))]); };
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const int gx = g_of(x), gy = g_of(y);
+    if (gx != gy) return gx < gy;
+    return (long long)n_of(x) * n_of(x) > (long long)n_of(y) * n_of(y);
+  });
+  int begin[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+  for (int s = 0; s < b->nsys; ++s) count[g_of(s)]++;
+  begin[1] = count[0];
+  begin[2] = count[0] + count[1];
+  if (cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * b->nsys, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
+      cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return MSTAR_ERR_CUDA;
+  destroy_graph(b);
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return MSTAR_ERR_CUDA;
+  int lo_prio = 0, hi_prio = 0;
+  cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+  bool ok = true;
+  int nodes = 0;
+  for (int q = 2; q >= 0 && ok; --q) {
+    if (!count[q]) continue;
+    int cnt = count[q];
+    const int* ordp = b->order + begin[q];
+    void* args[] = {&cnt, (void*)&ordp, (void*)&b->off, (void*)&b->bp, (void*)&b->tend, (void*)&b->mass,
+                    (void*)&b->body, (void*)&b->ibody, (void*)&b->sys, (void*)&b->tdiv};
+    cudaKernelNodeParams kp{};
+    kp.func = q == 0 ? (void*)mstar::k_batched_step<1> : (q == 1 ? (void*)mstar::k_batched_step<2>
+                                                                  : (void*)mstar::k_batched_step<4>);
+    kp.gridDim = dim3(cnt);
+    kp.blockDim = dim3(128 << q);
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    cudaGraphNode_t node;
+    ok = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) == cudaSuccess;
+    if (ok) {
+      cudaLaunchAttributeValue pv{};
+      pv.priority = q == 2 ? hi_prio : (q == 1 ? (hi_prio + lo_prio) / 2 : lo_prio);
+      cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &pv);  // a hint; failure is harmless
+      nodes++;
+    }
+  }
+  cudaGetLastError();
+  if (ok) ok = cudaGraphInstantiate(&b->exec, graph, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
+  cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    b->exec = nullptr;
+    return MSTAR_ERR_CUDA;
+  }
+  b->graph_nodes = nodes;
+  for (int c = 0; c < kNumClasses; ++c) b->sched[c] = sched[c];
+  for (int q = 0; q < 3; ++q) {
+    b->seg_begin[q] = begin[q];
+    b->seg_count[q] = count[q];
+  }
+  return MSTAR_OK;
+}
+
+int set_tend(mstar_batch* b, double t_end) {
+  if (b->tend_h == t_end) return MSTAR_OK;
+  b->tend_h = t_end;
+  // pageable source: the copy is staged before cudaMemcpyAsync returns
+  return cudaMemcpyAsync(b->tend, &b->tend_h, sizeof(double), cudaMemcpyHostToDevice, b->stream) == cudaSuccess
+             ? MSTAR_OK
+             : MSTAR_ERR_CUDA;
+}
+
+int launch_graph(mstar_batch* b, int launches) {
+  for (int l = 0; l < launches; ++l) {
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+    b->launches += b->graph_nodes;
+  }
+  return MSTAR_OK;
+}
+
 }  // namespace mstar_batch_detail
 
 using namespace mstar_batch_detail;
@@ -741,6 +926,7 @@ size_t mstar_batch_workspace_bytes(int nsys, const int* offsets, const mstar_par
 void mstar_batch_free(mstar_batch* b) {
   if (!b) return;
   if (b->stream) cudaStreamSynchronize(b->stream);
+  destroy_graph(b);
   if (b->own_ws && b->ws) cudaFree(b->ws);
   delete b;
 }
@@ -790,13 +976,6 @@ int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const doub
   b->bp = BatchParams{p->eta_gbs, p->a_gbs, p->fac_min, p->fac_max, p->q_first, p->t_tol, p->G,
                       p->k_fix, p->n_d, p->max_halvings, p->max_time_iter, kBodyDoublesBase + 6 * p->k_fix};
   b->off_h.assign(offsets, offsets + nsys + 1);
-  // systems in decreasing order of pair work, so the longest CTAs start first
-  std::vector<int> ord(nsys);
-  for (int s = 0; s < nsys; ++s) ord[s] = s;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) {
-    const long long na = offsets[a + 1] - offsets[a], nc = offsets[c + 1] - offsets[c];
-    return na * na > nc * nc;
-  });
   // host-side validation of the inputs (copied to the host when they live on the device)
   std::vector<double> mh(nbody), rh(3 * (size_t)nbody), vh(3 * (size_t)nbody);
   auto fetch = [&](double* dst, const double* src, size_t count) {
@@ -824,7 +1003,6 @@ int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const doub
   bool ok = cudaMemcpyToSymbol(mstar::c_bfac, fac, sizeof(fac)) == cudaSuccess &&
             cudaMemsetAsync(b->ws, 0, need, st) == cudaSuccess &&
             cudaMemcpyAsync(b->off, offsets, sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-            cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * nsys, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(b->mass, mh.data(), sizeof(double) * nbody, cudaMemcpyHostToDevice, st) == cudaSuccess &&
             cudaMemcpyAsync(b->stage, rh.data(), sizeof(double) * 3 * nbody, cudaMemcpyHostToDevice, st) == cudaSuccess;
   const int nb = (nbody + 255) / 256;
@@ -834,7 +1012,7 @@ int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const doub
   }
   if (ok) {
     k_scatter_vec<<<nb, 256, 0, st>>>(nbody, b->off, nsys, b->bp.body_doubles, B_V, b->stage, b->body, 1);
-    mstar::k_batched_init<<<nsys, kBThreads, 0, st>>>(nsys, b->off, b->bp, b->mass, b->body, b->ibody, b->sys);
+    mstar::k_batched_init<<<nsys, 32, 0, st>>>(nsys, b->off, b->bp, b->mass, b->body, b->ibody, b->sys);
     b->launches += 3;
     ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
   }
@@ -842,18 +1020,22 @@ int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, const doub
     mstar_batch_free(b);
     return MSTAR_ERR_CUDA;
   }
+  int sched[kNumClasses];
+  default_schedule(sched);
+  const int rc = apply_schedule(b, sched);
+  if (rc) {
+    mstar_batch_free(b);
+    return rc;
+  }
   *out = b;
   return MSTAR_OK;
 }
 
 int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out) {
   if (!b || !std::isfinite(t_end) || launches < 0) return MSTAR_ERR_INVALID_ARG;
-  for (int l = 0; l < launches; ++l) {
-    mstar::k_batched_step<<<b->nsys, kBThreads, 0, b->stream>>>(b->nsys, b->order, b->off, b->bp, t_end, b->mass, b->body,
-                                                          b->ibody, b->sys, b->tdiv);
-    b->launches++;
-  }
-  if (cudaGetLastError() != cudaSuccess) return MSTAR_ERR_CUDA;
+  int rc = set_tend(b, t_end);
+  if (!rc) rc = launch_graph(b, launches);
+  if (rc) return rc;
   if (out) {
     std::vector<SysScalars> h(b->nsys);
     if (cudaMemcpyAsync(h.data(), b->sys, sizeof(SysScalars) * b->nsys, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess ||
@@ -874,13 +1056,104 @@ int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_s
   return MSTAR_OK;
 }
 
+int mstar_batch_set_schedule(mstar_batch* b, const int* schedule) {
+  if (!b || !schedule) return MSTAR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  return apply_schedule(b, schedule);
+}
+
+int mstar_batch_get_schedule(const mstar_batch* b, int* schedule) {
+  if (!b || !schedule) return MSTAR_ERR_INVALID_ARG;
+  for (int c = 0; c < kNumClasses; ++c) schedule[c] = b->sched[c];
+  return MSTAR_OK;
+}
+
+int mstar_batch_autotune(mstar_batch* b, double t_end, int repeats, int* schedule_out, double* ms_out) {
+  if (!b || !std::isfinite(t_end) || repeats < 1) return MSTAR_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  // the trials run on the real state: snapshot the workspace and put it back before each
+  void* snap = nullptr;
+  if (cudaMalloc(&snap, b->ws_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return MSTAR_ERR_NOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = MSTAR_OK;
+  const double tend_saved = b->tend_h;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      cudaMemcpyAsync(snap, b->ws, b->ws_bytes, cudaMemcpyDeviceToDevice, b->stream) != cudaSuccess)
+    rc = MSTAR_ERR_CUDA;
+  auto restore = [&]() {
+    return cudaMemcpyAsync(b->ws, snap, b->ws_bytes, cudaMemcpyDeviceToDevice, b->stream) == cudaSuccess &&
+                   cudaStreamSynchronize(b->stream) == cudaSuccess
+               ? MSTAR_OK
+               : MSTAR_ERR_CUDA;
+  };
+  // time of one graph launch under schedule `sc` (the order segments are re-uploaded after
+  // each restore, since the snapshot holds the order of the schedule current at the call)
+  auto trial = [&](const int* sc, double* ms) {
+    double best = INFINITY;
+    for (int r = 0; r <= repeats; ++r) {  // r = 0 warms up (module load, caches)
+      int q = restore();
+      if (!q) q = apply_schedule(b, sc);
+      b->tend_h = NAN;
+      if (!q) q = set_tend(b, t_end);
+      if (q) return q;
+      if (cudaEventRecord(e0, b->stream) != cudaSuccess) return (int)MSTAR_ERR_CUDA;
+      if ((q = launch_graph(b, 1))) return q;
+      if (cudaEventRecord(e1, b->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        return (int)MSTAR_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) best = std::min(best, (double)t);
+    }
+    *ms = best;
+    return (int)MSTAR_OK;
+  };
+  int present[kNumClasses] = {};
+  for (int s = 0; s < b->nsys; ++s) present[mstar::size_class(b->off_h[s + 1] - b->off_h[s])] = 1;
+  int cur[kNumClasses];
+  for (int c = 0; c < kNumClasses; ++c) cur[c] = b->sched[c];
+  double cur_ms = 0.0;
+  if (!rc) rc = trial(cur, &cur_ms);
+  // one pass of coordinate descent, largest class first: each class keeps the group width
+  // that gave the shortest launch with the other classes fixed
+  static const int widths[3] = {1, 2, 4};
+  for (int c = kNumClasses - 1; c >= 0 && !rc; --c) {
+    if (!present[c]) continue;
+    for (int q = 0; q < 3 && !rc; ++q) {
+      if (widths[q] == cur[c]) continue;
+      int cand[kNumClasses];
+      for (int x = 0; x < kNumClasses; ++x) cand[x] = cur[x];
+      cand[c] = widths[q];
+      double ms = 0.0;
+      rc = trial(cand, &ms);
+      if (!rc && ms < cur_ms) {
+        cur_ms = ms;
+        cur[c] = widths[q];
+      }
+    }
+  }
+  if (!rc) rc = restore();
+  if (!rc) rc = apply_schedule(b, cur);
+  b->tend_h = NAN;
+  if (!rc && std::isfinite(tend_saved)) rc = set_tend(b, tend_saved);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(snap);
+  if (rc) return rc;
+  if (schedule_out)
+    for (int c = 0; c < kNumClasses; ++c) schedule_out[c] = cur[c];
+  if (ms_out) *ms_out = cur_ms;
+  return MSTAR_OK;
+}
+
 int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double* v, double* eps, int* status) {
   if (!b) return MSTAR_ERR_INVALID_ARG;
   std::vector<SysScalars> h(b->nsys);
   if (cudaMemcpyAsync(h.data(), b->sys, sizeof(SysScalars) * b->nsys, cudaMemcpyDeviceToHost, b->stream) != cudaSuccess)
     return MSTAR_ERR_CUDA;
   const int nb = (b->nbody + 255) / 256;
-  std::vector<double> tmp(3 * (size_t)b->nbody);
   for (int w = 0; w < 2; ++w) {
     double* dst = w == 0 ? r : v;
     if (!dst) continue;

@@ -31,9 +31,11 @@ EXPORTS = [
     "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
     "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate", "mstar_accelerations_noalloc",
     "mstar_batch_workspace_bytes", "mstar_batch_init", "mstar_step_batched", "mstar_batch_get_state",
-    "mstar_batch_set_H", "mstar_batch_launch_count", "mstar_batch_free",
+    "mstar_batch_set_H", "mstar_batch_set_schedule", "mstar_batch_get_schedule", "mstar_batch_autotune",
+    "mstar_batch_launch_count", "mstar_batch_free",
 ]
 MSTAR_BATCH_MAX_N = 512
+MSTAR_BATCH_NUM_CLASSES = 7
 MSTAR_NOALLOC_MAX_N = 2048
 
 
@@ -107,6 +109,9 @@ def load():
     L.mstar_step_batched.argtypes = [vp, C.c_double, C.c_int, C.POINTER(mstar_batch_stats)]
     L.mstar_batch_get_state.argtypes = [vp, dp, dp, dp, dp, ip]
     L.mstar_batch_set_H.argtypes = [vp, dp]
+    L.mstar_batch_set_schedule.argtypes = [vp, ip]
+    L.mstar_batch_get_schedule.argtypes = [vp, ip]
+    L.mstar_batch_autotune.argtypes = [vp, C.c_double, C.c_int, ip, C.POINTER(C.c_double)]
     L.mstar_batch_launch_count.argtypes = [vp]
     L.mstar_batch_launch_count.restype = C.c_longlong
     L.mstar_batch_free.argtypes = [vp]
@@ -349,6 +354,26 @@ def mstar_batch_set_H(b, H):
     _check(load().mstar_batch_set_H(b, _ptr(H)), "mstar_batch_set_H")
 
 
+def mstar_batch_set_schedule(b, schedule):
+    sc = np.ascontiguousarray(schedule, dtype=np.int32)
+    if sc.shape != (MSTAR_BATCH_NUM_CLASSES,):
+        raise ValueError(f"schedule needs {MSTAR_BATCH_NUM_CLASSES} entries")
+    _check(load().mstar_batch_set_schedule(b, _ptr(sc)), "mstar_batch_set_schedule")
+
+
+def mstar_batch_get_schedule(b):
+    sc = np.zeros(MSTAR_BATCH_NUM_CLASSES, np.int32)
+    _check(load().mstar_batch_get_schedule(b, _ptr(sc)), "mstar_batch_get_schedule")
+    return sc
+
+
+def mstar_batch_autotune(b, t_end, repeats=2):
+    sc = np.zeros(MSTAR_BATCH_NUM_CLASSES, np.int32)
+    ms = C.c_double()
+    _check(load().mstar_batch_autotune(b, float(t_end), int(repeats), _ptr(sc), C.byref(ms)), "mstar_batch_autotune")
+    return sc, ms.value
+
+
 def mstar_batch_launch_count(b) -> int:
     return load().mstar_batch_launch_count(b)
 
@@ -415,3 +440,13 @@ class Batch:
 
     def set_H(self, H):
         mstar_batch_set_H(self.b, H)
+
+    def set_schedule(self, schedule):
+        mstar_batch_set_schedule(self.b, schedule)
+
+    def schedule(self):
+        return mstar_batch_get_schedule(self.b)
+
+    def autotune(self, t_end, repeats=2):
+        """(schedule, ms of one launch) chosen by the library's autotuner; state unchanged."""
+        return mstar_batch_autotune(self.b, t_end, repeats)

@@ -1,10 +1,10 @@
 """Batched independent systems (mstar_step_batched) against the oracle, system by system.
 
 One launch advances every system by one GBS step attempt (one CTA per system, divisions
-spread over four warps by the greedy recipe of Sec. 4.2). With eta = 1 every attempt is
-accepted, so one launch at a fixed H must reproduce the oracle's single attempt for each
-system (1e-12 relative per system); with eta = 1e-12 repeated launches must land every
-system on t_end with the oracle's end state.
+spread over four groups of 1, 2 or 4 warps by the greedy recipe of Sec. 4.2). With eta = 1
+every attempt is accepted, so one launch at a fixed H must reproduce the oracle's single
+attempt for each system (1e-12 relative per system) under every schedule; with eta = 1e-12
+repeated launches must land every system on t_end with the oracle's end state.
 """
 import math
 
@@ -50,10 +50,17 @@ def step_sizes(systems):
     return np.array(H)
 
 
-def test_one_launch_matches_oracle_attempt():
+SCHEDULES = {"default": None, "g1": [1] * 7, "g2": [2] * 7, "g4": [4] * 7, "mixed": [4, 2, 1, 4, 2, 1, 2]}
+
+
+@pytest.mark.parametrize("name", list(SCHEDULES))
+def test_one_launch_matches_oracle_attempt(name):
     systems = mixed_systems()
     H = step_sizes(systems)
     b = M.Batch(systems, eta_gbs=1.0)
+    if SCHEDULES[name] is not None:
+        b.set_schedule(SCHEDULES[name])
+        assert list(b.schedule()) == SCHEDULES[name]
     b.set_H(H)
     st = b.step(1e9, launches=1)
     assert st["accepted"] == len(systems) and st["failed"] == 0
@@ -102,3 +109,36 @@ def test_batch_rejects_oversize_and_bad_input():
     with pytest.raises(M.MstarError) as e:
         M.Batch([(m, r, v)])
     assert e.value.code == M.MSTAR_ERR_NONFINITE
+
+
+def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
+    systems = mixed_systems()
+    H = step_sizes(systems)
+    b = M.Batch(systems, eta_gbs=1.0)
+    b.set_H(H)
+    before = b.state()
+    sched, ms = b.autotune(1e9, repeats=1)
+    assert ms > 0 and set(sched.tolist()) <= {1, 2, 4}
+    assert list(b.schedule()) == sched.tolist()
+    after = b.state()
+    for key in ("t", "eps", "status"):
+        assert np.array_equal(before[key], after[key])
+    for s in range(len(systems)):
+        assert np.array_equal(before["r"][s], after["r"][s]) and np.array_equal(before["v"][s], after["v"][s])
+    st = b.step(1e9, launches=1)  # the H set above survived the trials
+    assert st["accepted"] == len(systems)
+    S = b.state()
+    for s, (m, r, v) in enumerate(systems):
+        a = O.System(m, r, v).attempt(H[s])
+        assert relerr(S["r"][s], a["r"]) < 1e-12, s
+        assert relerr(S["v"][s], a["v"]) < 1e-12, s
+    b.close()
+
+
+def test_batch_rejects_bad_schedule():
+    b = M.Batch([W.plummer(10, 1)])
+    with pytest.raises(M.MstarError) as e:
+        b.set_schedule([1, 2, 3, 4, 1, 1, 1])
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+    assert list(b.schedule()) == [1, 1, 1, 1, 2, 4, 4]
+    b.close()
