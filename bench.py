@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-subsystems measurement and print its object")
+    ap.add_argument("--no-single-context", action="store_true",
+                    help="skip timing the one-context-per-system path beside the batch")
     return ap.parse_args()
 
 
@@ -251,6 +253,8 @@ def run_batched(args, dev, M, W, torch):
                         "size_classes": "[2,8] [9,16] [17,32] [33,64] [65,128] [129,256] [257,512]",
                         "autotune_launch_ms": tune_ms},
            "launch": "one CUDA graph launch per attempt (one kernel node per group width)"}
+    if args.no_single_context:
+        return out
     # the single-system path, one context per system, on every 128th system
     secs = 0.0
     steps = 0
