@@ -89,6 +89,11 @@ def lib():
             L.orc_integrate.restype = C.c_int
             L.orc_integrate.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(Stats)]
             L.orc_energy.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
+            L.orc_fixed_run.restype = C.c_int
+            L.orc_fixed_run.argtypes = [C.c_void_p, C.c_double, C.c_int]
+            L.orc_fixed_run_tl.restype = C.c_int
+            L.orc_fixed_run_tl.argtypes = [C.c_int, _D, _D, _D, _D, _D, _D, C.POINTER(Params), C.c_double,
+                                           C.c_int, _D, _D, _D, _D, _D, _D]
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_get_threads.restype = C.c_int
             _lib = L
@@ -248,3 +253,23 @@ class System:
         E = C.c_double(); T = C.c_double(); U = C.c_double(); P = np.empty(3); L = np.empty(3)
         lib().orc_energy(self._h, C.byref(E), C.byref(T), C.byref(U), _d(P), _d(L))
         return dict(E=E.value, T=T.value, U=U.value, P=P, L=L)
+
+    def fixed_run(self, H, nsteps):
+        """nsteps GBS steps of fixed fictitious step H, every attempt accepted."""
+        lib().orc_fixed_run(self._h, float(H), int(nsteps))
+
+
+def fixed_run_tl(m, r, v, dm, dr, dv, H, nsteps, params: Params | None = None, **kw):
+    """Tangent-linear of the fixed-step run from the raw inputs (m, r, v) along (dm, dr, dv):
+    dict(r, v, E) of the final state and their directional derivatives dr, dv, dE."""
+    p = params if params is not None else default_params(**kw)
+    m = _f64(m); n = len(m)
+    r = _f64(r, (n, 3)); v = _f64(v, (n, 3))
+    dm = _f64(dm); dr = _f64(dr, (n, 3)); dv = _f64(dv, (n, 3))
+    rf = np.empty((n, 3)); vf = np.empty((n, 3)); drf = np.empty((n, 3)); dvf = np.empty((n, 3))
+    E = C.c_double(); dE = C.c_double()
+    rc = lib().orc_fixed_run_tl(n, _d(m), _d(r), _d(v), _d(dm), _d(dr), _d(dv), C.byref(p), float(H), int(nsteps),
+                                _d(rf), _d(vf), C.byref(E), _d(drf), _d(dvf), C.byref(dE))
+    if rc != 0:
+        raise ValueError(f"orc_fixed_run_tl failed ({rc})")
+    return dict(r=rf, v=vf, E=E.value, dr=drf, dv=dvf, dE=dE.value)

@@ -567,3 +567,207 @@ void orc_energy(const orc_system* s, double* E, double* T, double* U, double P[3
   if (P) for (int k = 0; k < 3; ++k) P[k] = p[k];
   if (L) for (int k = 0; k < 3; ++k) L[k] = l[k];
 }
+
+/* ---------------------------------------------------------------- fixed-step runs */
+
+int orc_fixed_run(orc_system* s, double H, int nsteps) {
+  int n = s->n;
+  size_t n3 = sizeof(double) * 3 * (size_t)n;
+  double* r = (double*)malloc(n3);
+  double* v = (double*)malloc(n3);
+  for (int i = 0; i < nsteps; ++i) {
+    double eps, t;
+    orc_attempt(s, H, &eps, r, v, &t, NULL);
+    orc_set_state(s, t, r, v);
+  }
+  free(r);
+  free(v);
+  return ORC_OK;
+}
+
+/* Tangent-linear (forward-mode derivative) of the fixed-step run, in Cartesian form.
+   Exactly (in real arithmetic) the MST-coordinate step equals the Cartesian one: the
+   edge vectors X = r_v - r_parent are a linear change of variables, the near-pair edge
+   sums equal r_j - r_i, and the rebuild is its inverse plus a shift that is the identity
+   on the centre-of-mass frame. So the derivative of the step is taken here from the
+   Cartesian LogH equations of Sec. 2.1-2.2:
+     D(h): f = h / (T + B), r += f v        with T = sum m |v|^2 / 2
+     K(h): g = h / U,       v += g a        with a, U of Eq. 1-2
+   B = U0 - T0 of the initial COM-frame state (Eq. 1), k_fix leapfrog divisions per step
+   and Aitken-Neville extrapolation (linear in the division results, so the tangents are
+   extrapolated with the same tableau). Every quantity carries its tangent (value, d). */
+
+/* a_i = G sum_j m_j d_ij / |d_ij|^3, U = G sum_{i<j} m_i m_j / |d_ij|, d_ij = r_j - r_i,
+   with tangents for a tangent (dr, dm). */
+static void tl_forces(int n, const double* m, const double* dm, double G, const double* r, const double* dr,
+                      double* a, double* da, double* U, double* dU) {
+  double* ui = (double*)calloc((size_t)n, sizeof(double));
+  double* dui = (double*)calloc((size_t)n, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 8) num_threads(g_threads)
+  for (int i = 0; i < n; ++i) {
+    double ax = 0, ay = 0, az = 0, dax = 0, day = 0, daz = 0, u = 0, du = 0;
+    for (int j = 0; j < n; ++j) {
+      if (j == i) continue;
+      double d[3], dd[3];
+      for (int k = 0; k < 3; ++k) {
+        d[k] = r[3 * j + k] - r[3 * i + k];
+        dd[k] = dr[3 * j + k] - dr[3 * i + k];
+      }
+      double r2 = norm2(d), rr = sqrt(r2), r3 = r2 * rr, r5 = r3 * r2;
+      double dot = (d[0] * dd[0] + d[1] * dd[1]) + d[2] * dd[2];
+      /* d/dx of m_j d / r^3 = dm_j d / r^3 + m_j (dd / r^3 - 3 d (d . dd) / r^5) */
+      ax += m[j] * d[0] / r3;
+      ay += m[j] * d[1] / r3;
+      az += m[j] * d[2] / r3;
+      dax += dm[j] * d[0] / r3 + m[j] * (dd[0] / r3 - 3.0 * d[0] * dot / r5);
+      day += dm[j] * d[1] / r3 + m[j] * (dd[1] / r3 - 3.0 * d[1] * dot / r5);
+      daz += dm[j] * d[2] / r3 + m[j] * (dd[2] / r3 - 3.0 * d[2] * dot / r5);
+      if (j > i) {
+        /* d/dx of m_i m_j / r = (dm_i m_j + m_i dm_j) / r - m_i m_j (d . dd) / r^3 */
+        u += m[j] / rr;
+        du += (dm[i] * m[j] + m[i] * dm[j]) / rr - m[i] * m[j] * dot / r3;
+      }
+    }
+    a[3 * i] = G * ax; a[3 * i + 1] = G * ay; a[3 * i + 2] = G * az;
+    da[3 * i] = G * dax; da[3 * i + 1] = G * day; da[3 * i + 2] = G * daz;
+    ui[i] = m[i] * u;
+    dui[i] = du;
+  }
+  double Us = 0.0, dUs = 0.0;
+  for (int i = 0; i < n; ++i) {
+    Us += G * ui[i];
+    dUs += G * dui[i];
+  }
+  *U = Us;
+  *dU = dUs;
+  free(ui);
+  free(dui);
+}
+
+/* T = sum m |v|^2 / 2 and its tangent sum (dm |v|^2 / 2 + m v . dv) */
+static void tl_kinetic(int n, const double* m, const double* dm, const double* v, const double* dv, double* T,
+                       double* dT) {
+  double t = 0.0, dt = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double v2 = norm2(v + 3 * i);
+    double vdv = (v[3 * i] * dv[3 * i] + v[3 * i + 1] * dv[3 * i + 1]) + v[3 * i + 2] * dv[3 * i + 2];
+    t += m[i] * v2;
+    dt += dm[i] * v2 + 2.0 * m[i] * vdv;
+  }
+  *T = 0.5 * t;
+  *dT = 0.5 * dt;
+}
+
+/* w -= sum m w / M with its tangent: d(sum m w / M) = (sum (dm w + m dw) - (sum m w / M) dM) / M */
+static void tl_com_shift(int n, const double* m, const double* dm, double* w, double* dw) {
+  double M = 0.0, dM = 0.0, c[3] = {0, 0, 0}, dc[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    M += m[i];
+    dM += dm[i];
+    for (int k = 0; k < 3; ++k) {
+      c[k] += m[i] * w[3 * i + k];
+      dc[k] += dm[i] * w[3 * i + k] + m[i] * dw[3 * i + k];
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    c[k] /= M;
+    dc[k] = (dc[k] - c[k] * dM) / M;
+  }
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      w[3 * i + k] -= c[k];
+      dw[3 * i + k] -= dc[k];
+    }
+}
+
+typedef struct {
+  int n;
+  const double *m, *dm;
+  double G, B, dB;
+  double *r, *v, *dr, *dv, *a, *da;
+} tl_div;
+
+static void tl_drift(void* c, double h) {
+  tl_div* d = (tl_div*)c;
+  double T, dT;
+  tl_kinetic(d->n, d->m, d->dm, d->v, d->dv, &T, &dT);
+  double f = h / (T + d->B);
+  double df = -h * (dT + d->dB) / ((T + d->B) * (T + d->B));
+  for (int i = 0; i < 3 * d->n; ++i) {
+    d->dr[i] += df * d->v[i] + f * d->dv[i];
+    d->r[i] += f * d->v[i];
+  }
+}
+
+static void tl_kick(void* c, double h) {
+  tl_div* d = (tl_div*)c;
+  double U, dU;
+  tl_forces(d->n, d->m, d->dm, d->G, d->r, d->dr, d->a, d->da, &U, &dU);
+  double g = h / U, dg = -h * dU / (U * U);
+  for (int i = 0; i < 3 * d->n; ++i) {
+    d->dv[i] += dg * d->a[i] + g * d->da[i];
+    d->v[i] += g * d->a[i];
+  }
+}
+
+int orc_fixed_run_tl(int n, const double* m_in, const double* r_in, const double* v_in, const double* dm_in,
+                     const double* dr_in, const double* dv_in, const orc_params* p, double H, int nsteps,
+                     double* r_f, double* v_f, double* E_f, double* dr_f, double* dv_f, double* dE_f) {
+  if (n < 2 || !p || p->k_fix < 2 || nsteps < 0) return ORC_ERR_ARG;
+  int kf = p->k_fix;
+  size_t n3 = 3 * (size_t)n, b3 = sizeof(double) * n3, nv = 6 * (size_t)n;
+  double* m = (double*)malloc(sizeof(double) * (size_t)n);
+  double* dm = (double*)malloc(sizeof(double) * (size_t)n);
+  memcpy(m, m_in, sizeof(double) * (size_t)n);
+  memcpy(dm, dm_in, sizeof(double) * (size_t)n);
+  double *r = (double*)malloc(b3), *v = (double*)malloc(b3), *dr = (double*)malloc(b3), *dv = (double*)malloc(b3);
+  memcpy(r, r_in, b3); memcpy(v, v_in, b3); memcpy(dr, dr_in, b3); memcpy(dv, dv_in, b3);
+  tl_com_shift(n, m, dm, r, dr);
+  tl_com_shift(n, m, dm, v, dv);
+  tl_div d;
+  d.n = n; d.m = m; d.dm = dm; d.G = p->G;
+  d.a = (double*)malloc(b3); d.da = (double*)malloc(b3);
+  d.r = (double*)malloc(b3); d.v = (double*)malloc(b3); d.dr = (double*)malloc(b3); d.dv = (double*)malloc(b3);
+  {
+    double U, dU, T, dT;
+    tl_forces(n, m, dm, p->G, r, dr, d.a, d.da, &U, &dU);
+    tl_kinetic(n, m, dm, v, dv, &T, &dT);
+    d.B = U - T;  /* B = -H with H = T - U (Eq. 1) */
+    d.dB = dU - dT;
+  }
+  int* nseq = (int*)malloc(sizeof(int) * (size_t)kf);
+  double* S = (double*)malloc(sizeof(double) * nv * (size_t)kf);
+  double* dS = (double*)malloc(sizeof(double) * nv * (size_t)kf);
+  double* Tkk = (double*)malloc(sizeof(double) * nv);
+  double* Tprev = (double*)malloc(sizeof(double) * nv);
+  for (int step = 0; step < nsteps; ++step) {
+    for (int k = 0; k < kf; ++k) {
+      nseq[k] = 2 * (k + 1);
+      memcpy(d.r, r, b3); memcpy(d.v, v, b3); memcpy(d.dr, dr, b3); memcpy(d.dv, dv, b3);
+      orc_dkd(nseq[k], H, tl_drift, tl_kick, &d);
+      memcpy(S + (size_t)k * nv, d.r, b3);
+      memcpy(S + (size_t)k * nv + n3, d.v, b3);
+      memcpy(dS + (size_t)k * nv, d.dr, b3);
+      memcpy(dS + (size_t)k * nv + n3, d.dv, b3);
+    }
+    orc_neville(kf, nseq, (int)nv, S, Tkk, Tprev);
+    memcpy(r, Tkk, b3); memcpy(v, Tkk + n3, b3);
+    orc_neville(kf, nseq, (int)nv, dS, Tkk, Tprev);
+    memcpy(dr, Tkk, b3); memcpy(dv, Tkk + n3, b3);
+  }
+  {
+    double U, dU, T, dT;
+    tl_forces(n, m, dm, p->G, r, dr, d.a, d.da, &U, &dU);
+    tl_kinetic(n, m, dm, v, dv, &T, &dT);
+    if (E_f) *E_f = T - U;
+    if (dE_f) *dE_f = dT - dU;
+  }
+  if (r_f) memcpy(r_f, r, b3);
+  if (v_f) memcpy(v_f, v, b3);
+  if (dr_f) memcpy(dr_f, dr, b3);
+  if (dv_f) memcpy(dv_f, dv, b3);
+  free(m); free(dm); free(r); free(v); free(dr); free(dv);
+  free(d.a); free(d.da); free(d.r); free(d.v); free(d.dr); free(d.dv);
+  free(nseq); free(S); free(dS); free(Tkk); free(Tprev);
+  return ORC_OK;
+}

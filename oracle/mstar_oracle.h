@@ -98,6 +98,17 @@ void orc_set_state(orc_system* s, double t, const double* r, const double* v);
 int orc_integrate(orc_system* s, double t_end, int max_steps, orc_stats* st);
 /* Energy diagnostics of the current state: E = T - U (Eq. 1), momentum P, angular momentum L. */
 void orc_energy(const orc_system* s, double* E, double* T, double* U, double P[3], double L[3]);
+/* Fixed-step run: nsteps GBS steps of fictitious step H from the current state, every
+   attempt accepted (the error test and step control of Sec. 2.3-2.4 switched off). */
+int orc_fixed_run(orc_system* s, double H, int nsteps);
+/* Tangent-linear of the fixed-step run from the initial inputs (m, r, v; before the COM
+   shift) along (dm, dr, dv): the final state (r_f, v_f, E_f = T - U) and its directional
+   derivatives. Cartesian form of the same LogH leapfrog + extrapolation (equal to the MST
+   form in real arithmetic); B = U0 - T0 carries its tangent. Pinned: central finite
+   differences of orc_fixed_run, translation invariance, rotation equivariance. */
+int orc_fixed_run_tl(int n, const double* m, const double* r, const double* v, const double* dm,
+                     const double* dr, const double* dv, const orc_params* p, double H, int nsteps,
+                     double* r_f, double* v_f, double* E_f, double* dr_f, double* dv_f, double* dE_f);
 /* Threads used by the pair loop (OpenMP over i; results do not depend on it). */
 void orc_set_threads(int nthreads);
 int orc_get_threads(void);
