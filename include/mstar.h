@@ -265,6 +265,33 @@ MSTAR_API void mstar_batch_free(mstar_batch* b);
 MSTAR_API int mstar_accelerations_noalloc(int n, const double* m, const double* r, double G, double* a,
                                           double* U, void* cuda_stream);
 
+
+/* ---- Adjoint of a fixed-step run (no counterpart in the paper; reverse-mode derivative
+   of the method of Sec. 2-4 with the step control switched off). */
+
+typedef struct mstar_adjoint mstar_adjoint;
+
+/* Forward pass: nsteps GBS steps of fixed fictitious step H (k_fix divisions each, every
+   attempt accepted: no error test, no step-size control or end-time clamp) from the state
+   that mstar_init set up; the context must not have been stepped or given a new state
+   since (INVALID_ARG otherwise). Keeps (r, v) of every `checkpoint_every`-th step start in
+   device memory owned by *out (NOMEM if it cannot be allocated). The context ends at the
+   final state. Errors as mstar_step; on error *out is NULL. */
+MSTAR_API int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int checkpoint_every, mstar_adjoint** out);
+
+/* Reverse sweep of the run recorded by `a` for the loss L whose gradients with respect to
+   the final state are g_r = dL/dr_f, g_v = dL/dv_f (n x 3, host or device; NULL = 0) and
+   g_E = dL/dE_f (E_f = T - U of the final state, Eq. 1). Writes dL/dm (n), dL/dr, dL/dv
+   (n x 3) with respect to the masses, positions and velocities given to mstar_init,
+   through the centre-of-mass shift and B = U0 - T0 (any output may be NULL). Each segment
+   of checkpoint_every steps is recomputed from its checkpoint with its trajectory
+   recorded; the transposed substeps then run in reverse, one VJP pair loop per kick. The
+   MST of each step is held fixed (its topology is piecewise constant). The context ends at
+   the final state of the run. May be called again with other loss gradients. */
+MSTAR_API int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g_r, const double* g_v, double g_E,
+                                 double* d_r, double* d_v, double* d_m);
+MSTAR_API void mstar_adjoint_free(mstar_adjoint* a);
+
 #ifdef __cplusplus
 }
 #endif

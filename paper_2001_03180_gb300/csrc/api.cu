@@ -225,14 +225,31 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
 int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
   const int K = c->K;
   const size_t st = (size_t)3 * c->npad;
+  AdjTraj* tr = c->traj;
+  const size_t lvl = (size_t)K * st, nsc = (size_t)(K + 1) * kScal;
+  auto save = [&](double* dst, const double* src, size_t count) {
+    return cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, c->stream);
+  };
   CK(launch_init_drift(c, H));
+  if (tr) {
+    CK(save(tr->SC, c->d.sc, nsc));
+    CK(save(tr->v0, c->d.v, st));
+  }
   for (int tau = 1; tau <= 2 * K; ++tau) {
     const int lo = (tau + 1) / 2 - 1;  // divisions with n_k >= tau kick and drift
     CK(launch_forces(c, lo, K, c->p.n_d));
+    if (tr) {
+      CK(save(tr->R + (tau - 1) * lvl + lo * st, c->d.sr + lo * st, (K - lo) * st));
+      CK(save(tr->A + (tau - 1) * lvl + lo * st, c->d.sa + lo * st, (K - lo) * st));
+    }
     CK(launch_kick(c, lo, K, H));
     CK(launch_rebuild(c, c->d.sV + lo * st, c->d.sv + lo * st, st, K - lo, 1, c->d.Tblk + (size_t)lo * c->nblk,
                       c->d.comblk + (size_t)lo * c->nblk * 3));
     CK(launch_drift(c, lo, K, H, tau));
+    if (tr) {
+      CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
+      CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
+    }
     const int lo2 = tau / 2;  // divisions with n_k > tau need positions for the next kick
     if (lo2 < K)
       CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
@@ -276,6 +293,20 @@ int extract_out(mstar_ctx* c, double* r_out, double* v_out, const double* Xsrc, 
 // --------------------------------------------------------------------------- internals
 
 namespace mstar {
+
+int step_prepare(mstar_ctx* c, double* U0, double* T0) { return prepare_step(c, U0, T0); }
+int step_attempt(mstar_ctx* c, double H, double* eps, double* tnew) { return run_attempt(c, H, eps, tnew); }
+int step_accept(mstar_ctx* c) {
+  c->at_init = false;
+  return accept_state(c);
+}
+int vectors_in(mstar_ctx* c, const double* src, double* planes) { return load_vectors(c, stage_of(c), src, planes); }
+int vectors_out(mstar_ctx* c, const double* planes, double* dst) {
+  const int rc = store_vectors(c, stage_of(c), planes, dst);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(c->stream));
+  return MSTAR_OK;
+}
 
 int choose_tile_warps(int n) { return n <= 512 ? 1 : 4; }
 
@@ -474,6 +505,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   c->H = 0.0;
   c->force_evals = 0;
   c->mst_valid = false;
+  c->at_init = true;
   *out = c;
   return MSTAR_OK;
 }
@@ -504,6 +536,7 @@ int mstar_set_state(mstar_ctx* c, double t, const double* r, const double* v) {
   CK(cudaStreamSynchronize(c->stream));
   c->t = t;
   c->mst_valid = false;
+  c->at_init = false;
   return MSTAR_OK;
 }
 
@@ -594,6 +627,7 @@ int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) 
       Hs *= 0.5;
     }
     if ((rc = accept_state(c))) break;
+    c->at_init = false;
     c->t = tn;
     {
       // Eq. hnext with k = k_fix

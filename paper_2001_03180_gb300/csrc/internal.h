@@ -57,6 +57,19 @@ struct mstar_prof_rec {
   int nsl;
 };
 
+namespace mstar {
+// Device buffers that receive one GBS attempt's trajectory when a context's `traj` is set
+// (the reverse sweep of the fixed-step adjoint linearises around it). Level tau = 1..2K
+// of the attempt has slots lo(tau) = ceil(tau/2) - 1 .. K-1 active (slot s: n = 2(s+1)).
+struct AdjTraj {
+  double* R;   // [2K][K][3 npad] Cartesian positions at which the forces of level tau act
+  double* A;   // [2K][K][3 npad] those accelerations (G included)
+  double* Vv;  // [2K][K][3 npad] Cartesian velocities after the kick of level tau
+  double* SC;  // [2K + 1][(K + 1) kScal] slot scalars after the drift of level tau (0: first drift)
+  double* v0;  // [3 npad] Cartesian velocity of the step start
+};
+}  // namespace mstar
+
 struct mstar_ctx {
   int n = 0, npad = 0, K = 0, nslots = 0;
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
@@ -73,6 +86,8 @@ struct mstar_ctx {
   // host-side scalar state (the step control of Sec. 2.3-2.4 runs on the host)
   double t = 0.0, B = 0.0, H = 0.0, Mtot = 0.0;
   bool mst_valid = false;  // the MST/edge buffers describe the current state
+  bool at_init = false;    // the state is still the one mstar_init set up (no step taken)
+  mstar::AdjTraj* traj = nullptr;  // when set, run_attempt records its trajectory here
   long long launches = 0;
   long long force_evals = 0;
   // profiling of the tiled pair kernel: event pairs recorded around each launch, read
@@ -115,6 +130,15 @@ cudaError_t launch_com_shift(mstar_ctx* c, double* w, double* Tblk);
 
 // api.cu
 void prof_begin(mstar_ctx* c);
+// The pieces of one GBS step (MSTAR_OK or an MSTAR_ERR_* code): the MST and derivative
+// information of the step start, one attempt with fictitious step H (records the
+// trajectory when c->traj is set), and the acceptance of the extrapolated state.
+int step_prepare(mstar_ctx* c, double* U0, double* T0);
+int step_attempt(mstar_ctx* c, double H, double* eps, double* tnew);
+int step_accept(mstar_ctx* c);
+// n x 3 arrays (host or device) to and from three SoA planes of length npad.
+int vectors_in(mstar_ctx* c, const double* src, double* planes);
+int vectors_out(mstar_ctx* c, const double* planes, double* dst);
 void prof_end(mstar_ctx* c, int nsl);
 
 }  // namespace mstar

@@ -33,6 +33,7 @@ EXPORTS = [
     "mstar_batch_workspace_bytes", "mstar_batch_init", "mstar_step_batched", "mstar_batch_get_state",
     "mstar_batch_set_H", "mstar_batch_set_schedule", "mstar_batch_get_schedule", "mstar_batch_autotune",
     "mstar_batch_launch_count", "mstar_batch_free",
+    "mstar_adjoint_forward", "mstar_step_adjoint", "mstar_adjoint_free",
 ]
 MSTAR_BATCH_MAX_N = 512
 MSTAR_BATCH_NUM_CLASSES = 7
@@ -116,6 +117,10 @@ def load():
     L.mstar_batch_launch_count.restype = C.c_longlong
     L.mstar_batch_free.argtypes = [vp]
     L.mstar_batch_free.restype = None
+    L.mstar_adjoint_forward.argtypes = [vp, C.c_double, C.c_int, C.c_int, C.POINTER(vp)]
+    L.mstar_step_adjoint.argtypes = [vp, vp, dp, dp, C.c_double, dp, dp, dp]
+    L.mstar_adjoint_free.argtypes = [vp]
+    L.mstar_adjoint_free.restype = None
     _lib = L
     return L
 
@@ -450,3 +455,111 @@ class Batch:
     def autotune(self, t_end, repeats=2):
         """(schedule, ms of one launch) chosen by the library's autotuner; state unchanged."""
         return mstar_batch_autotune(self.b, t_end, repeats)
+
+
+# ---------------------------------------------------------------- adjoint of a fixed-step run
+
+def mstar_adjoint_forward(ctx, H, nsteps, checkpoint_every):
+    a = C.c_void_p()
+    _check(load().mstar_adjoint_forward(ctx, float(H), int(nsteps), int(checkpoint_every), C.byref(a)),
+           "mstar_adjoint_forward")
+    return a
+
+
+def mstar_step_adjoint(ctx, a, g_r=None, g_v=None, g_E=0.0, d_r=None, d_v=None, d_m=None):
+    _check(load().mstar_step_adjoint(ctx, a, _ptr(g_r), _ptr(g_v), float(g_E), _ptr(d_r), _ptr(d_v), _ptr(d_m)),
+           "mstar_step_adjoint")
+
+
+def mstar_adjoint_free(a):
+    if a:
+        load().mstar_adjoint_free(a)
+
+
+class FixedRun:
+    """nsteps GBS steps of fixed fictitious step H from (m, r, v) (numpy arrays or float64
+    torch tensors, host or device), with checkpoints for the reverse sweep. `final` holds
+    r, v (n x 3) and E of the final state; backward() gives the gradients of a loss with
+    respect to m, r, v from its gradients with respect to the final r, v and E."""
+
+    def __init__(self, m, r, v, H, nsteps, checkpoint_every=10, device=None, **params):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libmstar needs a CUDA GPU")
+        load()
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        t = lambda x, shape: torch.as_tensor(x, dtype=torch.float64).reshape(shape).contiguous()  # noqa: E731
+        n = int(torch.as_tensor(m).numel())
+        self.n = n
+        m, r, v = t(m, (n,)), t(r, (n, 3)), t(v, (n, 3))
+        self.p = mstar_default_params(**params)
+        nbytes = mstar_workspace_bytes(n, self.p)
+        if nbytes == 0:
+            raise MstarError(MSTAR_ERR_INVALID_ARG, "mstar_workspace_bytes")
+        self.a = None
+        self.ctx = None
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            ptr = self.ws.data_ptr() + (-self.ws.data_ptr()) % 256
+            self.stream = torch.cuda.current_stream(self.device)
+            ctx = C.c_void_p()
+            _check(load().mstar_init(C.byref(ctx), n, _ptr(m), _ptr(r), _ptr(v), C.byref(self.p), C.c_void_p(ptr),
+                                     nbytes, C.c_void_p(self.stream.cuda_stream)), "mstar_init")
+            self.ctx = ctx
+            self.a = mstar_adjoint_forward(self.ctx, H, nsteps, checkpoint_every)
+            rf = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+            vf = torch.empty((n, 3), dtype=torch.float64, device=self.device)
+            tf = mstar_get_state(self.ctx, rf, vf)
+            E, T, U = mstar_energy(self.ctx, np.empty(3), np.empty(3))
+        self.final = dict(r=rf, v=vf, E=E, t=tf)
+
+    def backward(self, g_r=None, g_v=None, g_E=0.0):
+        torch = self.torch
+        prep = lambda g: None if g is None else torch.as_tensor(g, dtype=torch.float64, device=self.device).reshape(  # noqa: E731
+            self.n, 3).contiguous()
+        g_r, g_v = prep(g_r), prep(g_v)
+        d_r = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        d_v = torch.empty((self.n, 3), dtype=torch.float64, device=self.device)
+        d_m = torch.empty((self.n,), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            mstar_step_adjoint(self.ctx, self.a, g_r, g_v, float(g_E), d_r, d_v, d_m)
+        return d_m, d_r, d_v
+
+    def close(self):
+        if getattr(self, "a", None):
+            mstar_adjoint_free(self.a)
+            self.a = None
+        if getattr(self, "ctx", None):
+            mstar_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        self.close()
+
+
+def fixed_run(m, r, v, H, nsteps, checkpoint_every=10, **params):
+    """Differentiable fixed-step run: (r_f, v_f, E_f) = run(m, r, v) as torch tensors on the
+    GPU; gradients flow to m, r, v through the library's reverse sweep."""
+    import torch
+
+    class _FixedRunFn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, m_, r_, v_):
+            run = FixedRun(m_.detach(), r_.detach(), v_.detach(), H, nsteps, checkpoint_every,
+                           device=r_.device if r_.is_cuda else None, **params)
+            fctx.run = run
+            fctx.in_device = r_.device
+            E = torch.tensor(run.final["E"], dtype=torch.float64, device=run.device)
+            return run.final["r"].clone(), run.final["v"].clone(), E
+
+        @staticmethod
+        def backward(fctx, g_r, g_v, g_E):
+            run = fctx.run
+            d_m, d_r, d_v = run.backward(g_r, g_v, 0.0 if g_E is None else float(g_E))
+            dev = fctx.in_device
+            return d_m.to(dev), d_r.to(dev), d_v.to(dev)
+
+    t = lambda x: torch.as_tensor(x, dtype=torch.float64)  # noqa: E731
+    return _FixedRunFn.apply(t(m), t(r), t(v))
