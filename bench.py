@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-subsystems measurement and print its object")
+    ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-single-context", action="store_true",
                     help="skip timing the one-context-per-system path beside the batch")
     return ap.parse_args()
@@ -272,6 +273,55 @@ def run_batched(args, dev, M, W, torch):
     return out
 
 
+ADJOINT_DESC = ("Plummer N=256 (seed 4), fixed fictitious step H = the first accepted step of the step control "
+                "(ds = q U dt with t_end = 1, halved until eps <= 1e-12), k_fix=8, 100 steps, checkpoints every 10; "
+                "loss w_r.r_f + w_v.v_f + w_E E_f with seeded weights")
+
+
+def first_accepted_H(M, m, r, v, dev):
+    g = M.Integrator(m, r, v, device=dev)
+    _, U = g.accelerations()
+    H = 0.1 * U
+    for _ in range(60):
+        if g.attempt(H)["eps"] <= 1e-12:
+            break
+        H *= 0.5
+    g.close()
+    return H
+
+
+def run_adjoint(args, dev, M, W, torch):
+    """Adjoint of the fixed-step run: wall time of the checkpointed forward and of the
+    reverse sweep (which recomputes each segment once), and their ratio."""
+    m, r, v = W.workload("plummer256")
+    n = len(m)
+    H = first_accepted_H(M, m, r, v, dev)
+    st = W.Stream(4, 5)
+    w_r = (st.uniform(3 * n) - 0.5).reshape(n, 3)
+    w_v = (st.uniform(3 * n) - 0.5).reshape(n, 3)
+    steps, every = 100, 10
+    fw, bw = [], []
+    for rep in range(3):  # the first repetition warms up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        run = M.FixedRun(m, r, v, H, steps, checkpoint_every=every, device=dev)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        run.backward(w_r, w_v, 0.7)
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        run.close()
+        if rep:
+            fw.append(t1 - t0)
+            bw.append(t2 - t1)
+    f, b = min(fw), min(bw)
+    return {"workload": ADJOINT_DESC, "n": n, "steps": steps, "checkpoint_every": every, "H": H,
+            "forward_ms": f * 1e3, "adjoint_ms": b * 1e3, "adjoint_to_forward": b / f,
+            "note": "wall time with the stream synchronised; the forward includes context set-up and checkpoints, "
+                    "the adjoint recomputes each segment once (a second forward) and runs one VJP pair loop "
+                    "per kick"}
+
+
 def run_mstar(args):
     import numpy as np
     import torch
@@ -402,6 +452,10 @@ def run_mstar(args):
     if rank == 0 and not args.no_batched:
         with torch.cuda.stream(stream):
             batched = run_batched(args, dev, M, W, torch)
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        with torch.cuda.stream(stream):
+            adjoint = run_adjoint(args, dev, M, W, torch)
 
     if rank == 0:
         out = {"metric": "FP64 pair-forces/s", "value": value, "unit": "pair-forces/s", "n_gpus": world,
@@ -413,7 +467,8 @@ def run_mstar(args):
                           "parallelism": "replicas" if world > 1 else "single"},
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-               "gpu_launches": launches, "clocks": clocks, "batched": batched}
+               "gpu_launches": launches, "clocks": clocks, "batched": batched,
+               "adjoint": adjoint}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:
