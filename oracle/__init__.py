@@ -39,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("eta", C.c_double), ("a_gbs", C.c_double), ("fac_min", C.c_double),
                 ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
                 ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int),
-                ("max_halvings", C.c_int), ("max_time_iter", C.c_int)]
+                ("max_halvings", C.c_int), ("max_time_iter", C.c_int), ("mst_method", C.c_int),
+                ("mst_leaf", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -66,6 +67,8 @@ def lib():
             L.orc_com_shift.argtypes = [C.c_int, _D, _D]
             L.orc_prim.restype = C.c_int
             L.orc_prim.argtypes = [C.c_int, _D, _I, _I, _I]
+            L.orc_dc_mst.restype = C.c_int
+            L.orc_dc_mst.argtypes = [C.c_int, _D, C.c_int, _I, _I, _I, _I, _I]
             L.orc_is_near.restype = C.c_int
             L.orc_is_near.argtypes = [_I, _I, C.c_int, C.c_int, C.c_int]
             L.orc_near_sep.argtypes = [_I, _I, _D, C.c_int, C.c_int, _D]
@@ -149,6 +152,16 @@ def prim(r):
     parent = np.empty(n, np.int32); level = np.empty(n, np.int32); order = np.empty(n, np.int32)
     root = lib().orc_prim(n, _d(r), _i(parent), _i(level), _i(order))
     return root, parent, level, order
+
+
+def dc_mst(r, leaf_cap=0):
+    """Divide-and-conquer spanning tree (Sec. 3.3): (root, parent, level, order, leaf_of, nleaf)."""
+    r = _f64(r, (-1, 3))
+    n = r.shape[0]
+    parent = np.empty(n, np.int32); level = np.empty(n, np.int32); order = np.empty(n, np.int32)
+    leaf = np.empty(n, np.int32); nleaf = np.zeros(1, np.int32)
+    root = lib().orc_dc_mst(n, _d(r), int(leaf_cap), _i(parent), _i(level), _i(order), _i(leaf), _i(nleaf))
+    return root, parent, level, order, leaf, int(nleaf[0])
 
 
 def is_near(parent, level, i, j, n_d=2) -> bool:

@@ -42,6 +42,8 @@ void orc_params_default(orc_params* p) {
   p->n_d = 2;
   p->max_halvings = 30;
   p->max_time_iter = 8;
+  p->mst_method = 0;
+  p->mst_leaf = 0;
 }
 
 /* ---------------------------------------------------------------- energies (Eq. 1) */
@@ -125,6 +127,249 @@ int orc_prim(int n, const double* r, int* parent, int* level, int* order) {
   }
   free(key);
   free(in_tree);
+  return root;
+}
+
+/* ---------------------------------------------------------------- divide-and-conquer MST (Sec. 3.3) */
+
+#define DC_DEPTH 16
+
+typedef struct {
+  double d2;
+  int i, j; /* i in the lower-numbered subgraph */
+} dc_edge;
+
+/* lexicographic (d2, i, j) */
+static int dc_less(dc_edge a, dc_edge b) {
+  if (a.d2 != b.d2) return a.d2 < b.d2;
+  if (a.i != b.i) return a.i < b.i;
+  return a.j < b.j;
+}
+
+typedef struct {
+  int nleaf;
+  int* leaf_of;     /* subgraph of each body */
+  int* leaf_start;  /* bodies of subgraph g: members[leaf_start[g] .. leaf_start[g+1]) */
+  int* members;     /* ascending body index within each subgraph */
+} dc_tree;
+
+/* The octree partition into about `target` subgraphs: starting from the bounding cube,
+   the cell holding the most bodies (the first in Morton order on ties) is replaced by its
+   non-empty children, until there are at least `target` cells or the most populous cell
+   cannot be split (one body, or depth DC_DEPTH). Children are ordered by their Morton
+   digit (x, y, z bits from most to least significant), so the cells stay in Morton order.
+   A cell is the range [lo, hi) of the bodies sorted by (key, index). */
+typedef struct {
+  int depth, lo, hi;
+} dc_cell;
+
+static int dc_partition(int n, const unsigned long long* skey, int target, dc_cell* cells) {
+  int nc = 1;
+  cells[0].depth = 0; cells[0].lo = 0; cells[0].hi = n;
+  while (nc < target) {
+    int best = 0;
+    for (int c = 1; c < nc; ++c)
+      if (cells[c].hi - cells[c].lo > cells[best].hi - cells[best].lo) best = c;
+    dc_cell b = cells[best];
+    if (b.hi - b.lo <= 1 || b.depth == DC_DEPTH) break;
+    int shift = 3 * (DC_DEPTH - b.depth - 1);
+    dc_cell kids[8];
+    int nk = 0, p = b.lo;
+    for (int dgt = 0; dgt < 8; ++dgt) {
+      int q = p;
+      while (q < b.hi && (int)((skey[q] >> shift) & 7u) == dgt) ++q;
+      if (q > p) { kids[nk].depth = b.depth + 1; kids[nk].lo = p; kids[nk].hi = q; ++nk; }
+      p = q;
+    }
+    for (int c = nc - 1; c > best; --c) cells[c + nk - 1] = cells[c];
+    for (int k = 0; k < nk; ++k) cells[best + k] = kids[k];
+    nc += nk - 1;
+  }
+  return nc;
+}
+
+int orc_dc_mst(int n, const double* r, int nsub, int* parent, int* level, int* order, int* leaf_of_out,
+               int* nleaf_out) {
+  /* root as for Prim: the body closest to the centre of mass, lowest index on ties */
+  int root = 0;
+  double best = norm2(r);
+  for (int i = 1; i < n; ++i) {
+    double d = norm2(r + 3 * i);
+    if (d < best) { best = d; root = i; }
+  }
+  int target = nsub > 0 ? nsub : (int)ceil(sqrt((double)n));
+  /* bounding cube: centre of the per-axis extent, half-size of the largest extent */
+  double mn[3], mx[3], c0[3], hs = 0.0;
+  for (int k = 0; k < 3; ++k) { mn[k] = r[k]; mx[k] = r[k]; }
+  for (int i = 1; i < n; ++i)
+    for (int k = 0; k < 3; ++k) {
+      if (r[3 * i + k] < mn[k]) mn[k] = r[3 * i + k];
+      if (r[3 * i + k] > mx[k]) mx[k] = r[3 * i + k];
+    }
+  for (int k = 0; k < 3; ++k) {
+    c0[k] = (mn[k] + mx[k]) * 0.5;
+    double e = (mx[k] - mn[k]) * 0.5;
+    if (e > hs) hs = e;
+  }
+  /* Morton key of the cell path: at each depth the child is chosen by x >= centre */
+  unsigned long long* key = (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)n);
+  for (int i = 0; i < n; ++i) {
+    double c[3] = {c0[0], c0[1], c0[2]}, h = hs;
+    unsigned long long kk = 0;
+    for (int d = 0; d < DC_DEPTH; ++d) {
+      h = h * 0.5;
+      unsigned bits = 0;
+      for (int k = 0; k < 3; ++k) {
+        int b = r[3 * i + k] >= c[k];
+        bits = (bits << 1) | (unsigned)b;
+        c[k] = b ? c[k] + h : c[k] - h;
+      }
+      kk = (kk << 3) | bits;
+    }
+    key[i] = kk;
+  }
+  /* bodies sorted by (key, index): each cell of the partition is a contiguous range */
+  int* sorted = (int*)malloc(sizeof(int) * (size_t)n);
+  for (int i = 0; i < n; ++i) sorted[i] = i;
+  for (int a = 1; a < n; ++a) { /* insertion sort by (key, index) */
+    int x = sorted[a], b = a - 1;
+    while (b >= 0 && (key[sorted[b]] > key[x] || (key[sorted[b]] == key[x] && sorted[b] > x))) {
+      sorted[b + 1] = sorted[b];
+      --b;
+    }
+    sorted[b + 1] = x;
+  }
+  unsigned long long* skey = (unsigned long long*)malloc(sizeof(unsigned long long) * (size_t)n);
+  for (int q = 0; q < n; ++q) skey[q] = key[sorted[q]];
+  dc_cell* cells = (dc_cell*)malloc(sizeof(dc_cell) * (size_t)(n + 8));
+  int ncell = dc_partition(n, skey, target, cells);
+  dc_tree t;
+  t.leaf_of = (int*)malloc(sizeof(int) * (size_t)n);
+  t.leaf_start = (int*)malloc(sizeof(int) * (size_t)(n + 1));
+  t.members = (int*)malloc(sizeof(int) * (size_t)n);
+  t.nleaf = ncell;
+  for (int g = 0; g < ncell; ++g) {
+    t.leaf_start[g] = cells[g].lo;
+    /* members of the subgraph in ascending body index */
+    int cnt = cells[g].hi - cells[g].lo;
+    for (int q = 0; q < cnt; ++q) t.members[cells[g].lo + q] = sorted[cells[g].lo + q];
+    for (int a = 1; a < cnt; ++a) {
+      int* mm = t.members + cells[g].lo;
+      int x = mm[a], b = a - 1;
+      while (b >= 0 && mm[b] > x) { mm[b + 1] = mm[b]; --b; }
+      mm[b + 1] = x;
+    }
+    for (int q = 0; q < cnt; ++q) t.leaf_of[t.members[cells[g].lo + q]] = g;
+  }
+  t.leaf_start[ncell] = n;
+  free(sorted); free(skey); free(cells);
+  int ng = t.nleaf;
+  int* eu = (int*)malloc(sizeof(int) * (size_t)n);
+  int* ev = (int*)malloc(sizeof(int) * (size_t)n);
+  int ne = 0;
+  /* Prim's algorithm inside every subgraph (complete graph on its bodies), from its lowest
+     index; keys replaced only by strictly smaller distances; argmin lowest index */
+  double* kd = (double*)malloc(sizeof(double) * (size_t)n);
+  int* kp = (int*)malloc(sizeof(int) * (size_t)n);
+  char* in = (char*)calloc((size_t)n, 1);
+  for (int g = 0; g < ng; ++g) {
+    const int* mem = t.members + t.leaf_start[g];
+    int cnt = t.leaf_start[g + 1] - t.leaf_start[g];
+    for (int q = 0; q < cnt; ++q) { kd[mem[q]] = INFINITY; kp[mem[q]] = -1; }
+    int u = mem[0];
+    in[u] = 1;
+    for (int it = 1; it < cnt; ++it) {
+      for (int q = 0; q < cnt; ++q) {
+        int v = mem[q];
+        if (in[v]) continue;
+        double d = w2(r, u, v);
+        if (d < kd[v]) { kd[v] = d; kp[v] = u; }
+      }
+      int nx = -1;
+      for (int q = 0; q < cnt; ++q) {
+        int v = mem[q];
+        if (in[v]) continue;
+        if (nx < 0 || kd[v] < kd[nx]) nx = v;
+      }
+      in[nx] = 1;
+      eu[ne] = kp[nx]; ev[ne] = nx; ++ne;
+      u = nx;
+    }
+  }
+  free(kd); free(kp); free(in);
+  /* meta-graph: subgraphs contracted to vertices; the weight of (a, b) is the cheapest
+     edge between them (cut property), ties by the lowest (i in a, j in b) */
+  dc_edge* W = (dc_edge*)malloc(sizeof(dc_edge) * (size_t)ng * (size_t)ng);
+  for (int a = 0; a < ng; ++a)
+    for (int b = a + 1; b < ng; ++b) {
+      dc_edge e = {INFINITY, -1, -1};
+      for (int p = t.leaf_start[a]; p < t.leaf_start[a + 1]; ++p)
+        for (int q = t.leaf_start[b]; q < t.leaf_start[b + 1]; ++q) {
+          dc_edge c = {w2(r, t.members[p], t.members[q]), t.members[p], t.members[q]};
+          if (e.i < 0 || dc_less(c, e)) e = c;
+        }
+      W[(size_t)a * ng + b] = e;
+      W[(size_t)b * ng + a] = e;
+    }
+  /* Prim's algorithm on the meta-graph from subgraph 0 */
+  if (ng > 1) {
+    dc_edge* key2 = (dc_edge*)malloc(sizeof(dc_edge) * (size_t)ng);
+    char* in2 = (char*)calloc((size_t)ng, 1);
+    for (int g = 0; g < ng; ++g) key2[g].i = -1;
+    int u = 0;
+    in2[0] = 1;
+    for (int it = 1; it < ng; ++it) {
+      for (int g = 0; g < ng; ++g) {
+        if (in2[g]) continue;
+        dc_edge c = W[(size_t)u * ng + g];
+        if (key2[g].i < 0 || dc_less(c, key2[g])) key2[g] = c;
+      }
+      int nx = -1;
+      for (int g = 0; g < ng; ++g) {
+        if (in2[g]) continue;
+        if (nx < 0 || dc_less(key2[g], key2[nx])) nx = g;
+      }
+      in2[nx] = 1;
+      eu[ne] = key2[nx].i; ev[ne] = key2[nx].j; ++ne;
+      u = nx;
+    }
+    free(key2); free(in2);
+  }
+  free(W);
+  /* the union of the edges, ordered and labelled by a breadth-first walk from the root
+     (neighbours in ascending index) */
+  int* deg = (int*)calloc((size_t)n + 1, sizeof(int));
+  for (int e = 0; e < ne; ++e) { deg[eu[e] + 1]++; deg[ev[e] + 1]++; }
+  for (int i = 0; i < n; ++i) deg[i + 1] += deg[i];
+  int* adj = (int*)malloc(sizeof(int) * (size_t)(2 * ne + 1));
+  int* fill = (int*)calloc((size_t)n, sizeof(int));
+  for (int e = 0; e < ne; ++e) {
+    adj[deg[eu[e]] + fill[eu[e]]++] = ev[e];
+    adj[deg[ev[e]] + fill[ev[e]]++] = eu[e];
+  }
+  for (int i = 0; i < n; ++i) { /* ascending neighbours: insertion sort of each list */
+    for (int a = deg[i] + 1; a < deg[i + 1]; ++a) {
+      int x = adj[a], b = a - 1;
+      while (b >= deg[i] && adj[b] > x) { adj[b + 1] = adj[b]; --b; }
+      adj[b + 1] = x;
+    }
+  }
+  for (int i = 0; i < n; ++i) { parent[i] = -2; level[i] = 0; }
+  parent[root] = -1;
+  int head = 0, tail = 0;
+  order[tail++] = root;
+  while (head < tail) {
+    int u = order[head++];
+    for (int a = deg[u]; a < deg[u + 1]; ++a) {
+      int w = adj[a];
+      if (parent[w] == -2) { parent[w] = u; level[w] = level[u] + 1; order[tail++] = w; }
+    }
+  }
+  if (leaf_of_out) memcpy(leaf_of_out, t.leaf_of, sizeof(int) * (size_t)n);
+  if (nleaf_out) *nleaf_out = ng;
+  free(deg); free(adj); free(fill);
+  free(eu); free(ev);
+  free(key); free(t.leaf_of); free(t.leaf_start); free(t.members);
   return root;
 }
 
@@ -394,7 +639,10 @@ void orc_set_H(orc_system* s, double H) { s->H = H; }
    information at s0 that the convergence criterion needs (one force evaluation). */
 static void orc_prepare(orc_system* s) {
   int n = s->n;
-  s->root = orc_prim(n, s->r, s->parent, s->level, s->order);
+  if (s->p.mst_method == 1)
+    s->root = orc_dc_mst(n, s->r, s->p.mst_leaf, s->parent, s->level, s->order, NULL, NULL);
+  else
+    s->root = orc_prim(n, s->r, s->parent, s->level, s->order);
   orc_to_mst(n, s->parent, s->r, s->X0);
   orc_to_mst(n, s->parent, s->v, s->V0);
   s->T0 = orc_kinetic(n, s->m, s->v);

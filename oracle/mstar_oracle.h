@@ -35,6 +35,8 @@ typedef struct {
   int n_d;           /* near-pair tree distance N_d (Eq. LCA) */
   int max_halvings;  /* step rejections before giving up (Sec. 2.3) */
   int max_time_iter; /* extra steps towards the end time (Sec. 2.4) */
+  int mst_method;    /* 0: Prim's MST (Sec. 3.2); 1: divide-and-conquer tree (Sec. 3.3) */
+  int mst_leaf;      /* subgraph size limit of the divide-and-conquer octree (0: ceil(sqrt(n))) */
 } orc_params;
 
 typedef struct {
@@ -57,6 +59,17 @@ void orc_com_shift(int n, const double* m, double* w);
 /* Prim's algorithm (Sec. 3.2) with the indexing of Sec. 3.4. r must be in the COM frame.
    Returns the root; fills parent (-1 at root), level, order (insertion order). Pinned. */
 int orc_prim(int n, const double* r, int* parent, int* level, int* order);
+/* Divide-and-conquer spanning tree (Sec. 3.3): an octree splits the bodies into
+   subgraphs of at most leaf_cap bodies (0: ceil(sqrt(n)); cells split while they hold more,
+   down to depth 16; leaves in Morton order); Prim's MST inside each subgraph; the
+   meta-graph of the contracted subgraphs weighted by their cheapest connecting edge (cut
+   property) and its Prim MST; the union of these edges is ordered by a breadth-first walk
+   from the root (the body closest to the COM). Same outputs as orc_prim (order: the walk),
+   plus the subgraph of every body and the number of subgraphs (either may be NULL).
+   Pinned: equal to Prim's tree for one subgraph and for singleton subgraphs; octree
+   invariants; local MSTs; meta edges minimal and forming the meta-graph's MST. */
+int orc_dc_mst(int n, const double* r, int leaf_cap, int* parent, int* level, int* order, int* leaf_of,
+               int* nleaf);
 /* Eq. LCA: 1 if i != j are within n_d tree edges. Pinned. */
 int orc_is_near(const int* parent, const int* level, int i, int j, int n_d);
 /* MST separation r_j - r_i by walking i -> LCA -> j over edge vectors X (Sec. 3.4). Pinned. */

@@ -1,0 +1,135 @@
+"""Pins of the oracle's divide-and-conquer spanning tree (Sec. 3.3).
+
+The tree is the union of Prim MSTs of octree subgraphs and the Prim MST of the meta-graph
+whose vertices are the contracted subgraphs and whose edge weights are their cheapest
+connecting edges (cut property), ordered by a walk from the root. Pinned against facts
+that do not come from the oracle's own code:
+- with one subgraph, and with one body per subgraph, it is the exact MST (Prim's tree);
+- it is a spanning tree, rooted at the body closest to the centre of mass;
+- restricted to any subgraph it is the MST of that subgraph (Kruskal), "locally true";
+- every edge between two subgraphs is the cheapest edge between them (brute force), and
+  these edges form the MST of the meta-graph (Kruskal on brute-force weights);
+- the partition has about sqrt(N) subgraphs;
+- its length exceeds the MST's by a few per cent (the paper: typically 5 %);
+- a run of the integrator on it stays in the |dE/E| ~ 1e-14..1e-13 regime. Its longer
+  root paths (mean level 1.3-1.9x the MST's at N = 300..10^4) add rounding in the rebuilds
+  (Sec. 3.5): over seeds its error ranges from equal to ~30x that of the exact MST.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2001_03180_gb300 import workloads as W
+
+from tests.helpers import edge_set, mst_kruskal, sqdist
+
+
+def length(r, parent):
+    return sum(math.sqrt(sqdist(r, v, int(p))) for v, p in enumerate(parent) if p >= 0)
+
+
+@pytest.mark.parametrize("n, seed", [(30, 1), (150, 2), (700, 3)])
+def test_one_subgraph_and_singletons_give_prims_tree(n, seed):
+    m, r, v = W.plummer(n, seed)
+    r = O.com_shift(m, r)
+    root, par, lev, order = O.prim(r)
+    for nsub in (1, n):
+        root2, par2, lev2, order2, leaf, ng = O.dc_mst(r, nsub)
+        assert root2 == root
+        assert np.array_equal(par2, par) and np.array_equal(lev2, lev)
+        assert ng == (1 if nsub == 1 else n)
+
+
+@pytest.mark.parametrize("n, seed", [(200, 4), (1000, 5)])
+def test_dc_tree_structure_local_and_meta_optimality(n, seed):
+    m, r, v = W.plummer(n, seed)
+    r = O.com_shift(m, r)
+    root, par, lev, order, leaf, ng = O.dc_mst(r)
+    target = math.ceil(math.sqrt(n))
+    # about sqrt(N) subgraphs: splitting a cell adds at most 7
+    assert target <= ng <= target + 7
+    # a spanning tree rooted at the body closest to the COM; levels are tree depths
+    assert root == int(np.argmin((r * r).sum(axis=1)))
+    assert par[root] == -1 and (par >= 0).sum() == n - 1
+    for w in order[1:]:
+        assert lev[w] == lev[par[w]] + 1
+    assert sorted(order.tolist()) == list(range(n))
+    edges = edge_set(par)
+    inside = {e for e in edges if leaf[e[0]] == leaf[e[1]]}
+    across = edges - inside
+    # locally true MSTs
+    for g in range(ng):
+        idx = np.flatnonzero(leaf == g)
+        local = {(int(idx[a]), int(idx[b])) for a, b in mst_kruskal(r[idx])}
+        assert {e for e in inside if leaf[e[0]] == g} == local
+    # meta edges: cheapest between their subgraphs, and the meta-graph's MST
+    assert len(across) == ng - 1
+    d2 = ((r[:, None, :] - r[None, :, :]) ** 2).sum(axis=2)
+    W2 = np.full((ng, ng), np.inf)
+    for a in range(ng):
+        ia = np.flatnonzero(leaf == a)
+        for b in range(a + 1, ng):
+            ib = np.flatnonzero(leaf == b)
+            W2[a, b] = W2[b, a] = d2[np.ix_(ia, ib)].min()
+    for i, j in across:
+        a, b = sorted((int(leaf[i]), int(leaf[j])))
+        assert d2[i, j] == W2[a, b]
+    pts = [(W2[a, b], a, b) for a in range(ng) for b in range(a + 1, ng)]
+    pts.sort()
+    uf = list(range(ng))
+
+    def find(x):
+        while uf[x] != x:
+            uf[x] = uf[uf[x]]
+            x = uf[x]
+        return x
+
+    meta = set()
+    for _, a, b in pts:
+        fa, fb = find(a), find(b)
+        if fa != fb:
+            uf[fa] = fb
+            meta.add((a, b))
+    assert {tuple(sorted((int(leaf[i]), int(leaf[j])))) for i, j in across} == meta
+
+
+@pytest.mark.parametrize("n, seed", [(1000, 3), (2000, 4), (4000, 5)])
+def test_dc_tree_a_few_per_cent_longer_than_the_mst(n, seed):
+    m, r, v = W.plummer(n, seed)
+    r = O.com_shift(m, r)
+    _, par_e, _, _ = O.prim(r)
+    _, par_d, _, _, _, _ = O.dc_mst(r)
+    ratio = length(r, par_d) / length(r, par_e)
+    assert 1.0 < ratio < 1.15, ratio
+
+
+def test_integrator_on_the_dc_tree_conserves_energy():
+    m, r, v = W.workload("plummer64")
+    s = O.System(m, r, v, mst_method=1)
+    e0 = s.energy()
+    rc, st = s.integrate(1.0)
+    e1 = s.energy()
+    assert rc == 0 and abs(st["t"] - 1.0) <= 1e-10
+    assert abs((e1["E"] - e0["E"]) / e0["E"]) < 5e-13
+
+
+def test_tie_rules_hand_computed():
+    """Exact ties (Sec. 3.2 leaves them open; readings: keys replaced only by strictly smaller
+    distances, lowest index first; between two subgraphs the cheapest pair is the lowest
+    (i, j) among equals, i in the lower-numbered subgraph).
+    1. Unit square 0 (0,0), 1 (1,0), 2 (0,1), 3 (1,1) in one subgraph, grown from body 0:
+       1 and 2 at distance 1, then 3 is equally close to 1 and 2 and keeps parent 1.
+    2. Body 0 at (-3,0,0) alone in one octree cell; bodies 1 (1,1,0.5) and 2 (1,0.5,1) share
+       the opposite cell, both at squared distance 17.25 (exact) from body 0: the meta edge is
+       (0, 1). The root is body 1 (|r|^2 = 2.25 ties with body 2; lowest index)."""
+    sq = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [1.0, 1.0, 0.0]]) - 0.5 * np.array([1, 1, 0])
+    root, par, lev, order, leaf, ng = O.dc_mst(sq, 1)
+    assert ng == 1 and root == 0
+    assert par.tolist() == [-1, 0, 0, 1] and lev.tolist() == [0, 1, 1, 2]
+    tri = np.array([[-3.0, 0.0, 0.0], [1.0, 1.0, 0.5], [1.0, 0.5, 1.0]])
+    root, par, lev, order, leaf, ng = O.dc_mst(tri, 2)
+    assert ng == 2 and leaf.tolist() == [0, 1, 1]
+    assert root == 1
+    assert par.tolist() == [1, -1, 1] and lev.tolist() == [1, 0, 1]
