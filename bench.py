@@ -322,6 +322,46 @@ def run_adjoint(args, dev, M, W, torch):
                     "per kick"}
 
 
+def run_mst_builders(args, dev, M, m, r, v, torch):
+    """Spanning-tree build time on the benchmark workload: the step's exact MST builder
+    (Boruvka rounds, Prim on ties), the divide-and-conquer tree of Sec. 3.3, and Prim's
+    algorithm (one CTA).
+    Each repetition re-sets the state from device copies so that the tree is rebuilt; the
+    time covers the build and the copy of parent and level to the host."""
+    import numpy as np
+
+    out = {}
+    for name, meth in (("exact_mst", 0), ("divide_and_conquer", 1)):
+        g = M.Integrator(m, r, v, device=dev, mst_method=meth)
+        rd = torch.empty((len(m), 3), dtype=torch.float64, device=dev)
+        vd = torch.empty((len(m), 3), dtype=torch.float64, device=dev)
+        t = M.mstar_get_state(g.ctx, rd, vd)
+        times = []
+        for rep in range(6):
+            M.mstar_set_state(g.ctx, t, rd, vd)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            root, parent, level, _ = g.mst(with_order=False)
+            times.append(time.perf_counter() - t0)
+        g.close()
+        out[name + "_ms"] = 1e3 * statistics.median(times[1:])
+        out[name + "_mean_level"] = float(np.mean(level))
+        d = np.linalg.norm(np.asarray(r)[np.flatnonzero(parent >= 0)] - np.asarray(r)[parent[parent >= 0]], axis=1)
+        out[name + "_length"] = float(d.sum())
+    # Prim's algorithm itself (the one-CTA kernel that also records the insertion order)
+    g = M.Integrator(m, r, v, device=dev)
+    times = []
+    for rep in range(4):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        g.mst(with_order=True)
+        times.append(time.perf_counter() - t0)
+    g.close()
+    out["prim_one_cta_ms"] = 1e3 * statistics.median(times[1:])
+    out["length_ratio"] = out["divide_and_conquer_length"] / out["exact_mst_length"]
+    return out
+
+
 def run_mstar(args):
     import numpy as np
     import torch
@@ -452,6 +492,10 @@ def run_mstar(args):
     if rank == 0 and not args.no_batched:
         with torch.cuda.stream(stream):
             batched = run_batched(args, dev, M, W, torch)
+    mst = None
+    if rank == 0:
+        with torch.cuda.stream(stream):
+            mst = run_mst_builders(args, dev, M, m, r, v, torch)
     adjoint = None
     if rank == 0 and not args.no_adjoint:
         with torch.cuda.stream(stream):
@@ -468,7 +512,7 @@ def run_mstar(args):
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
-               "adjoint": adjoint}
+               "adjoint": adjoint, "mst_builders": mst}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:

@@ -73,6 +73,11 @@ typedef struct {
   int n_d;           /* near-pair tree distance N_d of Eq. LCA, 0 <= n_d <= 2. 2 */
   int max_halvings;  /* rejections of one step before MSTAR_ERR_NO_CONVERGENCE. 30 */
   int max_time_iter; /* end-time-clamped steps per mstar_step call (Sec. 2.4). 8 */
+  int mst_method;    /* spanning tree of each step: 0 Prim's MST (Sec. 3.2), 1 the divide-and-conquer
+                        tree of Sec. 3.3 (octree subgraphs, their MSTs joined by the meta-graph's
+                        MST; a few per cent longer than the MST). Batches always use 0. 0 */
+  int mst_nsub;      /* subgraphs of the divide-and-conquer octree, 0 = ceil(sqrt(n)), at most
+                        1024. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */

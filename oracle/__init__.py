@@ -40,7 +40,7 @@ class Params(C.Structure):
                 ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
                 ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int),
                 ("max_halvings", C.c_int), ("max_time_iter", C.c_int), ("mst_method", C.c_int),
-                ("mst_leaf", C.c_int)]
+                ("mst_nsub", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -43,7 +43,7 @@ void orc_params_default(orc_params* p) {
   p->max_halvings = 30;
   p->max_time_iter = 8;
   p->mst_method = 0;
-  p->mst_leaf = 0;
+  p->mst_nsub = 0;
 }
 
 /* ---------------------------------------------------------------- energies (Eq. 1) */
@@ -640,7 +640,7 @@ void orc_set_H(orc_system* s, double H) { s->H = H; }
 static void orc_prepare(orc_system* s) {
   int n = s->n;
   if (s->p.mst_method == 1)
-    s->root = orc_dc_mst(n, s->r, s->p.mst_leaf, s->parent, s->level, s->order, NULL, NULL);
+    s->root = orc_dc_mst(n, s->r, s->p.mst_nsub, s->parent, s->level, s->order, NULL, NULL);
   else
     s->root = orc_prim(n, s->r, s->parent, s->level, s->order);
   orc_to_mst(n, s->parent, s->r, s->X0);

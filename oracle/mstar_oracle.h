@@ -36,7 +36,7 @@ typedef struct {
   int max_halvings;  /* step rejections before giving up (Sec. 2.3) */
   int max_time_iter; /* extra steps towards the end time (Sec. 2.4) */
   int mst_method;    /* 0: Prim's MST (Sec. 3.2); 1: divide-and-conquer tree (Sec. 3.3) */
-  int mst_leaf;      /* subgraph size limit of the divide-and-conquer octree (0: ceil(sqrt(n))) */
+  int mst_nsub;      /* subgraphs of the divide-and-conquer octree (0: ceil(sqrt(n))) */
 } orc_params;
 
 typedef struct {

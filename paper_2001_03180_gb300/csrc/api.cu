@@ -43,6 +43,7 @@ struct Carver {
 
 struct Shape {
   int n, npad, K, S, W, T, NT, nblk;
+  size_t dcb;  // divide-and-conquer tree scratch (0 unless that builder is selected)
 };
 
 Shape shape_of(int n, const mstar_params& p) {
@@ -55,6 +56,7 @@ Shape shape_of(int n, const mstar_params& p) {
   s.S = p.k_fix + 1;
   s.NT = s.npad / s.T;
   s.nblk = (s.npad + kBlock - 1) / kBlock;
+  s.dcb = p.mst_method == 1 ? dc_scratch_bytes(n, p.mst_nsub) : 0;
   return s;
 }
 
@@ -90,6 +92,7 @@ size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
   t.epsblk = c.take<double>(s.nblk);
   t.res = c.take<double>(8);
   t.mom = c.take<double>((size_t)s.nblk * 8);
+  t.dc = s.dcb ? c.take<char>(s.dcb) : nullptr;
   double* st = c.take<double>(2 * n3);
   if (d) *d = t;
   if (stage) *stage = st;
@@ -107,6 +110,7 @@ bool valid_params(const mstar_params* p) {
   if (p->k_fix < 2 || p->k_fix > kMaxKfix) return false;
   if (p->n_d < 0 || p->n_d > 2) return false;
   if (p->max_halvings < 0 || p->max_time_iter < 0) return false;
+  if (p->mst_method < 0 || p->mst_method > 1 || p->mst_nsub < 0 || p->mst_nsub > kDcMaxSub) return false;
   return true;
 }
 
@@ -203,9 +207,13 @@ void prof_flush(mstar_ctx* c) {
 // step start (one force evaluation); reads U0 and T0 back.
 int prepare_step(mstar_ctx* c, double* U0, double* T0) {
   if (!c->mst_valid) {
-    bool tied = true;
-    if (c->n >= kBoruvkaMinN) CK(launch_mst_boruvka(c, &tied));
-    if (tied) CK(launch_prim(c));
+    if (c->p.mst_method == 1) {
+      CK(launch_mst_dc(c));
+    } else {
+      bool tied = true;
+      if (c->n >= kBoruvkaMinN) CK(launch_mst_boruvka(c, &tied));
+      if (tied) CK(launch_prim(c));
+    }
     CK(launch_tree(c));
     c->mst_valid = true;
   }
@@ -355,6 +363,8 @@ void mstar_default_params(mstar_params* p) {
   p->n_d = 2;
   p->max_halvings = 30;
   p->max_time_iter = 8;
+  p->mst_method = 0;
+  p->mst_nsub = 0;
 }
 
 size_t mstar_workspace_bytes(int n, const mstar_params* p) {
@@ -542,7 +552,14 @@ int mstar_set_state(mstar_ctx* c, double t, const double* r, const double* v) {
 
 int mstar_get_mst(mstar_ctx* c, int* root, int* parent, int* level, int* order) {
   if (!c) return MSTAR_ERR_INVALID_ARG;
-  if (order) {
+  if (c->p.mst_method == 1) {
+    // the divide-and-conquer tree; its order is the breadth-first walk of the build
+    if (!c->mst_valid) {
+      CK(launch_mst_dc(c));
+      CK(launch_tree(c));
+      c->mst_valid = true;
+    }
+  } else if (order) {
     // Prim's kernel records the insertion order; it builds the same tree as the step's
     // MST builder, so the step buffers stay valid.
     CK(launch_prim(c));

@@ -306,6 +306,20 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
 
 }  // namespace
 
+// Orientation of an undirected spanning tree (edges eu[e]-ev[e], e < n-1) from Prim's root
+// into d.parent, d.level, d.root; `queue` receives the breadth-first order.
+cudaError_t launch_orient(mstar_ctx* c, const int* eu, const int* ev, int* adj_off, int* adj, int* queue) {
+  const int n = c->n;
+  const double* X = c->d.r;
+  const size_t smem = sizeof(int) * 2 * (size_t)n;
+  cudaError_t e = cudaFuncSetAttribute(k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_orient<<<1, 1024, smem, c->stream>>>(n, X, X + c->npad, X + 2 * (size_t)c->npad, eu, ev, adj_off, adj,
+                                         c->d.parent, c->d.level, c->d.root, queue);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
 // Boruvka MST of d.r into parent/level/root; returns cudaSuccess and sets *tied when a
 // tie was seen (the caller then runs the Prim kernel). Scratch lives in the pair partial
 // buffer, which is free while the tree is being built.

@@ -48,6 +48,7 @@ struct Dev {
   double* epsblk;   // nblk
   double* res;      // small results read by the host: [0] eps, [1] t, [2] U0, [3] T0
   double* mom;      // nblk x 8 block partials of T, P, L
+  char* dc;         // divide-and-conquer tree scratch (mst_method 1 only)
 };
 
 }  // namespace mstar
@@ -111,6 +112,12 @@ cudaError_t launch_tree(mstar_ctx* c);      // grandparents and children CSR
 // boruvka.cu: exact MST by Boruvka rounds; *tied = true asks for the Prim kernel instead
 cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied);
 constexpr int kBoruvkaMinN = 512;           // below this Prim in one CTA is as fast
+// BFS orientation of an undirected spanning tree from Prim's root (boruvka.cu)
+cudaError_t launch_orient(mstar_ctx* c, const int* eu, const int* ev, int* adj_off, int* adj, int* queue);
+// dcmst.cu: divide-and-conquer spanning tree of d.r (Sec. 3.3) into parent/level/root/order
+cudaError_t launch_mst_dc(mstar_ctx* c);
+size_t dc_scratch_bytes(int n, int nsub);    // device scratch the builder needs
+constexpr int kDcMaxSub = 1024;              // largest subgraph count the GPU builder accepts
 
 // pair.cu: slots [slot_lo, slot_hi) -> sa, Ublk. n_d as in params (0 = all Cartesian).
 cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d);

@@ -44,7 +44,7 @@ class mstar_params(C.Structure):
     _fields_ = [("eta_gbs", C.c_double), ("a_gbs", C.c_double), ("fac_min", C.c_double),
                 ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
                 ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int), ("max_halvings", C.c_int),
-                ("max_time_iter", C.c_int)]
+                ("max_time_iter", C.c_int), ("mst_method", C.c_int), ("mst_nsub", C.c_int)]
 
 
 class mstar_stats(C.Structure):
