@@ -67,6 +67,13 @@ def lib():
             L.orc_com_shift.argtypes = [C.c_int, _D, _D]
             L.orc_prim.restype = C.c_int
             L.orc_prim.argtypes = [C.c_int, _D, _I, _I, _I]
+            L.orc_chain.restype = C.c_int
+            L.orc_chain.argtypes = [C.c_int, _D, _I, _I, _I]
+            L.orc_energy_comp.restype = C.c_double
+            L.orc_energy_comp.argtypes = [C.c_int, _D, _D, _D, C.c_double]
+            L.orc_rebuild_run.restype = C.c_int
+            L.orc_rebuild_run.argtypes = [C.c_int, _D, _D, _D, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _I, _D, _I,
+                                          _D]
             L.orc_dc_mst.restype = C.c_int
             L.orc_dc_mst.argtypes = [C.c_int, _D, C.c_int, _I, _I, _I, _I, _I]
             L.orc_is_near.restype = C.c_int
@@ -152,6 +159,34 @@ def prim(r):
     parent = np.empty(n, np.int32); level = np.empty(n, np.int32); order = np.empty(n, np.int32)
     root = lib().orc_prim(n, _d(r), _i(parent), _i(level), _i(order))
     return root, parent, level, order
+
+
+def chain(r):
+    """Chained coordinates (Sec. 2.2) as a tree rooted at the tail: (tail, parent, level, order)."""
+    r = _f64(r, (-1, 3))
+    n = r.shape[0]
+    parent = np.empty(n, np.int32); level = np.empty(n, np.int32); order = np.empty(n, np.int32)
+    tail = lib().orc_chain(n, _d(r), _i(parent), _i(level), _i(order))
+    return tail, parent, level, order
+
+
+def energy_comp(m, r, v, G=1.0) -> float:
+    m = _f64(m); n = len(m)
+    return lib().orc_energy_comp(n, _d(m), _d(_f64(r, (n, 3))), _d(_f64(v, (n, 3))), float(G))
+
+
+def rebuild_run(m, r, v, coords, cycles, topo_every, sample_at, deconstruct=0):
+    """Rebuild test of Sec. 3.5 (coords 0: MST, 1: chain; deconstruct 0: COM shift, 1: root
+    kept). Returns dict(r, v, E, topo_changes, mean_level); E[s] after sample_at[s] cycles."""
+    m = _f64(m); n = len(m)
+    r = _f64(r, (n, 3)).copy(); v = _f64(v, (n, 3)).copy()
+    sa = np.ascontiguousarray(sample_at, dtype=np.int32)
+    E = np.empty(len(sa)); ch = np.zeros(1, np.int32); ml = np.zeros(1)
+    rc = lib().orc_rebuild_run(n, _d(m), _d(r), _d(v), int(coords), int(deconstruct), int(cycles), int(topo_every),
+                               len(sa), _i(sa), _d(E), _i(ch), _d(ml))
+    if rc != 0:
+        raise ValueError(f"orc_rebuild_run failed ({rc})")
+    return dict(r=r, v=v, E=E, topo_changes=int(ch[0]), mean_level=float(ml[0]))
 
 
 def dc_mst(r, leaf_cap=0):

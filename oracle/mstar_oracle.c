@@ -130,6 +130,121 @@ int orc_prim(int n, const double* r, int* parent, int* level, int* order) {
   return root;
 }
 
+/* ---------------------------------------------------------------- chained coordinates (Sec. 2.2) */
+
+int orc_chain(int n, const double* r, int* parent, int* level, int* order) {
+  /* the shortest inter-particle vector: its ends are the first tail and head (lowest pair
+     (i, j), i < j, on ties; i is the tail) */
+  int ti = 0, hj = 1;
+  double best = w2(r, 0, 1);
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      double d = w2(r, i, j);
+      if (d < best) { best = d; ti = i; hj = j; }
+    }
+  int* dq = (int*)malloc(sizeof(int) * (size_t)(2 * n)); /* the chain as a deque */
+  char* in = (char*)calloc((size_t)n, 1);
+  int lo = n, hi = n + 1;
+  dq[lo] = ti; dq[hi] = hj;
+  in[ti] = 1; in[hj] = 1;
+  for (int added = 2; added < n; ++added) {
+    /* the particle closest to either end; the tail wins a tie between the ends, then the
+       lowest index */
+    int tail = dq[lo], head = dq[hi], bp = -1, bend = 0;
+    double bd = INFINITY;
+    for (int p = 0; p < n; ++p) {
+      if (in[p]) continue;
+      double dt = w2(r, p, tail), dh = w2(r, p, head);
+      int end = dh < dt ? 1 : 0;
+      double d = end ? dh : dt;
+      if (bp < 0 || d < bd) { bd = d; bp = p; bend = end; }
+    }
+    in[bp] = 1;
+    if (bend) dq[++hi] = bp; else dq[--lo] = bp;
+  }
+  /* labels from the tail: edge vector X_k = r_{c_{k+1}} - r_{c_k}, stored at c_{k+1} */
+  for (int k = 0; k < n; ++k) {
+    int p = dq[lo + k];
+    order[k] = p;
+    parent[p] = k ? dq[lo + k - 1] : -1;
+    level[p] = k;
+  }
+  int tail = dq[lo];
+  free(dq);
+  free(in);
+  return tail;
+}
+
+/* Neumaier's compensated summation */
+typedef struct { double s, c; } comp_sum;
+static void comp_add(comp_sum* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x; else a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+double orc_energy_comp(int n, const double* m, const double* r, const double* v, double G) {
+  comp_sum T = {0.0, 0.0}, U = {0.0, 0.0};
+  for (int i = 0; i < n; ++i) comp_add(&T, 0.5 * (m[i] * norm2(v + 3 * i)));
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) comp_add(&U, (G * (m[i] * m[j])) / sqrt(w2(r, i, j)));
+  return (T.s + T.c) - (U.s + U.c);
+}
+
+/* Deconstruction with the root's position kept: w_v = (X_v + X_parent(v) + ...) + w_root. */
+static void from_edges_keep_root(int n, const int* parent, int root, const double* W, double* w) {
+  double r0[3] = {w[3 * root], w[3 * root + 1], w[3 * root + 2]};
+  for (int v = 0; v < n; ++v) {
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int u = v; parent[u] >= 0; u = parent[u])
+      for (int k = 0; k < 3; ++k) s[k] += W[3 * u + k];
+    for (int k = 0; k < 3; ++k) w[3 * v + k] = s[k] + r0[k];
+  }
+}
+
+int orc_rebuild_run(int n, const double* m, double* r, double* v, int coords, int deconstruct, int cycles,
+                    int topo_every, int nsample, const int* sample_at, double* E_out, int* topo_changes,
+                    double* mean_level) {
+  if (n < 2 || cycles < 0 || topo_every < 1 || (coords != 0 && coords != 1) || (deconstruct != 0 && deconstruct != 1))
+    return ORC_ERR_ARG;
+  size_t b3 = sizeof(double) * 3 * (size_t)n;
+  int* parent = (int*)malloc(sizeof(int) * (size_t)n);
+  int* prev = (int*)malloc(sizeof(int) * (size_t)n);
+  int* level = (int*)malloc(sizeof(int) * (size_t)n);
+  int* order = (int*)malloc(sizeof(int) * (size_t)n);
+  double* X = (double*)malloc(b3);
+  double* V = (double*)malloc(b3);
+  int changes = 0, s = 0;
+  double lsum = 0.0;
+  int builds = 0;
+  while (s < nsample && sample_at[s] == 0) E_out[s++] = orc_energy_comp(n, m, r, v, 1.0);
+  for (int c = 1; c <= cycles; ++c) {
+    if ((c - 1) % topo_every == 0) {
+      if (coords == 0) orc_prim(n, r, parent, level, order);
+      else orc_chain(n, r, parent, level, order);
+      if (builds) for (int i = 0; i < n; ++i) if (parent[i] != prev[i]) { ++changes; break; }
+      memcpy(prev, parent, sizeof(int) * (size_t)n);
+      for (int i = 0; i < n; ++i) lsum += level[i];
+      ++builds;
+    }
+    /* build the coordinates, deconstruct them (Sec. 3.5) */
+    orc_to_mst(n, parent, r, X);
+    orc_to_mst(n, parent, v, V);
+    if (deconstruct == 0) {
+      orc_from_mst(n, m, parent, X, r);
+      orc_from_mst(n, m, parent, V, v);
+    } else {
+      from_edges_keep_root(n, parent, order[0], X, r);
+      from_edges_keep_root(n, parent, order[0], V, v);
+    }
+    while (s < nsample && sample_at[s] == c) E_out[s++] = orc_energy_comp(n, m, r, v, 1.0);
+  }
+  if (topo_changes) *topo_changes = changes;
+  if (mean_level) *mean_level = builds ? lsum / ((double)builds * n) : 0.0;
+  free(parent); free(prev); free(level); free(order); free(X); free(V);
+  return ORC_OK;
+}
+
 /* ---------------------------------------------------------------- divide-and-conquer MST (Sec. 3.3) */
 
 #define DC_DEPTH 16

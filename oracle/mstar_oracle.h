@@ -59,6 +59,27 @@ void orc_com_shift(int n, const double* m, double* w);
 /* Prim's algorithm (Sec. 3.2) with the indexing of Sec. 3.4. r must be in the COM frame.
    Returns the root; fills parent (-1 at root), level, order (insertion order). Pinned. */
 int orc_prim(int n, const double* r, int* parent, int* level, int* order);
+/* Chained coordinates (Sec. 2.2): the shortest inter-particle vector starts the chain
+   (its lower index is the tail); then the particle closest to the tail or the head joins
+   at that end (the tail on a tie, then the lowest index), until all are chained. Written
+   as a tree rooted at the final tail: parent[c_k] = c_{k-1}, level[c_k] = k, order = the
+   chain from tail to head, so the edge-vector transforms below apply unchanged. Returns
+   the tail. Pinned: a Hamiltonian path whose first link is the shortest pair, no shorter
+   than the MST; a hand-computed case; <L_chain>/<L_MST> in the paper's range. */
+int orc_chain(int n, const double* r, int* parent, int* level, int* order);
+/* E = T - U (Eq. 1) with Neumaier-compensated sums. */
+double orc_energy_comp(int n, const double* m, const double* r, const double* v, double G);
+/* The rebuild test of Sec. 3.5: `cycles` times build the coordinate system (coords 0: the
+   MST, 1: the chain) from (r, v), i.e. the edge vectors X, V, and deconstruct them back to
+   (r, v) by per-vertex path sums from the vertex up to the root, then either
+   (deconstruct 0) the centre-of-mass shift, as the integrator does after every drift and
+   kick, or (deconstruct 1) adding the root's kept position. The topology is rebuilt every
+   `topo_every` cycles (the state moves only by rounding); topo_changes counts rebuilds
+   that changed it. E_out[s] = the compensated energy after sample_at[s] cycles (sample_at
+   ascending; 0 = the start). mean_level = the mean <L> of the topologies built. */
+int orc_rebuild_run(int n, const double* m, double* r, double* v, int coords, int deconstruct, int cycles,
+                    int topo_every, int nsample, const int* sample_at, double* E_out, int* topo_changes,
+                    double* mean_level);
 /* Divide-and-conquer spanning tree (Sec. 3.3): an octree splits the bodies into
    subgraphs of at most leaf_cap bodies (0: ceil(sqrt(n)); cells split while they hold more,
    down to depth 16; leaves in Morton order); Prim's MST inside each subgraph; the

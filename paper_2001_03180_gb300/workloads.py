@@ -113,6 +113,83 @@ def plummer(n: int, seed: int, total_mass: float = 1.0, r_cut_virial: float = 10
     return m, pos, vel
 
 
+def hernquist_df(binding, G=1.0, M=1.0, a=1.0):
+    """Isotropic distribution function f(E) of the Hernquist (1990) sphere, the closed form
+    of Eddington's inversion, for binding energy per unit mass E = Psi - v^2/2 in
+    [0, GM/a): with q = sqrt(a E / (G M)) and v_g = sqrt(G M / a),
+    f = M / (8 sqrt(2) pi^3 a^3 v_g^3) (1 - q^2)^(-5/2)
+        [3 asin q + q sqrt(1 - q^2) (1 - 2 q^2) (8 q^4 - 8 q^2 - 3)]."""
+    q = np.sqrt(np.clip(a * np.asarray(binding, np.float64) / (G * M), 0.0, 1.0 - 1e-16))
+    vg = math.sqrt(G * M / a)
+    q2 = q * q
+    br = 3.0 * np.arcsin(q) + q * np.sqrt(1.0 - q2) * (1.0 - 2.0 * q2) * (8.0 * q2 * q2 - 8.0 * q2 - 3.0)
+    return M / (8.0 * math.sqrt(2.0) * math.pi ** 3 * a ** 3 * vg ** 3) * np.power(1.0 - q2, -2.5) * np.maximum(br, 0.0)
+
+
+def hernquist(n: int, seed: int, total_mass: float = 1.0, r_half: float = 1.0, r_cut_half: float = 20.0,
+              reject_hard_binaries: bool = True, max_draws: int = 1000):
+    """Equal-mass Hernquist sphere (Sec. 6.1): density M a / (2 pi r (r + a)^3) with
+    a = r_half / (1 + sqrt 2), so that half the mass lies inside r_half. Radii from the
+    enclosed-mass fraction M(<r)/M = (r / (r + a))^2 (redrawn beyond r_cut_half half-mass
+    radii); speeds by rejection from v^2 f(Psi(r) - v^2/2), f the isotropic distribution
+    function (Eddington's formula, closed form), Psi = G M / (r + a); isotropic directions;
+    G = 1; shifted to rest at the origin.
+
+    A cluster that holds a hard binary is drawn again (the next draw of the same stream): a
+    pair is hard when its two-body binding energy G m_i m_j / (2 a_ij) exceeds the mean
+    kinetic energy of a particle, m sigma^2 / 2 with sigma^2 = sum m v^2 / sum m.
+    Returns (m, r, v, draws)."""
+    st = Stream(seed, 31)
+    a = r_half / (1.0 + math.sqrt(2.0))
+    rcut = r_cut_half * r_half
+    for draw in range(1, max_draws + 1):
+        rad = np.empty(n)
+        filled = 0
+        while filled < n:
+            x = st.uniform(n - filled)
+            s = np.sqrt(x)
+            with np.errstate(divide="ignore"):
+                rr = a * s / (1.0 - s)
+            ok = rr[(rr <= rcut) & np.isfinite(rr)]
+            rad[filled:filled + ok.size] = ok
+            filled += ok.size
+        pos = rad[:, None] * _isotropic(st, n)
+        psi = total_mass / (rad + a)
+        vesc = np.sqrt(2.0 * psi)
+        grid = np.linspace(0.0, 1.0, 257)[1:-1]
+        speed = np.empty(n)
+        for i in range(n):
+            vv = grid * vesc[i]
+            gmax = 1.05 * float(np.max(vv * vv * hernquist_df(psi[i] - 0.5 * vv * vv, M=total_mass, a=a)))
+            while True:
+                u1, u2 = st.uniform(2)
+                v = u1 * vesc[i]
+                if u2 * gmax <= v * v * float(hernquist_df(psi[i] - 0.5 * v * v, M=total_mass, a=a)):
+                    speed[i] = v
+                    break
+        vel = speed[:, None] * _isotropic(st, n)
+        m = np.full(n, total_mass / n)
+        pos, vel = _to_rest_frame(m, pos, vel)
+        if not reject_hard_binaries or not has_hard_binary(m, pos, vel):
+            return m, pos, vel, draw
+    raise RuntimeError("no Hernquist sample without a hard binary")
+
+
+def has_hard_binary(m, r, v, G=1.0):
+    """True if some pair's two-body binding energy exceeds m sigma^2 / 2 (Sec. 6.1)."""
+    m = np.asarray(m, np.float64)
+    sigma2 = float((m * (v * v).sum(axis=1)).sum() / m.sum())
+    threshold = 0.5 * float(m.mean()) * sigma2
+    d = r[:, None, :] - r[None, :, :]
+    dv = v[:, None, :] - v[None, :, :]
+    dist = np.sqrt((d * d).sum(axis=2))
+    mu = m[:, None] * m[None, :] / (m[:, None] + m[None, :])
+    with np.errstate(divide="ignore"):
+        e_rel = 0.5 * mu * (dv * dv).sum(axis=2) - G * m[:, None] * m[None, :] / dist
+    iu = np.triu_indices(len(m), 1)
+    return bool(np.any(e_rel[iu] < -threshold))
+
+
 def random_rotation(st: Stream) -> np.ndarray:
     """Uniform random rotation matrix from a unit quaternion (Shoemake 1992)."""
     u1, u2, u3 = st.uniform(3)
@@ -281,4 +358,6 @@ def workload(name: str):
         return plummer(256, 4)
     if name == "plummer10k_two_smbh":
         return plummer_two_smbh(10000, 5)
+    if name.startswith("hernquist379_seed"):
+        return hernquist(379, int(name[len("hernquist379_seed"):]))[:3]
     raise KeyError(name)
