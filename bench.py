@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-subsystems measurement and print its object")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-rebuild-test", action="store_true")
     ap.add_argument("--no-single-context", action="store_true",
                     help="skip timing the one-context-per-system path beside the batch")
     return ap.parse_args()
@@ -362,6 +363,37 @@ def run_mst_builders(args, dev, M, m, r, v, torch):
     return out
 
 
+REBUILD_DESC = ("rebuild test of Sec. 3.5: Hernquist N=379 (r_half=1, G=M=1; seeds 1..10, clusters with a hard "
+                "binary redrawn), 1e5 build/deconstruct cycles per system, MST and chain coordinates, "
+                "deconstruction with the centre-of-mass shift (the integrator's) and with the root position kept; "
+                "topology rebuilt every 1000 cycles; energies with compensated sums")
+
+
+def run_rebuild_test(args, dev, M, W, O_unused=None):
+    """The paper's rebuild experiment: mean |dE/E| over 10 seeds after n build/deconstruct
+    cycles, for the MST and the chain under both deconstruction rules."""
+    import numpy as np
+
+    systems = [W.hernquist(379, s)[:3] for s in range(1, 11)]
+    samples = [0, 1, 3, 10, 30, 100, 300, 1000, 3000, 10000, 30000, 100000]
+    jobs = [(s, c, d) for d in (0, 1) for c in (0, 1) for s in range(10)]
+    t0 = time.perf_counter()
+    g = M.mstar_rebuild_test([systems[s] for s, _, _ in jobs], [c for _, c, _ in jobs], [d for _, _, d in jobs],
+                             samples[-1], 1000, samples)
+    wall = time.perf_counter() - t0
+    out = {"workload": REBUILD_DESC, "samples": samples, "wall_s": wall, "jobs": len(jobs)}
+    for d, dname in ((0, "com_shift"), (1, "root_kept")):
+        for c, cname in ((0, "mst"), (1, "chain")):
+            idx = [k for k, (s, cc, dd) in enumerate(jobs) if cc == c and dd == d]
+            E = g["E"][idx]
+            rel = np.abs(E / E[:, :1] - 1.0)
+            out[f"{cname}_{dname}_mean_dE"] = rel.mean(axis=0).tolist()
+            out[f"{cname}_{dname}_mean_level"] = float(np.mean(g["mean_level"][idx]))
+            out[f"{cname}_{dname}_topo_changes"] = int(np.sum(g["topo_changes"][idx]))
+        out[f"chain_over_mst_{dname}_at_1e5"] = out[f"chain_{dname}_mean_dE"][-1] / out[f"mst_{dname}_mean_dE"][-1]
+    return out
+
+
 def run_mstar(args):
     import numpy as np
     import torch
@@ -496,6 +528,9 @@ def run_mstar(args):
     if rank == 0:
         with torch.cuda.stream(stream):
             mst = run_mst_builders(args, dev, M, m, r, v, torch)
+    rebuild = None
+    if rank == 0 and not args.no_rebuild_test:
+        rebuild = run_rebuild_test(args, dev, M, W)
     adjoint = None
     if rank == 0 and not args.no_adjoint:
         with torch.cuda.stream(stream):
@@ -512,7 +547,8 @@ def run_mstar(args):
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
-               "adjoint": adjoint, "mst_builders": mst}
+               "adjoint": adjoint, "mst_builders": mst,
+               "rebuild_test": rebuild}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:

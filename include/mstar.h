@@ -297,6 +297,33 @@ MSTAR_API int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g
                                  double* d_r, double* d_v, double* d_m);
 MSTAR_API void mstar_adjoint_free(mstar_adjoint* a);
 
+
+/* ---- The rebuild test of Sec. 3.5 (a numerical experiment on the coordinate systems). */
+
+/* Largest system of mstar_rebuild_test (one CTA holds a job's state in shared memory). */
+#define MSTAR_REBUILD_MAX_N 1024
+
+/* njobs independent runs of the rebuild test of Sec. 3.5 on systems of n bodies: each job
+   builds its coordinate system from the Cartesian state and deconstructs it back `cycles`
+   times, and records E = T - U (Eq. 1, Neumaier-compensated sums in index order) after
+   sample_at[s] cycles (ascending; 0 = the start) in E_out[job * nsample + s].
+   coords[job]: 0 the MST (Prim, Sec. 3.2; root closest to the centre of mass), 1 the chain
+   of Sec. 2.2 (shortest pair first, then the particle closest to either end, the tail on a
+   tie), as a path tree rooted at its tail. Building: X_v = w_v - w_parent(v). Deconstruction:
+   per-vertex sums of the edge vectors from the vertex up to the root, then
+   deconstruct[job] 0: the centre-of-mass shift (the integrator's rebuild) or 1: plus the
+   root's kept position. The topology is rebuilt every topo_every cycles; topo_changes[job]
+   counts rebuilds that changed it and mean_level[job] is the mean level <L> of the trees
+   built. m (njobs x n), r and v (njobs x n x 3), outputs: host or device; r_out, v_out,
+   topo_changes, mean_level may be NULL. The operations and their order are those of the CPU
+   definition, so the results are bit-identical to it. Allocates and frees device scratch;
+   synchronises the stream. Errors: INVALID_ARG (n outside [2, MSTAR_REBUILD_MAX_N], other
+   bad arguments), NOMEM, CUDA. */
+MSTAR_API int mstar_rebuild_test(int njobs, int n, const double* m, const double* r, const double* v,
+                                 const int* coords, const int* deconstruct, int cycles, int topo_every, int nsample,
+                                 const int* sample_at, double* E_out, double* r_out, double* v_out, int* topo_changes,
+                                 double* mean_level, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ EXPORTS = [
     "mstar_batch_workspace_bytes", "mstar_batch_init", "mstar_step_batched", "mstar_batch_get_state",
     "mstar_batch_set_H", "mstar_batch_set_schedule", "mstar_batch_get_schedule", "mstar_batch_autotune",
     "mstar_batch_launch_count", "mstar_batch_free",
-    "mstar_adjoint_forward", "mstar_step_adjoint", "mstar_adjoint_free",
+    "mstar_adjoint_forward", "mstar_step_adjoint", "mstar_adjoint_free", "mstar_rebuild_test",
 ]
 MSTAR_BATCH_MAX_N = 512
 MSTAR_BATCH_NUM_CLASSES = 7
@@ -121,6 +121,8 @@ def load():
     L.mstar_step_adjoint.argtypes = [vp, vp, dp, dp, C.c_double, dp, dp, dp]
     L.mstar_adjoint_free.argtypes = [vp]
     L.mstar_adjoint_free.restype = None
+    L.mstar_rebuild_test.argtypes = [C.c_int, C.c_int, dp, dp, dp, ip, ip, C.c_int, C.c_int, C.c_int, ip, dp, dp, dp,
+                                     ip, dp, vp]
     _lib = L
     return L
 
@@ -563,3 +565,30 @@ def fixed_run(m, r, v, H, nsteps, checkpoint_every=10, **params):
 
     t = lambda x: torch.as_tensor(x, dtype=torch.float64)  # noqa: E731
     return _FixedRunFn.apply(t(m), t(r), t(v))
+
+
+# ---------------------------------------------------------------- rebuild test (Sec. 3.5)
+
+MSTAR_REBUILD_MAX_N = 1024
+
+
+def mstar_rebuild_test(systems, coords, deconstruct, cycles, topo_every, sample_at, cuda_stream=None):
+    """Jobs j = (systems[j] = (m, r, v), coords[j], deconstruct[j]), all with the same n.
+    Returns dict(E (jobs x samples), r, v (jobs x n x 3), topo_changes, mean_level)."""
+    nj = len(systems)
+    n = len(systems[0][0])
+    m = np.ascontiguousarray(np.stack([np.asarray(s[0], np.float64) for s in systems]))
+    r = np.ascontiguousarray(np.stack([np.asarray(s[1], np.float64).reshape(n, 3) for s in systems]))
+    v = np.ascontiguousarray(np.stack([np.asarray(s[2], np.float64).reshape(n, 3) for s in systems]))
+    co = np.ascontiguousarray(coords, dtype=np.int32)
+    de = np.ascontiguousarray(deconstruct, dtype=np.int32)
+    sa = np.ascontiguousarray(sample_at, dtype=np.int32)
+    E = np.empty((nj, len(sa)))
+    ro = np.empty_like(r)
+    vo = np.empty_like(v)
+    tc = np.empty(nj, np.int32)
+    ml = np.empty(nj)
+    _check(load().mstar_rebuild_test(nj, n, _ptr(m), _ptr(r), _ptr(v), _ptr(co), _ptr(de), int(cycles),
+                                     int(topo_every), len(sa), _ptr(sa), _ptr(E), _ptr(ro), _ptr(vo), _ptr(tc),
+                                     _ptr(ml), cuda_stream), "mstar_rebuild_test")
+    return dict(E=E, r=ro, v=vo, topo_changes=tc, mean_level=ml)
