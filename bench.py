@@ -124,39 +124,27 @@ class ClockSampler:
 
 
 def dist_setup(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_2001_03180_gb300 import replicas as R
+
+    return R.env_ranks()
 
 
 def reduce_max(x, world, dev):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_2001_03180_gb300 import replicas as R
 
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return R.reduce_max(x, world, dev)
 
 
 def reduce_sum(x, world, dev):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
+    from paper_2001_03180_gb300 import replicas as R
 
-    t = torch.tensor([x], dtype=torch.float64, device=dev)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return R.reduce_sum(x, world, dev)
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
+    from paper_2001_03180_gb300 import replicas as R
 
-        dist.barrier()
+    R.barrier(world)
 
 
 def cpu_baseline_sample(n_threads):
@@ -224,11 +212,17 @@ BATCH_DESC = ("4096 independent systems (seed 3): even indices hierarchical trip
               "N~round(exp U[ln 3, ln 200]) bodies with a central mass of 0.1 of the cluster; eta_GBS=1e-12, k_fix=8")
 
 
-def run_batched(args, dev, M, W, torch):
+def run_batched(args, dev, M, W, torch, world=1, rank=0):
     """Batched subsystems: each launch gives every system one GBS step attempt (one CTA per
     system). Throughput = accepted system steps per second over the timed launches; the
-    plain one-context-per-system path is timed beside it on a sample of the same systems."""
-    systems = W.batched_systems(4096, 3)
+    plain one-context-per-system path is timed beside it on a sample of the same systems.
+    With several ranks the systems are split by the greedy longest-first rule on N^2 (no
+    collective on the data path); the rate is the sum of accepted steps over the max time."""
+    from paper_2001_03180_gb300 import replicas as R
+
+    all_systems = W.batched_systems(4096, 3)
+    mine = R.shard_greedy([len(s.m) ** 2 for s in all_systems], world)[rank]
+    systems = [all_systems[i] for i in mine]
     t_end = 1000.0  # no system gets there within the launches below: each launch is an attempt for all
     b = M.Batch([(s.m, s.r, s.v) for s in systems], device=dev)
     b.step(t_end, 40)  # step-size controllers settle from the first-step rule (halvings)
@@ -238,24 +232,27 @@ def run_batched(args, dev, M, W, torch):
     l0 = M.mstar_batch_launch_count(b.b)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    R.barrier(world)
     torch.cuda.synchronize(dev)
     e0.record(b.stream)
     st1 = b.step(t_end, launches)
     e1.record(b.stream)
     torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
+    R.barrier(world)
+    ms = R.reduce_max(e0.elapsed_time(e1), world, dev)
     nl = M.mstar_batch_launch_count(b.b) - l0
     b.close()
-    acc = st1["accepted"] - st0["accepted"]
-    att = acc + st1["rejected"] - st0["rejected"]
-    out = {"workload": BATCH_DESC, "systems": len(systems), "bodies": sum(len(s.m) for s in systems),
+    acc = R.reduce_sum(st1["accepted"] - st0["accepted"], world, dev)
+    att = acc + R.reduce_sum(st1["rejected"] - st0["rejected"], world, dev)
+    out = {"workload": BATCH_DESC, "systems": len(all_systems), "bodies": sum(len(s.m) for s in all_systems),
+           "ranks": world,
            "launches": nl, "ms_per_launch": ms / launches, "system_steps_per_s": acc / (ms * 1e-3),
            "system_attempts_per_s": att / (ms * 1e-3), "failed": st1["failed"],
            "schedule": {"warps_per_division_group_by_size_class": sched.tolist(),
                         "size_classes": "[2,8] [9,16] [17,32] [33,64] [65,128] [129,256] [257,512]",
                         "autotune_launch_ms": tune_ms},
            "launch": "one CUDA graph launch per attempt (one kernel node per group width)"}
-    if args.no_single_context:
+    if args.no_single_context or rank != 0:
         return out
     # the single-system path, one context per system, on every 128th system
     secs = 0.0
@@ -521,9 +518,9 @@ def run_mstar(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_sample(os.cpu_count() or 1)
     batched = None
-    if rank == 0 and not args.no_batched:
+    if not args.no_batched:
         with torch.cuda.stream(stream):
-            batched = run_batched(args, dev, M, W, torch)
+            batched = run_batched(args, dev, M, W, torch, world, rank)
     mst = None
     if rank == 0:
         with torch.cuda.stream(stream):
