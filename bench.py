@@ -38,7 +38,9 @@ FLOPS_PER_UNORDERED_PAIR = 33
 # 3.0 DADD and 7.0 DFMA per pair). r^2, 1/r, 1/r^3 and the mass products run exactly on the
 # integer pipe, so the binding FP64 pipe caps this kernel at FP64 issue rate / 10 pairs.
 FP64_INSTR_PER_PAIR = 10
-# SURVEY-style count for one ordered pair-force evaluated on its own (no symmetry).
+# Flops of one ordered pair-force evaluated on its own, without the i<->j symmetry (3 DADD,
+# r^2 and a Newton-refined reciprocal square root, the mass scalings, 3 DFMA accumulations, U),
+# reported beside the symmetric count for comparison.
 FLOPS_PER_ORDERED_PAIR_NONSYM = 28
 NOMINAL_FP64_TFLOPS = 1.25
 # FP64 FMA units: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
@@ -511,7 +513,7 @@ def run_mstar(args):
                 "peak_probe_tflops": 2.0 * fma_rate / 1e12,
                 "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
                 "pair_kernel_share_of_step": prof.pair_ms / ms if ms > 0 else None,
-                "survey_equiv_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * prof.pair_interactions
+                "ordered_pair_28flop_equiv_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * prof.pair_interactions
                 / (prof.pair_ms * 1e-3) / 1e12 if prof.pair_ms > 0 else None}
 
     cpu = None
