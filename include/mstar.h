@@ -210,8 +210,8 @@ MSTAR_API int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, 
    end-time-clamped steps, or (status -3) after more than max_halvings successive
    rejections. Each system is one CTA of four division groups of G warps (G from the
    schedule, by size class); its k_fix divisions go to the groups by the greedy
-   longest-first recipe of Sec. 4.2. The graph holds one independent kernel node per group
-   width in use. Synchronises the stream; out may be NULL. */
+   longest-first recipe of Sec. 4.2. The graph holds one independent kernel node per
+   schedule in use. Synchronises the stream; out may be NULL. */
 MSTAR_API int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out);
 
 /* Per-system time t[nsys], state r, v (nbody x 3, host or device), last error eps[nsys]
@@ -222,18 +222,20 @@ MSTAR_API int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double
 /* Set every system's next fictitious step (host array H[nsys]; 0 = unset). */
 MSTAR_API int mstar_batch_set_H(mstar_batch* b, const double* H);
 
-/* Schedule of the batch: warps per division group (1, 2 or 4) for each of the
-   MSTAR_BATCH_NUM_CLASSES size classes. A new schedule rebuilds the graph (INVALID_ARG for
-   any other width). The default is 1 up to 64 bodies, 2 up to 128, 4 above. The schedule
-   changes only the work split, not the arithmetic of a system beyond the order in which
-   partial sums are added. */
+/* Schedule of the batch, for each of the MSTAR_BATCH_NUM_CLASSES size classes: 1, 2 or 4
+   warps per division group (one CTA per system), or 0 for the classes of at most 16 bodies:
+   four division groups of 8 (class 0) or 16 (class 1) lanes per system, one body per lane,
+   the group's state in registers and the pair rotation and tree sums done by warp shuffles.
+   A new schedule rebuilds the graph (INVALID_ARG for any other value). The default is 0, 0,
+   1, 1, 1, 2, 4. The schedule changes only the work split, not the arithmetic of a system
+   beyond the order in which partial sums are added. */
 MSTAR_API int mstar_batch_set_schedule(mstar_batch* b, const int* schedule);
 MSTAR_API int mstar_batch_get_schedule(const mstar_batch* b, int* schedule);
 
 /* Autotuner with no counterpart in the paper (its GPU analogue of choosing how many
-   processes work on one force loop, Sec. 4.3): one pass of coordinate descent over the
+   processes work on one force loop, Sec. 4.3): two passes of coordinate descent over the
    size classes present, largest first, timing one graph launch towards t_end (best of
-   `repeats`, after a warm-up) for each group width with the other classes fixed, and
+   `repeats`, after a warm-up) for each allowed schedule with the other classes fixed, and
    keeping the fastest. Trials run on a snapshot of the batch, which is put back: the
    systems' state, time and step sizes are unchanged. Allocates a temporary device copy of
    the workspace (NOMEM if that fails). Sets and returns the schedule (schedule_out may be

@@ -345,6 +345,53 @@ __device__ __forceinline__ double d2x(const double* r, int u, int v) {
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Sec. 2.4: the fictitious step of this attempt -- the first step ds = q U dt, later the
+// controller's step, clamped so that t + H/U does not pass t_end (with the time-iteration
+// count) -- or true when the system stops here (t_end reached, iterations exhausted).
+__device__ bool choose_step(SysScalars* S, const BatchParams& P, double t_end, double t0, double U0, double* Hs_out) {
+  const double dt = t_end - t0;
+  double Hs = 0.0;
+  bool abort_ = false;
+  if (fabs(dt) <= P.t_tol * fabs(t_end)) {
+    S->status = 1;
+    abort_ = true;
+  } else {
+    Hs = (S->H == 0.0) ? P.q_first * U0 * dt : fabs(S->H) * (dt < 0 ? -1.0 : 1.0);
+    if (fabs(Hs / U0) >= fabs(dt)) {
+      Hs = U0 * dt;
+      if (S->halvings == 0) {
+        if (S->time_iters >= P.max_time_iter) {
+          S->status = 2;
+          abort_ = true;
+        } else {
+          S->time_iters++;
+        }
+      }
+    }
+  }
+  *Hs_out = Hs;
+  return abort_;
+}
+
+// Sec. 2.3 and Eq. hnext: accept (new H from eps, time of the extrapolated state) or halve H.
+__device__ bool accept_or_halve(SysScalars* S, const BatchParams& P, int K, double eps, double H, double tkk_t) {
+  S->eps = eps;
+  S->force_evals += 2 * K * (K + 1) / 2 + 1;
+  if (eps <= P.eta) {
+    double fc = (eps > 0.0) ? P.a_gbs * pow(P.eta / eps, 1.0 / (2 * K - 1)) : P.fac_max;
+    fc = fmin(fmax(fc, P.fac_min), P.fac_max);
+    S->H = fc * H;
+    S->t = tkk_t;
+    S->accepted++;
+    S->halvings = 0;
+    return true;
+  }
+  S->rejected++;
+  S->H = 0.5 * H;
+  if (++S->halvings > P.max_halvings) S->status = -3;
+  return false;
+}
+
 // One GBS step attempt for each of the `count` systems order[0 .. count-1].
 template <int G>
 __global__ void __launch_bounds__(128 * G)
@@ -490,31 +537,12 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
     gsum3<G>(t2, z1, z2, gi, s_gred);
     const double T0 = 0.5 * t2;
     if (gi.t == 0) {
-      // Sec. 2.4: first step ds = q U dt; then the controller's step, clamped to t_end
-      const double dt = t_end - t0;
-      double abort_ = 0.0;
       double Hs = 0.0;
-      if (fabs(dt) <= P.t_tol * fabs(t_end)) {
-        S->status = 1;
-        abort_ = 1.0;
-      } else {
-        Hs = (S->H == 0.0) ? P.q_first * U0 * dt : fabs(S->H) * (dt < 0 ? -1.0 : 1.0);
-        if (fabs(Hs / U0) >= fabs(dt)) {
-          Hs = U0 * dt;
-          if (S->halvings == 0) {
-            if (S->time_iters >= P.max_time_iter) {
-              S->status = 2;
-              abort_ = 1.0;
-            } else {
-              S->time_iters++;
-            }
-          }
-        }
-      }
+      const bool abort_ = choose_step(S, P, t_end, t0, U0, &Hs);
       s_scal[0] = U0;
       s_scal[1] = T0;
       s_scal[2] = Hs;
-      s_scal[3] = abort_;
+      s_scal[3] = abort_ ? 1.0 : 0.0;
       S->U0 = U0;
       S->T0 = T0;
     }
@@ -623,22 +651,7 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
   if (tid == 0) {
     double eps = s_red[0];
     for (int w = 1; w < NW; ++w) eps = nanmax(eps, s_red[w]);
-    S->eps = eps;
-    S->force_evals += 2 * K * (K + 1) / 2 + 1;
-    if (eps <= P.eta) {
-      double fc = (eps > 0.0) ? P.a_gbs * pow(P.eta / eps, 1.0 / (2 * K - 1)) : P.fac_max;
-      fc = fmin(fmax(fc, P.fac_min), P.fac_max);
-      S->H = fc * H;
-      S->t = tkk_t;
-      S->accepted++;
-      S->halvings = 0;
-      s_scal[3] = 1.0;
-    } else {
-      S->rejected++;
-      S->H = 0.5 * H;
-      if (++S->halvings > P.max_halvings) S->status = -3;
-      s_scal[3] = 0.0;
-    }
+    s_scal[3] = accept_or_halve(S, P, K, eps, H, tkk_t) ? 1.0 : 0.0;
   }
   __syncthreads();
   if (s_scal[3] == 0.0) return;
@@ -647,6 +660,352 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
     double* dst = gi.g == 0 ? R : Vs;
     const double* src = gi.g == 0 ? TKK : TKK + 3 * n;
     grebuild<G>(n, m, parent, src, dst, Mtot, false, gi, s_gred);
+  }
+}
+
+// ---------------------------------------------------------------------------- segment schedules
+//
+// Systems of at most WD bodies (WD = 8: size class 0, WD = 16: class 1): one system per
+// 4 x WD threads, four division groups of WD lanes, lane l of a group holding body l of
+// the group's division state in registers. The pair loop is the symmetric rotation of the
+// CTA schedules inside the group's lanes (partner (l + k) mod WD at step k, exchanged by
+// shuffles, the partner's share returned to its lane the same way); near pairs take their
+// separation from edge vectors; rebuilds sum edge vectors up the tree by shuffles.
+constexpr int kSegThreads = 128;
+
+template <int WD>
+struct Seg {
+  int g, l, base;       // group, lane in the group, first lane of the group within the warp
+  unsigned mask;        // the group's lanes
+  __device__ __forceinline__ double get(double x, int src) const { return __shfl_sync(mask, x, src, WD); }
+  __device__ __forceinline__ int get(int x, int src) const { return __shfl_sync(mask, x, src, WD); }
+  __device__ __forceinline__ double sum(double x) const {
+    for (int o = WD / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o, WD);
+    return x;
+  }
+};
+
+// Barrier over the 4 WD threads of one system (a warp, or named barrier 1 + system slot).
+template <int WD>
+__device__ __forceinline__ void sys_sync(int slot) {
+  if constexpr (4 * WD == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(4 * WD) : "memory");
+  }
+}
+
+// Path sums of the edge vectors W up the tree (vertex first, root excluded), then the
+// centre-of-mass shift; returns sum m |w|^2 of the group's bodies after the shift.
+template <int WD>
+__device__ double seg_rebuild(const Seg<WD>& sg, bool live, double mv, int par, const double W[3], double w[3],
+                              double Mtot) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  int u = live ? sg.l : -1;
+  for (int it = 0; it < WD; ++it) {
+    const int su = u >= 0 ? u : 0;
+    const double w0 = sg.get(W[0], su), w1 = sg.get(W[1], su), w2 = sg.get(W[2], su);
+    const int pu = sg.get(par, su);
+    if (u >= 0 && pu >= 0) {
+      s0 = __dadd_rn(s0, w0);
+      s1 = __dadd_rn(s1, w1);
+      s2 = __dadd_rn(s2, w2);
+    }
+    u = (u >= 0) ? pu : -1;
+  }
+  const double c0 = sg.sum(live ? __dmul_rn(mv, s0) : 0.0) / Mtot, c1 = sg.sum(live ? __dmul_rn(mv, s1) : 0.0) / Mtot,
+               c2 = sg.sum(live ? __dmul_rn(mv, s2) : 0.0) / Mtot;
+  w[0] = __dsub_rn(s0, c0);
+  w[1] = __dsub_rn(s1, c1);
+  w[2] = __dsub_rn(s2, c2);
+  const double t2 =
+      live ? __dmul_rn(mv, __dadd_rn(__dadd_rn(__dmul_rn(w[0], w[0]), __dmul_rn(w[1], w[1])), __dmul_rn(w[2], w[2])))
+           : 0.0;
+  return sg.sum(t2);
+}
+
+// The pair loop of one group: a (times G) of the lane's body and the return value U.
+template <int WD>
+__device__ double seg_forces(const Seg<WD>& sg, int n, int n_d, double Gc, double mv, int par, int gpar,
+                             const double r[3], const double X[3], double a[3]) {
+  const bool live = sg.l < n;
+  const MassSplit ms = mass_split(live ? mv : 1.0);
+  const double Xp0 = sg.get(X[0], par >= 0 ? par : 0), Xp1 = sg.get(X[1], par >= 0 ? par : 0),
+               Xp2 = sg.get(X[2], par >= 0 ? par : 0);  // X of this body's parent
+  const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
+  double ax = 0.0, ay = 0.0, az = 0.0, ui = 0.0;
+  const int msh = (int)(ms.m >> 32), msl = (int)(ms.m & 0xffffffffu);
+  for (int k = 1; k <= WD / 2; ++k) {
+    const int jl = (sg.l + k) & (WD - 1);
+    const double xj = sg.get(r[0], jl), yj = sg.get(r[1], jl), zj = sg.get(r[2], jl);
+    const double Xj0 = sg.get(X[0], jl), Xj1 = sg.get(X[1], jl), Xj2 = sg.get(X[2], jl);
+    const double Xpj0 = sg.get(Xp0, jl), Xpj1 = sg.get(Xp1, jl), Xpj2 = sg.get(Xp2, jl);
+    const double mj = sg.get(mv, jl);
+    const int pj = sg.get(par, jl), gj = sg.get(gpar, jl);
+    const int mjh = sg.get(msh, jl), mjl = sg.get(msl, jl), mje = sg.get(ms.e, jl);
+    const int i = sg.l, j = jl;
+    const bool valid = live && j < n && !(k == WD / 2 && sg.l >= WD / 2);
+    double dx, dy, dz;
+    if (nd1 && par == j) {                 // j is the parent of i
+      dx = -X[0]; dy = -X[1]; dz = -X[2];
+    } else if (nd1 && pj == i) {           // i is the parent of j
+      dx = Xj0; dy = Xj1; dz = Xj2;
+    } else if (nd2 && gpar == j) {         // j is the grandparent of i
+      dx = -(X[0] + Xp0); dy = -(X[1] + Xp1); dz = -(X[2] + Xp2);
+    } else if (nd2 && gj == i) {           // i is the grandparent of j
+      dx = Xj0 + Xpj0; dy = Xj1 + Xpj1; dz = Xj2 + Xpj2;
+    } else if (nd2 && par >= 0 && par == pj) {  // siblings
+      dx = Xj0 - X[0]; dy = Xj1 - X[1]; dz = Xj2 - X[2];
+    } else {
+      dx = xj - r[0]; dy = yj - r[1]; dz = zj - r[2];
+    }
+    double rinv = 0.0, sj = 0.0, si = 0.0;
+    if (valid) {
+      const MassSplit msj{((unsigned long long)(unsigned)mjh << 32) | (unsigned)mjl, mje};
+      pair_scalars_int(dx, dy, dz, msj, ms, rinv, sj, si);
+    }
+    ax = fma(sj, dx, ax);
+    ay = fma(sj, dy, ay);
+    az = fma(sj, dz, az);
+    ui = fma(valid ? mj : 0.0, rinv, ui);
+    // the partner's share, -si d, goes back to its lane
+    const int from = (sg.l - k) & (WD - 1);
+    const double bx = sg.get(-si * dx, from), by = sg.get(-si * dy, from), bz = sg.get(-si * dz, from);
+    ax += bx;
+    ay += by;
+    az += bz;
+  }
+  a[0] = Gc * ax;
+  a[1] = Gc * ay;
+  a[2] = Gc * az;
+  return Gc * sg.sum(live ? mv * ui : 0.0);
+}
+
+template <int WD>
+__global__ void __launch_bounds__(kSegThreads)
+k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ off, BatchParams P,
+              const double* __restrict__ tend, const double* __restrict__ mass, double* __restrict__ body,
+              int* __restrict__ ibody, SysScalars* __restrict__ sys, double* __restrict__ tdiv) {
+  constexpr int PER = kSegThreads / (4 * WD);  // systems per CTA
+  __shared__ int s_par[PER][WD];
+  __shared__ double s_E[PER][kMaxKfix][6][WD];
+  __shared__ double s_T[PER][6][WD];
+  __shared__ double s_t[PER][kMaxKfix];
+  __shared__ double s_scal[PER][4];
+  __shared__ double s_err[PER][4 * WD / 32];
+  const int slot = threadIdx.x / (4 * WD), lt = threadIdx.x % (4 * WD);
+  Seg<WD> sg;
+  sg.g = lt / WD;
+  sg.l = lt % WD;
+  sg.base = (threadIdx.x & 31) & ~(WD - 1);
+  sg.mask = (WD == 32 ? 0xffffffffu : ((1u << WD) - 1u)) << sg.base;
+  const int q = blockIdx.x * PER + slot;
+  if (q >= count) return;  // whole systems leave together
+  const int s = order[q];
+  SysScalars* S = sys + s;
+  if (S->status != 0) return;
+  const double t_end = *tend;
+  const int o = off[s], n = off[s + 1] - o;
+  const int K = P.k_fix;
+  const double* m = mass + o;
+  double* bd = body + (size_t)o * P.body_doubles;
+  double* Rg = bd + (size_t)B_R * n;
+  double* Vg = bd + (size_t)B_V * n;
+  const double t0 = S->t, B = S->B, Mtot = S->M;
+  const int l = sg.l;
+  const bool live = l < n;
+  const double mv = live ? m[l] : 0.0;
+  double R[3], Vs[3];
+  for (int c = 0; c < 3; ++c) {
+    R[c] = live ? Rg[3 * l + c] : 0.0;
+    Vs[c] = live ? Vg[3 * l + c] : 0.0;
+  }
+  // ---- MST by one thread (Prim with exact keys, lowest index on ties)
+  if (lt == 0) {
+    unsigned long long key[WD];
+    bool in[WD];
+    int root = 0;
+    unsigned long long best = ~0ull;
+    for (int w = 0; w < n; ++w) {
+      const double x = Rg[3 * w], y = Rg[3 * w + 1], z = Rg[3 * w + 2];
+      const unsigned long long d = key_bits(__dadd_rn(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)), __dmul_rn(z, z)));
+      if (d < best) {
+        best = d;
+        root = w;
+      }
+      key[w] = 0x7ff0000000000000ull;
+      in[w] = false;
+      s_par[slot][w] = -1;
+    }
+    in[root] = true;
+    int u = root;
+    for (int it = 1; it < n; ++it) {
+      int nx = -1;
+      for (int w = 0; w < n; ++w) {
+        if (in[w]) continue;
+        const unsigned long long d = key_bits(d2x(Rg, u, w));
+        if (d < key[w]) {
+          key[w] = d;
+          s_par[slot][w] = u;
+        }
+        if (nx < 0 || key[w] < key[nx]) nx = w;
+      }
+      in[nx] = true;
+      if (s_par[slot][nx] < 0) s_par[slot][nx] = root;
+      u = nx;
+    }
+  }
+  sys_sync<WD>(slot);
+  const int par = live ? s_par[slot][l] : -3;
+  const int gpar = par >= 0 ? s_par[slot][par] : (live ? -1 : -3);
+  // ---- edge coordinates and derivative information of the step start (every group)
+  double X0[3], V0[3], A0[3], a[3];
+  for (int c = 0; c < 3; ++c) {
+    const double Rp = sg.get(R[c], par >= 0 ? par : 0), Vp = sg.get(Vs[c], par >= 0 ? par : 0);
+    X0[c] = par >= 0 ? __dsub_rn(R[c], Rp) : 0.0;
+    V0[c] = par >= 0 ? __dsub_rn(Vs[c], Vp) : 0.0;
+  }
+  const double U0 = seg_forces<WD>(sg, n, P.n_d, P.G, mv, par, gpar, R, X0, a);
+  for (int c = 0; c < 3; ++c) {
+    const double ap = sg.get(a[c], par >= 0 ? par : 0);
+    A0[c] = par >= 0 ? __dsub_rn(a[c], ap) : 0.0;
+  }
+  const double T0 = 0.5 * sg.sum(live ? __dmul_rn(mv, __dadd_rn(__dadd_rn(__dmul_rn(Vs[0], Vs[0]),
+                                                                         __dmul_rn(Vs[1], Vs[1])),
+                                                                __dmul_rn(Vs[2], Vs[2])))
+                                      : 0.0);
+  if (lt == 0) {
+    double Hs = 0.0;
+    const bool ab = choose_step(S, P, t_end, t0, U0, &Hs);
+    s_scal[slot][0] = Hs;
+    s_scal[slot][1] = ab ? 1.0 : 0.0;
+  }
+  sys_sync<WD>(slot);
+  const double H = s_scal[slot][0];
+  if (s_scal[slot][1] != 0.0) return;
+  // ---- this group's divisions (greedy longest-first assignment to the four groups), run
+  // as one sequence of substeps so that the four groups of a warp stay in step: a division
+  // that ends is followed at once by the group's next one (its first half drift folded in)
+  int mydiv[kMaxKfix], nmy = 0;
+  int load[kGroups] = {0, 0, 0, 0};
+  for (int k = K; k >= 1; --k) {
+    int gsel = 0;
+    for (int w = 1; w < kGroups; ++w)
+      if (load[w] < load[gsel]) gsel = w;
+    load[gsel] += 2 * k;
+    if (gsel == sg.g) mydiv[nmy++] = k;
+  }
+  int steps = 0;
+  for (int w = 0; w < kGroups; ++w) steps = load[w] > steps ? load[w] : steps;
+  const int mine = load[sg.g];
+  {
+    int di = 0, k = mydiv[0], nk = 2 * k, sub = 0;
+    double delta = H / (double)nk;
+    double f = (0.5 * delta) / (T0 + B);
+    double X[3], V[3], r[3], v[3];
+    for (int c = 0; c < 3; ++c) {
+      X[c] = madd(X0[c], f, V0[c]);
+      V[c] = V0[c];
+    }
+    double t = t0 + f;
+    seg_rebuild<WD>(sg, live, mv, par, X, r, Mtot);
+    for (int step = 0; step < steps; ++step) {
+      const bool active = step < mine;
+      const double U = seg_forces<WD>(sg, n, P.n_d, P.G, mv, par, gpar, r, X, a);
+      const double fk = delta / U;
+      for (int c = 0; c < 3; ++c) {
+        const double ap = sg.get(a[c], par >= 0 ? par : 0);
+        if (par >= 0) V[c] = madd(V[c], fk, __dsub_rn(a[c], ap));
+      }
+      const double T = 0.5 * seg_rebuild<WD>(sg, live, mv, par, V, v, Mtot);
+      const bool last = sub == nk - 1;
+      f = (last ? 0.5 * delta : delta) / (T + B);
+      for (int c = 0; c < 3; ++c) X[c] = madd(X[c], f, V[c]);
+      t += f;
+      if (active && last) {
+        for (int c = 0; c < 3; ++c) {
+          s_E[slot][k - 1][c][l] = X[c];
+          s_E[slot][k - 1][3 + c][l] = V[c];
+        }
+        if (l == 0) s_t[slot][k - 1] = t;
+      }
+      if (last) {
+        sub = 0;
+        if (++di < nmy) {
+          k = mydiv[di];
+          nk = 2 * k;
+          delta = H / (double)nk;
+          f = (0.5 * delta) / (T0 + B);
+          for (int c = 0; c < 3; ++c) {
+            X[c] = madd(X0[c], f, V0[c]);
+            V[c] = V0[c];
+          }
+          t = t0 + f;
+        }
+      } else {
+        ++sub;
+      }
+      if (step + 1 < steps) seg_rebuild<WD>(sg, live, mv, par, X, r, Mtot);
+    }
+  }
+  sys_sync<WD>(slot);
+  // ---- Aitken-Neville extrapolation and the error of Eq. gbs-criterion: group 0 takes X,
+  // group 1 takes V of its lane's body, group 2 (lane 0) takes t
+  const double rate = 1.0 / (T0 + B), delta = H / (double)(2 * K);
+  auto neville = [&](const double* Sv, double& tkk, double& tprev) {
+    double prev[kMaxKfix], cur[kMaxKfix];
+    for (int k = 0; k < K; ++k) {
+      cur[0] = Sv[k];
+      for (int j = 1; j <= k; ++j) cur[j] = fma(__dsub_rn(cur[j - 1], prev[j - 1]), c_bfac[k][j], cur[j - 1]);
+      if (k == K - 2) tprev = cur[k];
+      for (int j = 0; j <= k; ++j) prev[j] = cur[j];
+    }
+    tkk = prev[K - 1];
+  };
+  double e = 0.0, tkk_t = 0.0;
+  auto nrm = [](const double* x) {
+    return sqrt(__dadd_rn(__dadd_rn(__dmul_rn(x[0], x[0]), __dmul_rn(x[1], x[1])), __dmul_rn(x[2], x[2])));
+  };
+  if (sg.g < 2 && live) {
+    double Sv[kMaxKfix], dd[3];
+    for (int c = 0; c < 3; ++c) {
+      double tkk, tp = 0.0;
+      for (int k = 0; k < K; ++k) Sv[k] = s_E[slot][k][3 * sg.g + c][l];
+      neville(Sv, tkk, tp);
+      s_T[slot][3 * sg.g + c][l] = tkk;
+      dd[c] = __dsub_rn(tkk, tp);
+    }
+    if (par >= 0) {
+      double qv[3];
+      for (int c = 0; c < 3; ++c)
+        qv[c] = sg.g == 0 ? madd(X0[c], delta, __dmul_rn(V0[c], rate)) : madd(V0[c], delta, A0[c] / U0);
+      e = nrm(dd) / fmax(nrm(qv), 1e-300);
+    }
+  }
+  if (sg.g == 2 && l == 0) {
+    double Sv[kMaxKfix], tp = 0.0;
+    for (int k = 0; k < K; ++k) Sv[k] = s_t[slot][k];
+    neville(Sv, tkk_t, tp);
+    e = fabs(__dsub_rn(tkk_t, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300);
+    s_scal[slot][2] = tkk_t;
+  }
+  for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+  if ((threadIdx.x & 31) == 0) s_err[slot][lt / 32] = e;
+  sys_sync<WD>(slot);
+  if (lt == 0) {
+    double eps = s_err[slot][0];
+    for (int w = 1; w < 4 * WD / 32; ++w) eps = nanmax(eps, s_err[slot][w]);
+    s_scal[slot][3] = accept_or_halve(S, P, K, eps, H, s_scal[slot][2]) ? 1.0 : 0.0;
+  }
+  sys_sync<WD>(slot);
+  if (s_scal[slot][3] == 0.0) return;
+  // ---- accept: deconstruct the extrapolated edge vectors into the Cartesian state
+  if (sg.g < 2) {
+    double W[3], w[3];
+    for (int c = 0; c < 3; ++c) W[c] = live ? s_T[slot][3 * sg.g + c][l] : 0.0;
+    seg_rebuild<WD>(sg, live, mv, par, W, w, Mtot);
+    if (live)
+      for (int c = 0; c < 3; ++c) (sg.g ? Vg : Rg)[3 * l + c] = w[c];
   }
 }
 
@@ -733,7 +1092,7 @@ struct mstar_batch {
   // schedule: warps per division group for each size class, the systems of each schedule
   // (largest first) as consecutive segments of `order`, and the graph of one launch
   int sched[kNumClasses] = {};
-  int seg_begin[3] = {}, seg_count[3] = {};  // schedules G = 1, 2, 4
+  int seg_begin[5] = {}, seg_count[5] = {};  // G = 1, 2, 4 and the 8- and 16-lane segment kernels
   cudaGraphExec_t exec = nullptr;
   int graph_nodes = 0;
   double tend_h = NAN;
@@ -807,11 +1166,18 @@ __global__ void k_scatter_vec(int nbody, const int* __restrict__ off, int nsys, 
   }
 }
 
-int sched_index(int G) { return G == 1 ? 0 : (G == 2 ? 1 : (G == 4 ? 2 : -1)); }
+// Schedule values: 1, 2, 4 warps per division group (one CTA per system), or 0 for the size
+// classes of at most 16 bodies: groups of 8 (class 0) or 16 (class 1) lanes, one body per
+// lane. Node index: 0, 1, 2 for G = 1, 2, 4; 3 and 4 for the 8- and 16-lane kernels.
+int sched_index(int cls, int G) {
+  if (G == 0) return cls == 0 ? 3 : (cls == 1 ? 4 : -1);
+  return G == 1 ? 0 : (G == 2 ? 1 : (G == 4 ? 2 : -1));
+}
+bool sched_ok(int cls, int G) { return sched_index(cls, G) >= 0; }
 
 // Warps per division group by size class before any tuning: wider groups for larger systems.
 void default_schedule(int* sched) {
-  static const int d[kNumClasses] = {1, 1, 1, 1, 2, 4, 4};
+  static const int d[kNumClasses] = {0, 0, 1, 1, 1, 2, 4};
   for (int c = 0; c < kNumClasses; ++c) sched[c] = d[c];
 }
 
@@ -826,20 +1192,22 @@ void destroy_graph(mstar_batch* b) {
 // segment, the widest schedule at the highest priority.
 int apply_schedule(mstar_batch* b, const int* sched) {
   for (int c = 0; c < kNumClasses; ++c)
-    if (sched_index(sched[c]) < 0) return MSTAR_ERR_INVALID_ARG;
+    if (!sched_ok(c, sched[c])) return MSTAR_ERR_INVALID_ARG;
   std::vector<int> ord(b->nsys);
   for (int s = 0; s < b->nsys; ++s) ord[s] = s;
   auto n_of = [&](int s) { return b->off_h[s + 1] - b->off_h[s]; };
-  auto g_of = [&](int s) { return sched_index(sched[mstar::size_class(n_of(s))]); };
+  auto g_of = [&](int s) {
+    const int c = mstar::size_class(n_of(s));
+    return sched_index(c, sched[c]);
+  };
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
     const int gx = g_of(x), gy = g_of(y);
     if (gx != gy) return gx < gy;
     return (long long)n_of(x) * n_of(x) > (long long)n_of(y) * n_of(y);
   });
-  int begin[3] = {0, 0, 0}, count[3] = {0, 0, 0};
+  int begin[5] = {0, 0, 0, 0, 0}, count[5] = {0, 0, 0, 0, 0};
   for (int s = 0; s < b->nsys; ++s) count[g_of(s)]++;
-  begin[1] = count[0];
-  begin[2] = count[0] + count[1];
+  for (int q = 1; q < 5; ++q) begin[q] = begin[q - 1] + count[q - 1];
   if (cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * b->nsys, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return MSTAR_ERR_CUDA;
@@ -850,24 +1218,33 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
   bool ok = true;
   int nodes = 0;
-  for (int q = 2; q >= 0 && ok; --q) {
-    if (!count[q]) continue;
-    int cnt = count[q];
-    const int* ordp = b->order + begin[q];
+  static const int node_order[5] = {2, 1, 0, 4, 3};  // widest groups first
+  for (int t = 0; t < 5 && ok; ++t) {
+    const int qi = node_order[t];
+    if (!count[qi]) continue;
+    int cnt = count[qi];
+    const int* ordp = b->order + begin[qi];
     void* args[] = {&cnt, (void*)&ordp, (void*)&b->off, (void*)&b->bp, (void*)&b->tend, (void*)&b->mass,
                     (void*)&b->body, (void*)&b->ibody, (void*)&b->sys, (void*)&b->tdiv};
     cudaKernelNodeParams kp{};
-    kp.func = q == 0 ? (void*)mstar::k_batched_step<1> : (q == 1 ? (void*)mstar::k_batched_step<2>
-                                                                  : (void*)mstar::k_batched_step<4>);
-    kp.gridDim = dim3(cnt);
-    kp.blockDim = dim3(128 << q);
+    if (qi >= 3) {
+      const int per = mstar::kSegThreads / (4 * (qi == 3 ? 8 : 16));
+      kp.func = qi == 3 ? (void*)mstar::k_batched_seg<8> : (void*)mstar::k_batched_seg<16>;
+      kp.gridDim = dim3((cnt + per - 1) / per);
+      kp.blockDim = dim3(mstar::kSegThreads);
+    } else {
+      kp.func = qi == 0 ? (void*)mstar::k_batched_step<1> : (qi == 1 ? (void*)mstar::k_batched_step<2>
+                                                                      : (void*)mstar::k_batched_step<4>);
+      kp.gridDim = dim3(cnt);
+      kp.blockDim = dim3(128 << qi);
+    }
     kp.sharedMemBytes = 0;
     kp.kernelParams = args;
     cudaGraphNode_t node;
     ok = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) == cudaSuccess;
     if (ok) {
       cudaLaunchAttributeValue pv{};
-      pv.priority = q == 2 ? hi_prio : (q == 1 ? (hi_prio + lo_prio) / 2 : lo_prio);
+      pv.priority = qi == 2 ? hi_prio : (qi == 1 ? (hi_prio + lo_prio) / 2 : lo_prio);
       cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &pv);  // a hint; failure is harmless
       nodes++;
     }
@@ -882,7 +1259,7 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   }
   b->graph_nodes = nodes;
   for (int c = 0; c < kNumClasses; ++c) b->sched[c] = sched[c];
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < 5; ++q) {
     b->seg_begin[q] = begin[q];
     b->seg_count[q] = count[q];
   }
@@ -1116,13 +1493,14 @@ int mstar_batch_autotune(mstar_batch* b, double t_end, int repeats, int* schedul
   for (int c = 0; c < kNumClasses; ++c) cur[c] = b->sched[c];
   double cur_ms = 0.0;
   if (!rc) rc = trial(cur, &cur_ms);
-  // one pass of coordinate descent, largest class first: each class keeps the group width
+  // two passes of coordinate descent, largest class first: each class keeps the schedule
   // that gave the shortest launch with the other classes fixed
-  static const int widths[3] = {1, 2, 4};
-  for (int c = kNumClasses - 1; c >= 0 && !rc; --c) {
+  static const int widths[4] = {1, 2, 4, 0};
+  for (int pass = 0; pass < 2 * kNumClasses && !rc; ++pass) {
+    const int c = kNumClasses - 1 - pass % kNumClasses;
     if (!present[c]) continue;
-    for (int q = 0; q < 3 && !rc; ++q) {
-      if (widths[q] == cur[c]) continue;
+    for (int q = 0; q < 4 && !rc; ++q) {
+      if (widths[q] == cur[c] || !sched_ok(c, widths[q])) continue;
       int cand[kNumClasses];
       for (int x = 0; x < kNumClasses; ++x) cand[x] = cur[x];
       cand[c] = widths[q];

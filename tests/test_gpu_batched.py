@@ -1,7 +1,8 @@
 """Batched independent systems (mstar_step_batched) against the oracle, system by system.
 
-One launch advances every system by one GBS step attempt (one CTA per system, divisions
-spread over four groups of 1, 2 or 4 warps by the greedy recipe of Sec. 4.2). With eta = 1
+One launch advances every system by one GBS step attempt (one CTA per system with
+divisions spread over four groups of 1, 2 or 4 warps by the greedy recipe of Sec. 4.2, or
+groups of 8 or 16 lanes with one body per lane for systems of at most 16 bodies). With eta = 1
 every attempt is accepted, so one launch at a fixed H must reproduce the oracle's single
 attempt for each system (1e-12 relative per system) under every schedule; with eta = 1e-12
 repeated launches must land every system on t_end with the oracle's end state.
@@ -36,7 +37,7 @@ def mixed_systems():
     st = W.Stream(17, 3)
     out = [W.kepler_binary(seed=2, e=0.7), W.pythagorean(),
            W.hierarchical_triple(1.0, 1.0, 0.1, 1.0, 0.3, 20.0, 0.0, math.radians(60.0), st)]
-    for n, seed in [(5, 1), (33, 2), (64, 3), (100, 4), (257, 5), (512, 6)]:
+    for n, seed in [(5, 1), (12, 7), (16, 8), (33, 2), (64, 3), (100, 4), (257, 5), (512, 6)]:
         out.append(W.plummer(n, seed))
     return out
 
@@ -50,7 +51,8 @@ def step_sizes(systems):
     return np.array(H)
 
 
-SCHEDULES = {"default": None, "g1": [1] * 7, "g2": [2] * 7, "g4": [4] * 7, "mixed": [4, 2, 1, 4, 2, 1, 2]}
+SCHEDULES = {"default": None, "g1": [1] * 7, "g2": [2] * 7, "g4": [4] * 7, "mixed": [4, 2, 1, 4, 2, 1, 2],
+             "segments": [0, 0, 2, 1, 1, 1, 2]}
 
 
 @pytest.mark.parametrize("name", list(SCHEDULES))
@@ -118,7 +120,7 @@ def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
     b.set_H(H)
     before = b.state()
     sched, ms = b.autotune(1e9, repeats=1)
-    assert ms > 0 and set(sched.tolist()) <= {1, 2, 4}
+    assert ms > 0 and set(sched.tolist()) <= {0, 1, 2, 4}
     assert list(b.schedule()) == sched.tolist()
     after = b.state()
     for key in ("t", "eps", "status"):
@@ -137,8 +139,10 @@ def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
 
 def test_batch_rejects_bad_schedule():
     b = M.Batch([W.plummer(10, 1)])
-    with pytest.raises(M.MstarError) as e:
-        b.set_schedule([1, 2, 3, 4, 1, 1, 1])
-    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
-    assert list(b.schedule()) == [1, 1, 1, 1, 2, 4, 4]
+    assert list(b.schedule()) == [0, 0, 1, 1, 1, 2, 4]
+    for bad in ([1, 2, 3, 4, 1, 1, 1], [0, 0, 0, 1, 1, 1, 1]):  # width 3; segments above 16 bodies
+        with pytest.raises(M.MstarError) as e:
+            b.set_schedule(bad)
+        assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+    assert list(b.schedule()) == [0, 0, 1, 1, 1, 2, 4]
     b.close()
