@@ -66,6 +66,8 @@ def parse():
                     help="run only the batched-subsystems measurement and print its object")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-rebuild-test", action="store_true")
+    ap.add_argument("--batched-schedule", default=None,
+                    help="comma-separated schedule per size class instead of the autotuner's (profiling)")
     ap.add_argument("--no-single-context", action="store_true",
                     help="skip timing the one-context-per-system path beside the batch")
     return ap.parse_args()
@@ -220,6 +222,8 @@ def run_batched(args, dev, M, W, torch, world=1, rank=0):
     plain one-context-per-system path is timed beside it on a sample of the same systems.
     With several ranks the systems are split by the greedy longest-first rule on N^2 (no
     collective on the data path); the rate is the sum of accepted steps over the max time."""
+    import numpy as np
+
     from paper_2001_03180_gb300 import replicas as R
 
     all_systems = W.batched_systems(4096, 3)
@@ -228,7 +232,12 @@ def run_batched(args, dev, M, W, torch, world=1, rank=0):
     t_end = 1000.0  # no system gets there within the launches below: each launch is an attempt for all
     b = M.Batch([(s.m, s.r, s.v) for s in systems], device=dev)
     b.step(t_end, 40)  # step-size controllers settle from the first-step rule (halvings)
-    sched, tune_ms = b.autotune(t_end, repeats=2)  # setup, state unchanged
+    if args.batched_schedule:
+        sched = np.array([int(x) for x in args.batched_schedule.split(",")], np.int32)
+        b.set_schedule(sched)
+        tune_ms = None
+    else:
+        sched, tune_ms = b.autotune(t_end, repeats=2)  # setup, state unchanged
     launches = 5 * max(args.steps, 1)
     st0 = b.step(t_end, 0)
     l0 = M.mstar_batch_launch_count(b.b)
