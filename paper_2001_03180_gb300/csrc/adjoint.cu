@@ -37,8 +37,16 @@
 namespace mstar {
 namespace {
 
-constexpr int kAdjI = 64;    // bodies i per CTA of the VJP pair loop
-constexpr int kAdjJ = 256;   // partners j per CTA (grid z splits the partners)
+constexpr int kAdjI = 32;    // bodies i per CTA of the VJP pair loop
+constexpr int kAdjZMax = 16; // partner ranges (grid z): ceil(n / 32) up to 16, each a multiple of kAdjI
+
+// Partner range length for n bodies: at most kAdjZMax ranges of at least kAdjI partners.
+int adj_jchunk(int n) {
+  int nz = (n + kAdjI - 1) / kAdjI;
+  if (nz > kAdjZMax) nz = kAdjZMax;
+  const int per = (n + nz - 1) / nz;
+  return (per + kAdjI - 1) / kAdjI * kAdjI;
+}
 
 struct Weights {
   double c[kMaxKfix];
@@ -119,7 +127,7 @@ k_adj_drift(int n, int npad, int slot_lo, int tau, double H, double B, const dou
   if (blockIdx.x == 0 && threadIdx.x == 0) lB[s] += lT;
 }
 
-// VJP pair loop. For body i of slot s against partners j in [z kAdjJ, (z+1) kAdjJ):
+// VJP pair loop. For body i of slot s against partners j in [z jchunk, (z+1) jchunk):
 //   mu_i  = G g sum_j [ w / r^3 - 3 d (d . w) / r^5 ],  w = m_i L_j - m_j L_i
 //   nu_i  = -G g sum_j (L_j . d) / r^3
 //   phi_i = G sum_j m_j / r,   a_i = G sum_j m_j d / r^3,   d = r_j - r_i
@@ -128,7 +136,7 @@ k_adj_drift(int n, int npad, int slot_lo, int tau, double H, double B, const dou
 __global__ void __launch_bounds__(kAdjI)
 k_adj_pair(int n, int npad, int slot_lo, double G, double H, const double* __restrict__ m,
            const double* __restrict__ Rb, size_t rs, const double* __restrict__ Lb, size_t ls,
-           const double* __restrict__ SC, int nz, double* __restrict__ mu, double* __restrict__ nu,
+           const double* __restrict__ SC, int nz, int jchunk, double* __restrict__ mu, double* __restrict__ nu,
            double* __restrict__ phi, double* __restrict__ aout) {
   __shared__ double sx[kAdjI], sy[kAdjI], sz[kAdjI], sm[kAdjI], slx[kAdjI], sly[kAdjI], slz[kAdjI];
   const int s = slot_lo + blockIdx.y;
@@ -143,8 +151,8 @@ k_adj_pair(int n, int npad, int slot_lo, double G, double H, const double* __res
   const double lxi = (live && L) ? L[i] : 0.0, lyi = (live && L) ? L[npad + i] : 0.0,
                lzi = (live && L) ? L[2 * (size_t)npad + i] : 0.0;
   double mux = 0.0, muy = 0.0, muz = 0.0, nuv = 0.0, ph = 0.0, ax = 0.0, ay = 0.0, az = 0.0;
-  const int jend = min(n, (z + 1) * kAdjJ);
-  for (int j0 = z * kAdjJ; j0 < jend; j0 += kAdjI) {
+  const int jend = min(n, (z + 1) * jchunk);
+  for (int j0 = z * jchunk; j0 < jend; j0 += kAdjI) {
     const int j = j0 + threadIdx.x;
     const bool jl = j < jend;
     sx[threadIdx.x] = jl ? R[j] : 0.0;
@@ -338,7 +346,7 @@ using namespace mstar;
 
 struct mstar_adjoint {
   mstar_ctx* c = nullptr;
-  int nsteps = 0, every = 0, nck = 0, nz = 0;
+  int nsteps = 0, every = 0, nck = 0, nz = 0, jchunk = 0;
   double H = 0.0;
   void* mem = nullptr;
   double* ck = nullptr;              // nck x (r planes, v planes)
@@ -438,7 +446,7 @@ int save_planes(mstar_ctx* c, double* rv) {
 int pair_state(mstar_ctx* c, mstar_adjoint* a, const double* R) {
   const dim3 grid((c->n + kAdjI - 1) / kAdjI, 1, a->nz);
   k_adj_pair<<<grid, kAdjI, 0, c->stream>>>(c->n, c->npad, 0, c->p.G, a->H, c->d.m, R, 0, nullptr, 0, nullptr,
-                                             a->nz, a->mu, a->nu, a->phi, a->aout);
+                                             a->nz, a->jchunk, a->mu, a->nu, a->phi, a->aout);
   MSTAR_LAUNCHED(c);
   ACK(cudaGetLastError());
   return MSTAR_OK;
@@ -466,7 +474,7 @@ int backward_step(mstar_ctx* c, mstar_adjoint* a, const AdjTraj& t) {
     if (tau > 0) {
       const dim3 grid((n + kAdjI - 1) / kAdjI, nsl, a->nz);
       k_adj_pair<<<grid, kAdjI, 0, s>>>(n, np, lo, c->p.G, a->H, c->d.m, t.R + (tau - 1) * lvl, st, a->lv, st, SC,
-                                         a->nz, a->mu, a->nu, a->phi, nullptr);
+                                         a->nz, a->jchunk, a->mu, a->nu, a->phi, nullptr);
       k_adj_kick<<<dim3(nb, nsl), kBlock, 0, s>>>(n, np, lo, a->H, c->d.m, A, SC, a->pg, nb, a->mu, a->nu, a->phi,
                                                    a->nz, a->lr, a->lm);
       c->launches += 2;
@@ -501,7 +509,8 @@ int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int checkpoint_eve
   a->nsteps = nsteps;
   a->every = checkpoint_every < nsteps ? checkpoint_every : nsteps;
   a->nck = (nsteps + a->every - 1) / a->every;
-  a->nz = (c->n + kAdjJ - 1) / kAdjJ;
+  a->jchunk = adj_jchunk(c->n);
+  a->nz = (c->n + a->jchunk - 1) / a->jchunk;
   a->tr.resize(a->every);
   a->tck.resize(a->nck);
   // Lagrange weights of the extrapolation to 0 over the nodes x_k = (1/n_k)^2
