@@ -402,6 +402,29 @@ def run_rebuild_test(args, dev, M, W, O_unused=None):
     return out
 
 
+def run_small_configs(args, dev, M, W, torch):
+    """The two smaller configurations: Plummer 64 integrated to t = 1, and Plummer 2048 with a
+    central SMBH binary for 200 accepted GBS steps (wall time through mstar_step, energy error)."""
+    out = {}
+    for key, name, t_end, steps in (("plummer64_to_t1", "plummer64", 1.0, 1 << 30),
+                                    ("plummer2048_smbh_binary_200_steps", "plummer2048_smbh_binary", 10.0, 200)):
+        m, r, v = W.workload(name)
+        g = M.Integrator(m, r, v, device=dev)
+        e0 = g.energy()["E"]
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        rc, st = g.step(t_end, steps)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        e1 = g.energy()["E"]
+        n = len(m)
+        out[key] = {"n": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
+                    "t_reached": st["t"], "gbs_steps_per_s": st["accepted"] / wall,
+                    "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0)}
+        g.close()
+    return out
+
+
 def run_mstar(args):
     import numpy as np
     import torch
@@ -532,6 +555,10 @@ def run_mstar(args):
     if not args.no_batched:
         with torch.cuda.stream(stream):
             batched = run_batched(args, dev, M, W, torch, world, rank)
+    small = None
+    if rank == 0:
+        with torch.cuda.stream(stream):
+            small = run_small_configs(args, dev, M, W, torch)
     mst = None
     if rank == 0:
         with torch.cuda.stream(stream):
@@ -556,7 +583,7 @@ def run_mstar(args):
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
                "adjoint": adjoint, "mst_builders": mst,
-               "rebuild_test": rebuild}
+               "rebuild_test": rebuild, "small_configs": small}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:

@@ -211,6 +211,25 @@ def test_plummer64_run_to_t1_matches_oracle():
     g.close()
 
 
+def test_smbh_binary_2050_200_steps_energy_within_10x_of_oracle():
+    """Plummer 2048 with a central SMBH binary, 200 accepted GBS steps: the energy error of
+    the GPU run is within 10x of the oracle's over the same number of steps, and both runs
+    reach comparable times (their step sequences may differ where eps sits at eta)."""
+    m, r, v = W.workload("plummer2048_smbh_binary")
+    g = M.Integrator(m, r, v)
+    o = O.System(m, r, v)
+    e0g = g.energy()["E"]
+    e0o = o.energy()["E"]
+    rc, st = g.step(10.0, 200)
+    rco, sto = o.integrate(10.0, 200)
+    assert rc == 0 and rco == 0 and st["accepted"] == 200 and sto["accepted"] == 200
+    dEg = abs((g.energy()["E"] - e0g) / e0g)
+    dEo = abs((o.energy()["E"] - e0o) / e0o)
+    assert dEg <= 10 * max(dEo, 1e-15), (dEg, dEo)
+    assert abs(st["t"] - sto["t"]) <= 0.05 * sto["t"], (st["t"], sto["t"])
+    g.close()
+
+
 def test_kepler_gbs_matches_analytic():
     m, r, v = W.kepler_binary(seed=4, e=0.9)
     g = M.Integrator(m, r, v)
