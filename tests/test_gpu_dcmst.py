@@ -97,3 +97,23 @@ def test_invalid_subgraph_count_rejected():
     assert e.value.code == M.MSTAR_ERR_INVALID_ARG
     with pytest.raises(M.MstarError):
         M.Integrator(m, r, v, mst_method=2)
+
+
+def test_run_to_t1_on_dc_tree_matches_oracle():
+    """Plummer 64 (8 subgraphs) to t = 1 with the divide-and-conquer tree in every step: the
+    end state agrees with the oracle's run on the same trees and the energy error is within
+    10x of the oracle's."""
+    m, r, v = W.workload("plummer64")
+    g = M.Integrator(m, r, v, mst_method=1)
+    o = O.System(m, r, v, mst_method=1)
+    e0g, e0o = g.energy()["E"], o.energy()["E"]
+    rc, st = g.step(1.0)
+    rco, sto = o.integrate(1.0)
+    assert rc == 0 and rco == 0
+    S, So = g.state(), o.state()
+    rel = lambda x, y: float(np.abs(x - y).max() / np.abs(y).max())  # noqa: E731
+    assert rel(S["r"], So["r"]) < 1e-9 and rel(S["v"], So["v"]) < 1e-9
+    dEg = abs((g.energy()["E"] - e0g) / e0g)
+    dEo = abs((o.energy()["E"] - e0o) / e0o)
+    assert dEg <= 10 * max(dEo, 1e-15), (dEg, dEo)
+    g.close()
