@@ -555,19 +555,22 @@ def run_mstar(args):
     if not args.no_batched:
         with torch.cuda.stream(stream):
             batched = run_batched(args, dev, M, W, torch, world, rank)
+    # the single-system extras (no data-path collective) run in single-GPU runs only, so that
+    # a multi-GPU run holds its GPUs for the timed work and the sharded batch alone
+    extras = world == 1
     small = None
-    if rank == 0:
+    if extras:
         with torch.cuda.stream(stream):
             small = run_small_configs(args, dev, M, W, torch)
     mst = None
-    if rank == 0:
+    if extras:
         with torch.cuda.stream(stream):
             mst = run_mst_builders(args, dev, M, m, r, v, torch)
     rebuild = None
-    if rank == 0 and not args.no_rebuild_test:
+    if extras and not args.no_rebuild_test:
         rebuild = run_rebuild_test(args, dev, M, W)
     adjoint = None
-    if rank == 0 and not args.no_adjoint:
+    if extras and not args.no_adjoint:
         with torch.cuda.stream(stream):
             adjoint = run_adjoint(args, dev, M, W, torch)
 
