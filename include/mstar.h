@@ -208,10 +208,11 @@ MSTAR_API int mstar_batch_init(mstar_batch** out, int nsys, const int* offsets, 
    Eq. hnext; rejected: H halves for the next launch; Sec. 2.3-2.4 as in mstar_step, per
    system). A system stops at |t - t_end| <= t_tol |t_end|, after max_time_iter
    end-time-clamped steps, or (status -3) after more than max_halvings successive
-   rejections. Each system is one CTA of four division groups of G warps (G from the
-   schedule, by size class); its k_fix divisions go to the groups by the greedy
-   longest-first recipe of Sec. 4.2. The graph holds one independent kernel node per
-   schedule in use. Synchronises the stream; out may be NULL. */
+   rejections. Each system runs four division groups of G warps (G from the schedule, by
+   size class), in one CTA or split over four CTAs; its k_fix divisions go to the groups by
+   the greedy longest-first recipe of Sec. 4.2. The graph holds one independent kernel node
+   per schedule in use (a chain of three for a split schedule). Synchronises the stream; out
+   may be NULL. */
 MSTAR_API int mstar_step_batched(mstar_batch* b, double t_end, int launches, mstar_batch_stats* out);
 
 /* Per-system time t[nsys], state r, v (nbody x 3, host or device), last error eps[nsys]
@@ -222,13 +223,20 @@ MSTAR_API int mstar_batch_get_state(mstar_batch* b, double* t, double* r, double
 /* Set every system's next fictitious step (host array H[nsys]; 0 = unset). */
 MSTAR_API int mstar_batch_set_H(mstar_batch* b, const double* H);
 
-/* Schedule of the batch, for each of the MSTAR_BATCH_NUM_CLASSES size classes: 1, 2 or 4
-   warps per division group (one CTA per system), or 0 for the classes of at most 16 bodies:
-   four division groups of 8 (class 0) or 16 (class 1) lanes per system, one body per lane,
-   the group's state in registers and the pair rotation and tree sums done by warp shuffles.
+/* Schedule of the batch, for each of the MSTAR_BATCH_NUM_CLASSES size classes:
+     1, 2, 4     G warps per division group, one CTA of 4 G warps per system;
+     -1, -2, -4  G = |value| warps per division group, the attempt split into three graph
+                 nodes: the start (MST, derivative information, step size; one CTA per
+                 system), the divisions (one CTA of G warps per system and group, so that
+                 a system's groups run on up to four SMs) and the finish (extrapolation,
+                 error, step control; one CTA per system);
+     0           for the classes of at most 16 bodies: four division groups of 8 (class 0)
+                 or 16 (class 1) lanes per system, one body per lane, the group's state in
+                 registers and the pair rotation and tree sums done by warp shuffles.
    A new schedule rebuilds the graph (INVALID_ARG for any other value). The default is 0, 0,
    1, 1, 1, 2, 4. The schedule changes only the work split, not the arithmetic of a system
-   beyond the order in which partial sums are added. */
+   beyond the order in which partial sums are added (a split schedule gives the same results
+   as the one-CTA schedule of the same G). */
 MSTAR_API int mstar_batch_set_schedule(mstar_batch* b, const int* schedule);
 MSTAR_API int mstar_batch_get_schedule(const mstar_batch* b, int* schedule);
 

@@ -48,10 +48,10 @@ __host__ __device__ __forceinline__ int size_class(int n) {
 
 // Per-system scalars in device memory.
 struct SysScalars {
-  double t, B, H, M, U0, T0, eps, t_end_reached;
+  double t, B, H, M, U0, T0, eps, Ha;  // Ha: the fictitious step of the current attempt
   long long accepted, rejected, force_evals;
   int status;      // 0 running, 1 reached t_end, 2 time-iteration limit, -3 no convergence
-  int halvings, time_iters, pad;
+  int halvings, time_iters, go;  // go: the current attempt runs (1) or the system stopped (0)
 };
 
 // Per-body storage (doubles), offsets in units of n doubles (a 3-vector field spans 3).
@@ -123,11 +123,15 @@ __device__ __forceinline__ void gsum3(double& a, double& b, double& c, const GI&
 
 // Path sums from edge vectors (w_v = W_v + W_parent(v) + ...), then the COM shift; returns
 // sum m |w|^2 after the shift when want_T. Group-level; ends with the group synchronised.
+// The path walks take the bodies in order of tree level (bylev), so that the lanes of a
+// warp walk paths of about equal length.
 template <int G>
-__device__ double grebuild(int n, const double* __restrict__ m, const int* __restrict__ parent, const double* W,
-                           double* w, double Mtot, bool want_T, const GI& gi, double (*red)[kMaxG][3]) {
+__device__ double grebuild(int n, const double* __restrict__ m, const int* __restrict__ parent,
+                           const int* __restrict__ bylev, const double* W, double* w, double Mtot, bool want_T,
+                           const GI& gi, double (*red)[kMaxG][3]) {
   double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-  for (int v = gi.t; v < n; v += 32 * G) {
+  for (int i = gi.t; i < n; i += 32 * G) {
+    const int v = bylev[i];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     for (int u = v; parent[u] >= 0; u = parent[u]) {
       s0 = __dadd_rn(s0, W[3 * u]);
@@ -159,6 +163,79 @@ __device__ double grebuild(int n, const double* __restrict__ m, const int* __res
   gsum3<G>(t2, z1, z2, gi, red);
   return t2;
 }
+
+// x with its sign bit flipped when neg (an integer operation: no FP64 issue slot).
+__device__ __forceinline__ double flip(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+
+// The near partners of body p (tree distance <= n_d <= 2, Sec. 3.4) in the order parent,
+// children, grandparent, grandchildren (by child), siblings, each with the edges whose
+// vectors give the separation r_q - r_p: q = parent: -X_p; child: X_q; grandparent:
+// -(X_p + X_parent(p)); grandchild: X_q + X_parent(q); sibling: X_q - X_p. Integer work only.
+struct NearWalk {
+  int p, pp, g, stage, c, cend, ch, gc, gcend, sb, send;
+  __device__ __forceinline__ NearWalk(int p_, int n_d, const int* parent, const int* gp, const int* coff)
+      : p(p_), pp(parent[p_]), g(n_d >= 2 ? gp[p_] : -1), stage(0), c(coff[p_]), cend(coff[p_ + 1]), ch(-1),
+        gc(0), gcend(0), sb(0), send(0) {
+    if (n_d < 2) stage = 10;  // parent and children only
+  }
+  // next partner q and separation edges (ea with sign na, eb >= 0 with sign nb, or eb = -1)
+  __device__ __forceinline__ bool next(const int* cidx, const int* coff, int& q, int& ea, bool& na, int& eb, bool& nb) {
+    for (;;) {
+      switch (stage) {
+        case 0:
+        case 10:
+          stage += 1;
+          if (pp >= 0) {
+            q = pp; ea = p; na = true; eb = -1; nb = false;
+            return true;
+          }
+          break;
+        case 1:
+        case 11:
+          if (c < cend) {
+            q = cidx[c++]; ea = q; na = false; eb = -1; nb = false;
+            return true;
+          }
+          if (stage == 11) return false;
+          stage = 2;
+          break;
+        case 2:
+          stage = 3;
+          c = coff[p];
+          if (g >= 0) {
+            q = g; ea = p; na = true; eb = pp; nb = true;
+            return true;
+          }
+          break;
+        case 3:
+          while (gc == gcend && c < cend) {
+            ch = cidx[c++];
+            gc = coff[ch];
+            gcend = coff[ch + 1];
+          }
+          if (gc < gcend) {
+            q = cidx[gc++]; ea = q; na = false; eb = ch; nb = false;
+            return true;
+          }
+          stage = 4;
+          if (pp >= 0) {
+            sb = coff[pp];
+            send = coff[pp + 1];
+          }
+          break;
+        default:
+          while (sb < send && cidx[sb] == p) ++sb;
+          if (sb < send) {
+            q = cidx[sb++]; ea = q; na = false; eb = p; nb = true;
+            return true;
+          }
+          return false;
+      }
+    }
+  }
+};
 
 // One 32-block of partners and their accumulators, per warp.
 struct WarpShared {
@@ -212,12 +289,20 @@ __device__ double gforces(int n, int n_d, double Gc, const double* __restrict__ 
       sh.ay[lane] = 0.0;
       sh.az[lane] = 0.0;
       __syncwarp();
+      // A partner block with t < 32 bodies (the last one) is swept at width Wb = the power of
+      // two >= t: lane l pairs with slot (l + k) mod Wb, Wb steps (Wb/2 + 1 on the diagonal),
+      // and the 32 / Wb lane groups keep separate partner accumulators (added below in group
+      // order), so that no two lanes update the same accumulator at a step.
       const bool self = (I == J);
-      const int kbeg = self ? 1 : 0, kend = self ? 17 : 32;
+      const int tail = n - J * 32;
+      const int Wb = tail >= 32 ? 32 : (1 << (32 - __clz(tail - 1)));
+      const int cb = lane & ~(Wb - 1);
+      const int kbeg = self ? 1 : 0, kend = self ? Wb / 2 + 1 : Wb;
       for (int k = kbeg; k < kend; ++k) {
-        const int jl = (lane + k) & 31;
+        const int jl = (lane + k) & (Wb - 1);
+        const int ja = cb + jl;
         const int j = J * 32 + jl;
-        bool masked = ipad | (j >= n) | (self & (k == 16) & (lane >= 16));
+        bool masked = ipad | (j >= n) | (self & (k == Wb / 2) & ((lane & (Wb - 1)) >= Wb / 2));
         const int pj = sh.p[jl], gj = sh.g[jl];
         masked |= nd1 & ((pi == j) | (pj == i));
         masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
@@ -233,16 +318,22 @@ __device__ double gforces(int n, int n_d, double Gc, const double* __restrict__ 
         ayi = fma(sj, dy, ayi);
         azi = fma(sj, dz, azi);
         ui = fma(sh.mm[jl], rinv, ui);
-        sh.ax[jl] = fma(si, dx, sh.ax[jl]);
-        sh.ay[jl] = fma(si, dy, sh.ay[jl]);
-        sh.az[jl] = fma(si, dz, sh.az[jl]);
+        sh.ax[ja] = fma(si, dx, sh.ax[ja]);
+        sh.ay[ja] = fma(si, dy, sh.ay[ja]);
+        sh.az[ja] = fma(si, dz, sh.az[ja]);
         __syncwarp();
       }
       // body jb and body i of this item are only ever touched by this lane of this warp
       if (!jpad) {  // partner sums were kept with the opposite sign
-        a[3 * jb] -= sh.ax[lane];
-        a[3 * jb + 1] -= sh.ay[lane];
-        a[3 * jb + 2] -= sh.az[lane];
+        double sx = sh.ax[lane], sy = sh.ay[lane], sz = sh.az[lane];
+        for (int c = Wb; c < 32; c += Wb) {
+          sx += sh.ax[c + lane];
+          sy += sh.ay[c + lane];
+          sz += sh.az[c + lane];
+        }
+        a[3 * jb] -= sx;
+        a[3 * jb + 1] -= sy;
+        a[3 * jb + 2] -= sz;
       }
       if (!ipad) {
         a[3 * i] += axi;
@@ -253,44 +344,31 @@ __device__ double gforces(int n, int n_d, double Gc, const double* __restrict__ 
       __syncwarp();
     }
   }
-  // near pairs from edge vectors: parent, children, grandparent, grandchildren, siblings.
+  // near pairs from edge vectors: parent, children, grandparent, grandchildren, siblings,
+  // walked as one list per body (NearWalk) so that the FP64 part of a warp's loop runs as
+  // many times as its longest list, with the pair scalars on the integer pipe.
   // Body p goes to thread p mod 32G, i.e. lane p mod 32 of this warp: the same lane that
   // updated it in the loop above.
   if (n_d >= 1) {
     for (int p = gi.t; p < n; p += 32 * G) {
       double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
-      auto add = [&](int q2, double dx, double dy, double dz) {
-        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-        const double ri = rsqrt_fp64(r2);
-        const double s = m[q2] * ((ri * ri) * ri);
-        ax = fma(s, dx, ax);
-        ay = fma(s, dy, ay);
-        az = fma(s, dz, az);
-        if (q2 > p) u = fma(m[q2], ri, u);
-      };
-      const int pp = parent[p];
-      const double xp = X[3 * p], yp = X[3 * p + 1], zp = X[3 * p + 2];
-      if (pp >= 0) add(pp, -xp, -yp, -zp);
-      for (int c = coff[p]; c < coff[p + 1]; ++c) {
-        const int ch = cidx[c];
-        add(ch, X[3 * ch], X[3 * ch + 1], X[3 * ch + 2]);
-      }
-      if (n_d >= 2) {
-        const int g = gp[p];
-        if (g >= 0) add(g, -(xp + X[3 * pp]), -(yp + X[3 * pp + 1]), -(zp + X[3 * pp + 2]));
-        for (int c = coff[p]; c < coff[p + 1]; ++c) {
-          const int ch = cidx[c];
-          for (int e = coff[ch]; e < coff[ch + 1]; ++e) {
-            const int gc = cidx[e];
-            add(gc, X[3 * gc] + X[3 * ch], X[3 * gc + 1] + X[3 * ch + 1], X[3 * gc + 2] + X[3 * ch + 2]);
-          }
-        }
-        if (pp >= 0) {
-          for (int c = coff[pp]; c < coff[pp + 1]; ++c) {
-            const int sb = cidx[c];
-            if (sb != p) add(sb, X[3 * sb] - xp, X[3 * sb + 1] - yp, X[3 * sb + 2] - zp);
-          }
-        }
+      NearWalk nw(p, n_d, parent, gp, coff);
+      int q, ea, eb;
+      bool na, nb;
+      while (nw.next(cidx, coff, q, ea, na, eb, nb)) {
+        // d = r_q - r_p = (+/-) X_ea (+/-) X_eb, one rounding per component (as the
+        // edge-vector sums of the reference order: j side summed upward, minus the i side)
+        const double dx = __dadd_rn(flip(X[3 * ea], na), eb >= 0 ? flip(X[3 * eb], nb) : 0.0);
+        const double dy = __dadd_rn(flip(X[3 * ea + 1], na), eb >= 0 ? flip(X[3 * eb + 1], nb) : 0.0);
+        const double dz = __dadd_rn(flip(X[3 * ea + 2], na), eb >= 0 ? flip(X[3 * eb + 2], nb) : 0.0);
+        const double mq = m[q];
+        const MassSplit ms = mass_split(mq);
+        double rinv, sq, unused;
+        pair_scalars_int(dx, dy, dz, ms, ms, rinv, sq, unused);
+        ax = fma(sq, dx, ax);
+        ay = fma(sq, dy, ay);
+        az = fma(sq, dz, az);
+        if (q > p) u = fma(mq, rinv, u);
       }
       a[3 * p] += ax;
       a[3 * p + 1] += ay;
@@ -392,45 +470,55 @@ __device__ bool accept_or_halve(SysScalars* S, const BatchParams& P, int K, doub
   return false;
 }
 
-// One GBS step attempt for each of the `count` systems order[0 .. count-1].
+// Per-system view of the batch storage: body-major blocks of 3-vectors (field f of body v
+// at bd[f * n + 3 v + c]) and the integer tree arrays.
+struct SysView {
+  int n;
+  const double* m;
+  double* bd;
+  int *parent, *gp, *coff, *cidx;  // coff: n + 1 entries, cidx: n - 1 entries
+  int* bylev;                        // the bodies by tree level (ascending), then index
+  __device__ __forceinline__ double* F(int field) const { return bd + (size_t)field * n; }
+};
+
+__device__ __forceinline__ SysView sys_view(int s, const int* __restrict__ off, const double* __restrict__ mass,
+                                            double* body, int* ibody, int body_doubles) {
+  SysView V;
+  const int o = off[s];
+  V.n = off[s + 1] - o;
+  V.m = mass + o;
+  V.bd = body + (size_t)o * body_doubles;
+  int* ib = ibody + (size_t)o * 5;
+  V.parent = ib;
+  V.gp = ib + V.n;
+  V.coff = ib + 2 * V.n;
+  V.cidx = ib + 3 * V.n + 1;
+  V.bylev = ib + 4 * V.n;
+  return V;
+}
+
+// Start of an attempt, by a CTA of 128 G threads: the MST (Prim with exact FP64 keys) and
+// its children lists, the edge coordinates of the step start, the derivative information
+// (one force evaluation by group 0) and the step size. Leaves U0, T0, the attempt's H (Ha)
+// and go = 0 (system stops) or 1 in S; the caller synchronises before reading them.
 template <int G>
-__global__ void __launch_bounds__(128 * G)
-k_batched_step(int count, const int* __restrict__ order, const int* __restrict__ off, BatchParams P,
-               const double* __restrict__ tend, const double* __restrict__ mass, double* __restrict__ body,
-               int* __restrict__ ibody, SysScalars* __restrict__ sys, double* __restrict__ tdiv) {
+__device__ void attempt_begin(const SysView& V, SysScalars* S, const BatchParams& P, double t_end, WarpShared* wsh,
+                              unsigned long long* rk, int* ri, int* s_cnt, int* s_lev, double (*s_gred)[kMaxG][3]) {
   constexpr int NT = 128 * G, NW = 4 * G, VPT = kBMaxN / NT;
-  __shared__ WarpShared wsh[NW];
-  __shared__ unsigned long long rk[NW];
-  __shared__ int ri[NW];
-  __shared__ int s_cnt[kBMaxN + 1];
-  __shared__ double s_red[NW];
-  __shared__ double s_gred[kGroups][kMaxG][3];
-  __shared__ double s_scal[4];  // U0, T0, H, abort flag
-  if ((int)blockIdx.x >= count) return;
-  const int s = order[blockIdx.x];
-  SysScalars* S = sys + s;
-  if (S->status != 0) return;
-  const double t_end = *tend;
-  const int o = off[s], n = off[s + 1] - o;
+  const int n = V.n;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const GI gi{warp / G, warp % G, lane, (warp % G) * 32 + lane};
-  const int K = P.k_fix;
-  const double* m = mass + o;
-  double* bd = body + (size_t)o * P.body_doubles;
-  // body-major blocks of 3-vectors: field f of body v at bd[f * n + 3 v + c]
-  auto F = [&](int field) { return bd + (size_t)field * n; };
-  double* R = F(B_R);
-  double* Vs = F(B_V);
-  double* X0 = F(B_X0);
-  double* V0 = F(B_V0);
-  double* A0 = F(B_A0);
-  double* TKK = F(B_TKK);
-  int* ib = ibody + (size_t)o * 5;
-  int* parent = ib;
-  int* gp = ib + n;
-  int* coff = ib + 2 * n;       // n + 1 entries
-  int* cidx = ib + 3 * n + 1;   // n - 1 entries
-  const double t0 = S->t, B = S->B, Mtot = S->M;
+  const double* m = V.m;
+  double* R = V.F(B_R);
+  double* Vs = V.F(B_V);
+  double* X0 = V.F(B_X0);
+  double* V0 = V.F(B_V0);
+  double* A0 = V.F(B_A0);
+  int* parent = V.parent;
+  int* gp = V.gp;
+  int* coff = V.coff;
+  int* cidx = V.cidx;
+  const double t0 = S->t;
 
   // ---- MST (Prim with exact FP64 keys, one CTA) and the children lists
   {
@@ -507,6 +595,26 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
       }
     }
     __syncthreads();
+    // bodies by tree level (counting sort; ascending index within a level)
+    for (int v = tid; v < n; v += NT) {
+      int d = 0;
+      for (int w = parent[v]; w >= 0; w = parent[w]) ++d;
+      s_lev[v] = d;
+    }
+    for (int v = tid; v <= n; v += NT) s_cnt[v] = 0;
+    __syncthreads();
+    for (int v = tid; v < n; v += NT) atomicAdd(&s_cnt[s_lev[v]], 1);
+    __syncthreads();
+    if (tid == 0) {
+      int acc = 0;
+      for (int l = 0; l < n; ++l) {
+        const int c = s_cnt[l];
+        s_cnt[l] = acc;
+        acc += c;
+      }
+      for (int v = 0; v < n; ++v) V.bylev[s_cnt[s_lev[v]]++] = v;
+    }
+    __syncthreads();
   }
 
   // ---- edge coordinates of the step start
@@ -518,13 +626,9 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
     }
   }
   __syncthreads();
-  double* gX = F(B_GRP + gi.g * kGrpStride);
-  double* gV = gX + 3 * n;
-  double* gr = gX + 6 * n;
-  double* gv = gX + 9 * n;
-  double* ga = gX + 12 * n;
   // ---- derivative information of the step start (group 0) and the step size
   if (gi.g == 0) {
+    double* ga = V.F(B_GRP) + 12 * n;
     const double U0 = gforces<G>(n, P.n_d, P.G, m, parent, gp, coff, cidx, R, X0, ga, wsh[warp], gi, s_gred);
     double t2 = 0.0;
     for (int v = gi.t; v < n; v += 32 * G) {
@@ -539,68 +643,92 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
     if (gi.t == 0) {
       double Hs = 0.0;
       const bool abort_ = choose_step(S, P, t_end, t0, U0, &Hs);
-      s_scal[0] = U0;
-      s_scal[1] = T0;
-      s_scal[2] = Hs;
-      s_scal[3] = abort_ ? 1.0 : 0.0;
       S->U0 = U0;
       S->T0 = T0;
+      S->Ha = Hs;
+      S->go = abort_ ? 0 : 1;
     }
   }
-  __syncthreads();
-  if (s_scal[3] != 0.0) return;
-  {
-    const double T0 = s_scal[1], H = s_scal[2];
-    // ---- this group's divisions (greedy longest-first assignment to the four groups)
-    int load[kGroups] = {0, 0, 0, 0};
-    for (int k = K; k >= 1; --k) {
-      int gsel = 0;
-      for (int w = 1; w < kGroups; ++w)
-        if (load[w] < load[gsel]) gsel = w;
-      load[gsel] += 2 * k;
-      if (gsel != gi.g) continue;
-      const int nk = 2 * k;
-      const double delta = H / (double)nk;
-      double f = (0.5 * delta) / (T0 + B);
-      for (int v = gi.t; v < n; v += 32 * G)
-        for (int c = 0; c < 3; ++c) {
-          gX[3 * v + c] = madd(X0[3 * v + c], f, V0[3 * v + c]);
-          gV[3 * v + c] = V0[3 * v + c];
-        }
-      double t = t0 + f;
-      gsync<G>(gi.g);
-      grebuild<G>(n, m, parent, gX, gr, Mtot, false, gi, s_gred);
-      for (int tau = 1; tau <= nk; ++tau) {
-        const double U = gforces<G>(n, P.n_d, P.G, m, parent, gp, coff, cidx, gr, gX, ga, wsh[warp], gi, s_gred);
-        const double fk = delta / U;
-        for (int v = gi.t; v < n; v += 32 * G) {
-          const int p = parent[v];
-          if (p >= 0)
-            for (int c = 0; c < 3; ++c) gV[3 * v + c] = madd(gV[3 * v + c], fk, __dsub_rn(ga[3 * v + c], ga[3 * p + c]));
-        }
-        gsync<G>(gi.g);
-        const double T = 0.5 * grebuild<G>(n, m, parent, gV, gv, Mtot, true, gi, s_gred);
-        f = ((tau == nk) ? 0.5 * delta : delta) / (T + B);
-        for (int v = gi.t; v < n; v += 32 * G)
-          for (int c = 0; c < 3; ++c) gX[3 * v + c] = madd(gX[3 * v + c], f, gV[3 * v + c]);
-        t += f;
-        gsync<G>(gi.g);
-        if (tau < nk) grebuild<G>(n, m, parent, gX, gr, Mtot, false, gi, s_gred);
-      }
-      double* E = F(B_END + 6 * (k - 1));
-      for (int v = gi.t; v < n; v += 32 * G)
-        for (int c = 0; c < 3; ++c) {
-          E[3 * v + c] = gX[3 * v + c];
-          E[3 * n + 3 * v + c] = gV[3 * v + c];
-        }
-      if (gi.t == 0) tdiv[(size_t)s * kMaxKfix + (k - 1)] = t;
-      gsync<G>(gi.g);
-    }
-  }
-  __syncthreads();
+}
 
-  // ---- Aitken-Neville extrapolation and the error of Eq. gbs-criterion
-  const double H = s_scal[2], T0 = s_scal[1], U0 = s_scal[0];
+// The divisions of group gi.g (greedy longest-first assignment of the k_fix divisions to
+// the four groups, Sec. 4.2), by the group's G warps with group-level barriers only.
+template <int G>
+__device__ void attempt_divisions(const SysView& V, const SysScalars* S, const BatchParams& P, const GI& gi,
+                                  WarpShared& wsh, double (*s_gred)[kMaxG][3], double* tdiv_s) {
+  const int n = V.n, K = P.k_fix;
+  const double* m = V.m;
+  const double* X0 = V.F(B_X0);
+  const double* V0 = V.F(B_V0);
+  const int* parent = V.parent;
+  double* gX = V.F(B_GRP + gi.g * kGrpStride);
+  double* gV = gX + 3 * n;
+  double* gr = gX + 6 * n;
+  double* gv = gX + 9 * n;
+  double* ga = gX + 12 * n;
+  const double t0 = S->t, B = S->B, Mtot = S->M, T0 = S->T0, H = S->Ha;
+  int load[kGroups] = {0, 0, 0, 0};
+  for (int k = K; k >= 1; --k) {
+    int gsel = 0;
+    for (int w = 1; w < kGroups; ++w)
+      if (load[w] < load[gsel]) gsel = w;
+    load[gsel] += 2 * k;
+    if (gsel != gi.g) continue;
+    const int nk = 2 * k;
+    const double delta = H / (double)nk;
+    double f = (0.5 * delta) / (T0 + B);
+    for (int v = gi.t; v < n; v += 32 * G)
+      for (int c = 0; c < 3; ++c) {
+        gX[3 * v + c] = madd(X0[3 * v + c], f, V0[3 * v + c]);
+        gV[3 * v + c] = V0[3 * v + c];
+      }
+    double t = t0 + f;
+    gsync<G>(gi.g);
+    grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, false, gi, s_gred);
+    for (int tau = 1; tau <= nk; ++tau) {
+      const double U = gforces<G>(n, P.n_d, P.G, m, parent, V.gp, V.coff, V.cidx, gr, gX, ga, wsh, gi, s_gred);
+      const double fk = delta / U;
+      for (int v = gi.t; v < n; v += 32 * G) {
+        const int p = parent[v];
+        if (p >= 0)
+          for (int c = 0; c < 3; ++c) gV[3 * v + c] = madd(gV[3 * v + c], fk, __dsub_rn(ga[3 * v + c], ga[3 * p + c]));
+      }
+      gsync<G>(gi.g);
+      const double T = 0.5 * grebuild<G>(n, m, parent, V.bylev, gV, gv, Mtot, true, gi, s_gred);
+      f = ((tau == nk) ? 0.5 * delta : delta) / (T + B);
+      for (int v = gi.t; v < n; v += 32 * G)
+        for (int c = 0; c < 3; ++c) gX[3 * v + c] = madd(gX[3 * v + c], f, gV[3 * v + c]);
+      t += f;
+      gsync<G>(gi.g);
+      if (tau < nk) grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, false, gi, s_gred);
+    }
+    double* E = V.F(B_END + 6 * (k - 1));
+    for (int v = gi.t; v < n; v += 32 * G)
+      for (int c = 0; c < 3; ++c) {
+        E[3 * v + c] = gX[3 * v + c];
+        E[3 * n + 3 * v + c] = gV[3 * v + c];
+      }
+    if (gi.t == 0) tdiv_s[k - 1] = t;
+    gsync<G>(gi.g);
+  }
+}
+
+// End of an attempt, by a CTA of 128 G threads: Aitken-Neville extrapolation of the
+// division end states, the error of Eq. gbs-criterion, the step control and, when the
+// attempt is accepted, the deconstruction of the extrapolated edge vectors.
+template <int G>
+__device__ void attempt_finish(const SysView& V, SysScalars* S, const BatchParams& P, const double* tdiv_s,
+                               double* s_red, int* s_flag, double (*s_gred)[kMaxG][3]) {
+  constexpr int NT = 128 * G, NW = 4 * G;
+  const int n = V.n, K = P.k_fix;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const GI gi{warp / G, warp % G, lane, (warp % G) * 32 + lane};
+  const double* X0 = V.F(B_X0);
+  const double* V0 = V.F(B_V0);
+  const double* A0 = V.F(B_A0);
+  double* TKK = V.F(B_TKK);
+  const double t0 = S->t, B = S->B, Mtot = S->M;
+  const double H = S->Ha, T0 = S->T0, U0 = S->U0;
   const double rate = 1.0 / (T0 + B), delta = H / (double)(2 * K);
   auto neville = [&](const double* Sv, double& tkk, double& tprev) {
     double prev[kMaxKfix], cur[kMaxKfix];
@@ -617,16 +745,16 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
     double Sv[kMaxKfix], dX[3], dV[3];
     for (int c = 0; c < 3; ++c) {
       double tkk, tp = 0.0;
-      for (int k = 0; k < K; ++k) Sv[k] = F(B_END + 6 * k)[3 * v + c];
+      for (int k = 0; k < K; ++k) Sv[k] = V.F(B_END + 6 * k)[3 * v + c];
       neville(Sv, tkk, tp);
       TKK[3 * v + c] = tkk;
       dX[c] = __dsub_rn(tkk, tp);
-      for (int k = 0; k < K; ++k) Sv[k] = F(B_END + 6 * k)[3 * n + 3 * v + c];
+      for (int k = 0; k < K; ++k) Sv[k] = V.F(B_END + 6 * k)[3 * n + 3 * v + c];
       neville(Sv, tkk, tp);
       TKK[3 * n + 3 * v + c] = tkk;
       dV[c] = __dsub_rn(tkk, tp);
     }
-    if (parent[v] >= 0) {
+    if (V.parent[v] >= 0) {
       double q[3], g[3];
       for (int c = 0; c < 3; ++c) {
         q[c] = madd(X0[3 * v + c], delta, __dmul_rn(V0[3 * v + c], rate));
@@ -641,7 +769,7 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
   double tkk_t = 0.0;
   if (tid == 0) {
     double Sv[kMaxKfix], tp = 0.0;
-    for (int k = 0; k < K; ++k) Sv[k] = tdiv[(size_t)s * kMaxKfix + k];
+    for (int k = 0; k < K; ++k) Sv[k] = tdiv_s[k];
     neville(Sv, tkk_t, tp);
     e = nanmax(e, fabs(__dsub_rn(tkk_t, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300));
   }
@@ -651,16 +779,99 @@ k_batched_step(int count, const int* __restrict__ order, const int* __restrict__
   if (tid == 0) {
     double eps = s_red[0];
     for (int w = 1; w < NW; ++w) eps = nanmax(eps, s_red[w]);
-    s_scal[3] = accept_or_halve(S, P, K, eps, H, tkk_t) ? 1.0 : 0.0;
+    *s_flag = accept_or_halve(S, P, K, eps, H, tkk_t) ? 1 : 0;
   }
   __syncthreads();
-  if (s_scal[3] == 0.0) return;
+  if (*s_flag == 0) return;
   // ---- accept: deconstruct the extrapolated edge vectors into the Cartesian state
   if (gi.g < 2) {
-    double* dst = gi.g == 0 ? R : Vs;
+    double* dst = gi.g == 0 ? V.F(B_R) : V.F(B_V);
     const double* src = gi.g == 0 ? TKK : TKK + 3 * n;
-    grebuild<G>(n, m, parent, src, dst, Mtot, false, gi, s_gred);
+    grebuild<G>(n, V.m, V.parent, V.bylev, src, dst, Mtot, false, gi, s_gred);
   }
+}
+
+// All batched-step kernels take the same arguments, so that one argument list serves every
+// node of the graph.
+#define MSTAR_BSTEP_ARGS                                                                                    \
+  int count, const int *__restrict__ order, const int *__restrict__ off, BatchParams P,                     \
+      const double *__restrict__ tend, const double *__restrict__ mass, double *__restrict__ body,          \
+      int *__restrict__ ibody, SysScalars *__restrict__ sys, double *__restrict__ tdiv
+
+// One GBS step attempt for each of the `count` systems order[0 .. count-1], one CTA per
+// system: the whole CTA starts the attempt, its four groups run the divisions, the whole CTA
+// finishes it.
+template <int G>
+__global__ void __launch_bounds__(128 * G) k_batched_step(MSTAR_BSTEP_ARGS) {
+  __shared__ WarpShared wsh[4 * G];
+  __shared__ unsigned long long rk[4 * G];
+  __shared__ int ri[4 * G];
+  __shared__ int s_cnt[kBMaxN + 1];
+  __shared__ int s_lev[kBMaxN];
+  __shared__ double s_red[4 * G];
+  __shared__ double s_gred[kGroups][kMaxG][3];
+  __shared__ int s_flag;
+  if ((int)blockIdx.x >= count) return;
+  const int s = order[blockIdx.x];
+  SysScalars* S = sys + s;
+  if (S->status != 0) return;
+  const SysView V = sys_view(s, off, mass, body, ibody, P.body_doubles);
+  attempt_begin<G>(V, S, P, *tend, wsh, rk, ri, s_cnt, s_lev, s_gred);
+  __syncthreads();
+  if (S->go == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GI gi{warp / G, warp % G, lane, (warp % G) * 32 + lane};
+  attempt_divisions<G>(V, S, P, gi, wsh[warp], s_gred, tdiv + (size_t)s * kMaxKfix);
+  __syncthreads();
+  attempt_finish<G>(V, S, P, tdiv + (size_t)s * kMaxKfix, s_red, &s_flag, s_gred);
+}
+
+// The same attempt as three graph nodes, so that one system's four division groups run as
+// four CTAs (on up to four SMs) instead of one: the start (one CTA per system), the
+// divisions (one CTA of G warps per system and group; CTA 4 i + g runs group g of system
+// order[i]) and the finish (one CTA per system).
+template <int G>
+__global__ void __launch_bounds__(128 * G) k_bsplit_begin(MSTAR_BSTEP_ARGS) {
+  __shared__ WarpShared wsh[4 * G];
+  __shared__ unsigned long long rk[4 * G];
+  __shared__ int ri[4 * G];
+  __shared__ int s_cnt[kBMaxN + 1];
+  __shared__ int s_lev[kBMaxN];
+  __shared__ double s_gred[kGroups][kMaxG][3];
+  if ((int)blockIdx.x >= count) return;
+  const int s = order[blockIdx.x];
+  SysScalars* S = sys + s;
+  if (S->status != 0) return;
+  const SysView V = sys_view(s, off, mass, body, ibody, P.body_doubles);
+  attempt_begin<G>(V, S, P, *tend, wsh, rk, ri, s_cnt, s_lev, s_gred);
+}
+
+template <int G>
+__global__ void __launch_bounds__(32 * G) k_bsplit_div(MSTAR_BSTEP_ARGS) {
+  __shared__ WarpShared wsh[G];
+  __shared__ double s_gred[kGroups][kMaxG][3];
+  const int item = (int)(blockIdx.x >> 2), g = (int)(blockIdx.x & 3);
+  if (item >= count) return;
+  const int s = order[item];
+  const SysScalars* S = sys + s;
+  if (S->status != 0 || S->go == 0) return;
+  const SysView V = sys_view(s, off, mass, body, ibody, P.body_doubles);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const GI gi{g, warp, lane, warp * 32 + lane};
+  attempt_divisions<G>(V, S, P, gi, wsh[warp], s_gred, tdiv + (size_t)s * kMaxKfix);
+}
+
+template <int G>
+__global__ void __launch_bounds__(128 * G) k_bsplit_finish(MSTAR_BSTEP_ARGS) {
+  __shared__ double s_red[4 * G];
+  __shared__ double s_gred[kGroups][kMaxG][3];
+  __shared__ int s_flag;
+  if ((int)blockIdx.x >= count) return;
+  const int s = order[blockIdx.x];
+  SysScalars* S = sys + s;
+  if (S->status != 0 || S->go == 0) return;
+  const SysView V = sys_view(s, off, mass, body, ibody, P.body_doubles);
+  attempt_finish<G>(V, S, P, tdiv + (size_t)s * kMaxKfix, s_red, &s_flag, s_gred);
 }
 
 // ---------------------------------------------------------------------------- segment schedules
@@ -1092,7 +1303,9 @@ struct mstar_batch {
   // schedule: warps per division group for each size class, the systems of each schedule
   // (largest first) as consecutive segments of `order`, and the graph of one launch
   int sched[kNumClasses] = {};
-  int seg_begin[5] = {}, seg_count[5] = {};  // G = 1, 2, 4 and the 8- and 16-lane segment kernels
+  // node kinds: one CTA per system with G = 1, 2, 4; the 8- and 16-lane segment kernels; the
+  // split attempt (start, divisions, finish) with G = 1, 2, 4
+  int seg_begin[8] = {}, seg_count[8] = {};
   cudaGraphExec_t exec = nullptr;
   int graph_nodes = 0;
   double tend_h = NAN;
@@ -1166,11 +1379,15 @@ __global__ void k_scatter_vec(int nbody, const int* __restrict__ off, int nsys, 
   }
 }
 
-// Schedule values: 1, 2, 4 warps per division group (one CTA per system), or 0 for the size
-// classes of at most 16 bodies: groups of 8 (class 0) or 16 (class 1) lanes, one body per
-// lane. Node index: 0, 1, 2 for G = 1, 2, 4; 3 and 4 for the 8- and 16-lane kernels.
+// Schedule values: 1, 2, 4 warps per division group (one CTA per system); -1, -2, -4 for the
+// same groups with the attempt split into three nodes (one CTA per division group); 0 for
+// the size classes of at most 16 bodies: groups of 8 (class 0) or 16 (class 1) lanes, one
+// body per lane. Node kind: 0, 1, 2 for G = 1, 2, 4; 3 and 4 for the 8- and 16-lane
+// kernels; 5, 6, 7 for the split attempt with G = 1, 2, 4.
+constexpr int kNodeKinds = 8;
 int sched_index(int cls, int G) {
   if (G == 0) return cls == 0 ? 3 : (cls == 1 ? 4 : -1);
+  if (G < 0) return G == -1 ? 5 : (G == -2 ? 6 : (G == -4 ? 7 : -1));
   return G == 1 ? 0 : (G == 2 ? 1 : (G == 4 ? 2 : -1));
 }
 bool sched_ok(int cls, int G) { return sched_index(cls, G) >= 0; }
@@ -1187,9 +1404,9 @@ void destroy_graph(mstar_batch* b) {
   b->graph_nodes = 0;
 }
 
-// Order the systems by schedule (G = 1, 2, 4 segments), largest pair work first within a
-// segment, upload the order and build the graph: one independent kernel node per nonempty
-// segment, the widest schedule at the highest priority.
+// Order the systems by node kind, largest pair work first within a kind, upload the order
+// and build the graph: one independent kernel node per nonempty kind (a chain of three for
+// the split attempt), the widest groups at the highest priority.
 int apply_schedule(mstar_batch* b, const int* sched) {
   for (int c = 0; c < kNumClasses; ++c)
     if (!sched_ok(c, sched[c])) return MSTAR_ERR_INVALID_ARG;
@@ -1205,9 +1422,9 @@ int apply_schedule(mstar_batch* b, const int* sched) {
     if (gx != gy) return gx < gy;
     return (long long)n_of(x) * n_of(x) > (long long)n_of(y) * n_of(y);
   });
-  int begin[5] = {0, 0, 0, 0, 0}, count[5] = {0, 0, 0, 0, 0};
+  int begin[kNodeKinds] = {}, count[kNodeKinds] = {};
   for (int s = 0; s < b->nsys; ++s) count[g_of(s)]++;
-  for (int q = 1; q < 5; ++q) begin[q] = begin[q - 1] + count[q - 1];
+  for (int q = 1; q < kNodeKinds; ++q) begin[q] = begin[q - 1] + count[q - 1];
   if (cudaMemcpyAsync(b->order, ord.data(), sizeof(int) * b->nsys, cudaMemcpyHostToDevice, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return MSTAR_ERR_CUDA;
@@ -1218,35 +1435,50 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
   bool ok = true;
   int nodes = 0;
-  static const int node_order[5] = {2, 1, 0, 4, 3};  // widest groups first
-  for (int t = 0; t < 5 && ok; ++t) {
+  static const int node_order[kNodeKinds] = {7, 2, 6, 1, 5, 0, 4, 3};  // widest groups first
+  auto add_node = [&](void* func, dim3 grid, dim3 block, void** args, const cudaGraphNode_t* dep, int prio,
+                      cudaGraphNode_t* node) {
+    cudaKernelNodeParams kp{};
+    kp.func = func;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = 0;
+    kp.kernelParams = args;
+    if (cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp) != cudaSuccess) return false;
+    cudaLaunchAttributeValue pv{};
+    pv.priority = prio;
+    cudaGraphKernelNodeSetAttribute(*node, cudaLaunchAttributePriority, &pv);  // a hint; failure is harmless
+    nodes++;
+    return true;
+  };
+  for (int t = 0; t < kNodeKinds && ok; ++t) {
     const int qi = node_order[t];
     if (!count[qi]) continue;
     int cnt = count[qi];
     const int* ordp = b->order + begin[qi];
     void* args[] = {&cnt, (void*)&ordp, (void*)&b->off, (void*)&b->bp, (void*)&b->tend, (void*)&b->mass,
                     (void*)&b->body, (void*)&b->ibody, (void*)&b->sys, (void*)&b->tdiv};
-    cudaKernelNodeParams kp{};
-    if (qi >= 3) {
+    const int G = qi >= 5 ? 1 << (qi - 5) : 1 << qi;  // warps per division group (not used for 3, 4)
+    const int prio = G == 4 ? hi_prio : (G == 2 ? (hi_prio + lo_prio) / 2 : lo_prio);
+    cudaGraphNode_t n0, n1, n2;
+    if (qi == 3 || qi == 4) {
       const int per = mstar::kSegThreads / (4 * (qi == 3 ? 8 : 16));
-      kp.func = qi == 3 ? (void*)mstar::k_batched_seg<8> : (void*)mstar::k_batched_seg<16>;
-      kp.gridDim = dim3((cnt + per - 1) / per);
-      kp.blockDim = dim3(mstar::kSegThreads);
+      ok = add_node(qi == 3 ? (void*)mstar::k_batched_seg<8> : (void*)mstar::k_batched_seg<16>,
+                    dim3((cnt + per - 1) / per), dim3(mstar::kSegThreads), args, nullptr, lo_prio, &n0);
+    } else if (qi < 3) {
+      void* f = G == 1 ? (void*)mstar::k_batched_step<1> : (G == 2 ? (void*)mstar::k_batched_step<2>
+                                                                   : (void*)mstar::k_batched_step<4>);
+      ok = add_node(f, dim3(cnt), dim3(128 * G), args, nullptr, prio, &n0);
     } else {
-      kp.func = qi == 0 ? (void*)mstar::k_batched_step<1> : (qi == 1 ? (void*)mstar::k_batched_step<2>
-                                                                      : (void*)mstar::k_batched_step<4>);
-      kp.gridDim = dim3(cnt);
-      kp.blockDim = dim3(128 << qi);
-    }
-    kp.sharedMemBytes = 0;
-    kp.kernelParams = args;
-    cudaGraphNode_t node;
-    ok = cudaGraphAddKernelNode(&node, graph, nullptr, 0, &kp) == cudaSuccess;
-    if (ok) {
-      cudaLaunchAttributeValue pv{};
-      pv.priority = qi == 2 ? hi_prio : (qi == 1 ? (hi_prio + lo_prio) / 2 : lo_prio);
-      cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &pv);  // a hint; failure is harmless
-      nodes++;
+      void* fb = G == 1 ? (void*)mstar::k_bsplit_begin<1> : (G == 2 ? (void*)mstar::k_bsplit_begin<2>
+                                                                    : (void*)mstar::k_bsplit_begin<4>);
+      void* fd = G == 1 ? (void*)mstar::k_bsplit_div<1> : (G == 2 ? (void*)mstar::k_bsplit_div<2>
+                                                                  : (void*)mstar::k_bsplit_div<4>);
+      void* ff = G == 1 ? (void*)mstar::k_bsplit_finish<1> : (G == 2 ? (void*)mstar::k_bsplit_finish<2>
+                                                                     : (void*)mstar::k_bsplit_finish<4>);
+      ok = add_node(fb, dim3(cnt), dim3(128 * G), args, nullptr, prio, &n0) &&
+           add_node(fd, dim3(4 * cnt), dim3(32 * G), args, &n0, prio, &n1) &&
+           add_node(ff, dim3(cnt), dim3(128 * G), args, &n1, prio, &n2);
     }
   }
   cudaGetLastError();
@@ -1259,7 +1491,7 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   }
   b->graph_nodes = nodes;
   for (int c = 0; c < kNumClasses; ++c) b->sched[c] = sched[c];
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < kNodeKinds; ++q) {
     b->seg_begin[q] = begin[q];
     b->seg_count[q] = count[q];
   }
@@ -1495,11 +1727,11 @@ int mstar_batch_autotune(mstar_batch* b, double t_end, int repeats, int* schedul
   if (!rc) rc = trial(cur, &cur_ms);
   // two passes of coordinate descent, largest class first: each class keeps the schedule
   // that gave the shortest launch with the other classes fixed
-  static const int widths[4] = {1, 2, 4, 0};
+  static const int widths[7] = {1, 2, 4, 0, -1, -2, -4};
   for (int pass = 0; pass < 2 * kNumClasses && !rc; ++pass) {
     const int c = kNumClasses - 1 - pass % kNumClasses;
     if (!present[c]) continue;
-    for (int q = 0; q < 4 && !rc; ++q) {
+    for (int q = 0; q < 7 && !rc; ++q) {
       if (widths[q] == cur[c] || !sched_ok(c, widths[q])) continue;
       int cand[kNumClasses];
       for (int x = 0; x < kNumClasses; ++x) cand[x] = cur[x];

@@ -391,7 +391,7 @@ def mstar_batch_free(b):
 
 
 class Batch:
-    """Many independent systems integrated together (one CTA per system per launch); device
+    """Many independent systems integrated together (one or four CTAs per system per launch); device
     memory from torch, work on the torch stream current at construction."""
 
     def __init__(self, systems, device=None, **params):

@@ -52,7 +52,8 @@ def step_sizes(systems):
 
 
 SCHEDULES = {"default": None, "g1": [1] * 7, "g2": [2] * 7, "g4": [4] * 7, "mixed": [4, 2, 1, 4, 2, 1, 2],
-             "segments": [0, 0, 2, 1, 1, 1, 2]}
+             "segments": [0, 0, 2, 1, 1, 1, 2], "split1": [-1] * 7, "split2": [-2] * 7, "split4": [-4] * 7,
+             "split_mixed": [0, -4, 1, -1, -2, 2, -4]}
 
 
 @pytest.mark.parametrize("name", list(SCHEDULES))
@@ -76,6 +77,26 @@ def test_one_launch_matches_oracle_attempt(name):
         if a["eps"] > 1e-11:
             assert abs(S["eps"][s] - a["eps"]) <= 1e-2 * a["eps"], (s, S["eps"][s], a["eps"])
     b.close()
+
+
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_split_attempt_is_bit_identical_to_one_cta(G):
+    """The split schedule -G runs the same arithmetic as the one-CTA schedule G: start, the
+    four groups' divisions and the finish, with the same partial sums in the same order."""
+    systems = mixed_systems()
+    H = step_sizes(systems)
+    out = []
+    for sched in ([G] * 7, [-G] * 7):
+        b = M.Batch(systems)
+        b.set_schedule(sched)
+        b.set_H(H)
+        b.step(1e9, launches=3)
+        out.append(b.state())
+        b.close()
+    for key in ("t", "eps", "status"):
+        assert np.array_equal(out[0][key], out[1][key]), key
+    for s in range(len(systems)):
+        assert np.array_equal(out[0]["r"][s], out[1]["r"][s]) and np.array_equal(out[0]["v"][s], out[1]["v"][s]), s
 
 
 def test_batch_integrates_to_end_time_like_the_oracle():
@@ -120,7 +141,7 @@ def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
     b.set_H(H)
     before = b.state()
     sched, ms = b.autotune(1e9, repeats=1)
-    assert ms > 0 and set(sched.tolist()) <= {0, 1, 2, 4}
+    assert ms > 0 and set(sched.tolist()) <= {0, 1, 2, 4, -1, -2, -4}
     assert list(b.schedule()) == sched.tolist()
     after = b.state()
     for key in ("t", "eps", "status"):
@@ -140,7 +161,8 @@ def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
 def test_batch_rejects_bad_schedule():
     b = M.Batch([W.plummer(10, 1)])
     assert list(b.schedule()) == [0, 0, 1, 1, 1, 2, 4]
-    for bad in ([1, 2, 3, 4, 1, 1, 1], [0, 0, 0, 1, 1, 1, 1]):  # width 3; segments above 16 bodies
+    # width 3; segments above 16 bodies; split width 3
+    for bad in ([1, 2, 3, 4, 1, 1, 1], [0, 0, 0, 1, 1, 1, 1], [1, 1, 1, -3, 1, 1, 1]):
         with pytest.raises(M.MstarError) as e:
             b.set_schedule(bad)
         assert e.value.code == M.MSTAR_ERR_INVALID_ARG
