@@ -166,9 +166,20 @@ def cpu_baseline_sample(n_threads):
     dt = time.perf_counter() - t0
     n = len(m)
     pairs = 73 * n * (n - 1)
+    # the same oracle on one core: one pair-loop evaluation of the same state
+    oracle.set_threads(1)
+    st = s.state()
+    root, parent, level, order = oracle.prim(st["r"])
+    X = oracle.to_mst(parent, st["r"])
+    t1 = time.perf_counter()
+    oracle.forces(m, st["r"], parent, level, X)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(n_threads)
     return {"value": pairs / dt, "unit": "pair-forces/s", "cores": n_threads, "kind": "oracle",
             "sample": f"one GBS step attempt (73 pair-loop evaluations, Prim, rebuilds, extrapolation) of "
-                      f"the N={n} workload at H={H}, {dt:.2f} s wall on {n_threads} threads"}
+                      f"the N={n} workload at H={H}, {dt:.2f} s wall on {n_threads} threads",
+            "single_core": {"value": n * (n - 1) / dt1, "unit": "pair-forces/s", "cores": 1,
+                            "sample": f"one oracle pair-loop evaluation of the N={n} state, {dt1:.2f} s"}}
 
 
 def run_reference(args):
@@ -261,8 +272,12 @@ def run_batched(args, dev, M, W, torch, world=1, rank=0):
            "system_attempts_per_s": att / (ms * 1e-3), "failed": st1["failed"],
            "schedule": {"warps_per_division_group_by_size_class": sched.tolist(),
                         "size_classes": "[2,8] [9,16] [17,32] [33,64] [65,128] [129,256] [257,512]",
+                        "values": "G > 0: one CTA per system, four division groups of G warps; -G: the same "
+                                  "groups as one CTA each (start, divisions, finish nodes); 0: 8- or 16-lane "
+                                  "groups, one body per lane",
                         "autotune_launch_ms": tune_ms},
-           "launch": "one CUDA graph launch per attempt (one kernel node per group width)"}
+           "launch": "one CUDA graph launch per attempt (independent kernel nodes per schedule kind; a chain "
+                     "of three for a split schedule)"}
     if args.no_single_context or rank != 0:
         return out
     # the single-system path, one context per system, on every 128th system
@@ -545,6 +560,10 @@ def run_mstar(args):
                 "peak_probe_tflops": 2.0 * fma_rate / 1e12,
                 "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
                 "pair_kernel_share_of_step": prof.pair_ms / ms if ms > 0 else None,
+                # the whole timed step (every kernel of the hot path, rejected attempts and the
+                # L2 flush included) against the same ceiling
+                "whole_step_tflops": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12,
+                "whole_step_frac": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12 / peak,
                 "ordered_pair_28flop_equiv_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * prof.pair_interactions
                 / (prof.pair_ms * 1e-3) / 1e12 if prof.pair_ms > 0 else None}
 

@@ -86,6 +86,14 @@ __device__ __forceinline__ double warp_sum(double x) {
 
 __device__ __forceinline__ double madd(double a, double f, double b) { return __dadd_rn(a, __dmul_rn(f, b)); }
 
+// S / M from rM = 1/M (rounded) and one residual correction (Markstein's method): three FP64
+// instructions instead of a full division, and the correctly rounded quotient except in rare
+// cases next to a rounding boundary, where it is one unit in the last place away.
+__device__ __forceinline__ double quot(double S, double M, double rM) {
+  const double q = S * rM;
+  return fma(fma(-q, M, S), rM, q);
+}
+
 // Barrier over the 32 G threads of group g (named barrier g + 1; 0 is __syncthreads).
 template <int G>
 __device__ __forceinline__ void gsync(int g) {
@@ -94,6 +102,20 @@ __device__ __forceinline__ void gsync(int g) {
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(32 * G) : "memory");
   }
+}
+
+// Sum of one value over the group, added warp by warp in a fixed order.
+template <int G>
+__device__ __forceinline__ double gsum1(double a, const GI& gi, double (*red)[kMaxG][3]) {
+  a = warp_sum(a);
+  if constexpr (G > 1) {
+    if (gi.lane == 0) red[gi.g][gi.w][0] = a;
+    gsync<G>(gi.g);
+    a = red[gi.g][0][0];
+    for (int q = 1; q < G; ++q) a += red[gi.g][q][0];
+    gsync<G>(gi.g);
+  }
+  return a;
 }
 
 // Sums of three values over the group, added warp by warp in a fixed order.
@@ -127,8 +149,8 @@ __device__ __forceinline__ void gsum3(double& a, double& b, double& c, const GI&
 // warp walk paths of about equal length.
 template <int G>
 __device__ double grebuild(int n, const double* __restrict__ m, const int* __restrict__ parent,
-                           const int* __restrict__ bylev, const double* W, double* w, double Mtot, bool want_T,
-                           const GI& gi, double (*red)[kMaxG][3]) {
+                           const int* __restrict__ bylev, const double* W, double* w, double Mtot, double rM,
+                           bool want_T, const GI& gi, double (*red)[kMaxG][3]) {
   double c0 = 0.0, c1 = 0.0, c2 = 0.0;
   for (int i = gi.t; i < n; i += 32 * G) {
     const int v = bylev[i];
@@ -146,9 +168,9 @@ __device__ double grebuild(int n, const double* __restrict__ m, const int* __res
     c2 += __dmul_rn(m[v], s2);
   }
   gsum3<G>(c0, c1, c2, gi, red);
-  c0 = c0 / Mtot;
-  c1 = c1 / Mtot;
-  c2 = c2 / Mtot;
+  c0 = quot(c0, Mtot, rM);
+  c1 = quot(c1, Mtot, rM);
+  c2 = quot(c2, Mtot, rM);
   double t2 = 0.0;
   for (int v = gi.t; v < n; v += 32 * G) {
     const double q0 = __dsub_rn(w[3 * v], c0), q1 = __dsub_rn(w[3 * v + 1], c1), q2 = __dsub_rn(w[3 * v + 2], c2);
@@ -159,9 +181,7 @@ __device__ double grebuild(int n, const double* __restrict__ m, const int* __res
   }
   gsync<G>(gi.g);
   if (!want_T) return 0.0;
-  double z1 = 0.0, z2 = 0.0;
-  gsum3<G>(t2, z1, z2, gi, red);
-  return t2;
+  return gsum1<G>(t2, gi, red);
 }
 
 // x with its sign bit flipped when neg (an integer operation: no FP64 issue slot).
@@ -386,9 +406,7 @@ __device__ double gforces(int n, int n_d, double Gc, const double* __restrict__ 
     }
   }
   gsync<G>(gi.g);
-  double z1 = 0.0, z2 = 0.0;
-  gsum3<G>(usum, z1, z2, gi, red);
-  return Gc * usum;
+  return Gc * gsum1<G>(usum, gi, red);
 }
 
 template <int NW>
@@ -637,9 +655,7 @@ __device__ void attempt_begin(const SysView& V, SysScalars* S, const BatchParams
       const int p = parent[v];
       for (int c = 0; c < 3; ++c) A0[3 * v + c] = p >= 0 ? __dsub_rn(ga[3 * v + c], ga[3 * p + c]) : 0.0;
     }
-    double z1 = 0.0, z2 = 0.0;
-    gsum3<G>(t2, z1, z2, gi, s_gred);
-    const double T0 = 0.5 * t2;
+    const double T0 = 0.5 * gsum1<G>(t2, gi, s_gred);
     if (gi.t == 0) {
       double Hs = 0.0;
       const bool abort_ = choose_step(S, P, t_end, t0, U0, &Hs);
@@ -666,7 +682,7 @@ __device__ void attempt_divisions(const SysView& V, const SysScalars* S, const B
   double* gr = gX + 6 * n;
   double* gv = gX + 9 * n;
   double* ga = gX + 12 * n;
-  const double t0 = S->t, B = S->B, Mtot = S->M, T0 = S->T0, H = S->Ha;
+  const double t0 = S->t, B = S->B, Mtot = S->M, T0 = S->T0, H = S->Ha, rM = 1.0 / Mtot;
   int load[kGroups] = {0, 0, 0, 0};
   for (int k = K; k >= 1; --k) {
     int gsel = 0;
@@ -684,7 +700,7 @@ __device__ void attempt_divisions(const SysView& V, const SysScalars* S, const B
       }
     double t = t0 + f;
     gsync<G>(gi.g);
-    grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, false, gi, s_gred);
+    grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, rM, false, gi, s_gred);
     for (int tau = 1; tau <= nk; ++tau) {
       const double U = gforces<G>(n, P.n_d, P.G, m, parent, V.gp, V.coff, V.cidx, gr, gX, ga, wsh, gi, s_gred);
       const double fk = delta / U;
@@ -694,13 +710,13 @@ __device__ void attempt_divisions(const SysView& V, const SysScalars* S, const B
           for (int c = 0; c < 3; ++c) gV[3 * v + c] = madd(gV[3 * v + c], fk, __dsub_rn(ga[3 * v + c], ga[3 * p + c]));
       }
       gsync<G>(gi.g);
-      const double T = 0.5 * grebuild<G>(n, m, parent, V.bylev, gV, gv, Mtot, true, gi, s_gred);
+      const double T = 0.5 * grebuild<G>(n, m, parent, V.bylev, gV, gv, Mtot, rM, true, gi, s_gred);
       f = ((tau == nk) ? 0.5 * delta : delta) / (T + B);
       for (int v = gi.t; v < n; v += 32 * G)
         for (int c = 0; c < 3; ++c) gX[3 * v + c] = madd(gX[3 * v + c], f, gV[3 * v + c]);
       t += f;
       gsync<G>(gi.g);
-      if (tau < nk) grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, false, gi, s_gred);
+      if (tau < nk) grebuild<G>(n, m, parent, V.bylev, gX, gr, Mtot, rM, false, gi, s_gred);
     }
     double* E = V.F(B_END + 6 * (k - 1));
     for (int v = gi.t; v < n; v += 32 * G)
@@ -787,7 +803,7 @@ __device__ void attempt_finish(const SysView& V, SysScalars* S, const BatchParam
   if (gi.g < 2) {
     double* dst = gi.g == 0 ? V.F(B_R) : V.F(B_V);
     const double* src = gi.g == 0 ? TKK : TKK + 3 * n;
-    grebuild<G>(n, V.m, V.parent, V.bylev, src, dst, Mtot, false, gi, s_gred);
+    grebuild<G>(n, V.m, V.parent, V.bylev, src, dst, Mtot, 1.0 / Mtot, false, gi, s_gred);
   }
 }
 
@@ -909,11 +925,11 @@ __device__ __forceinline__ void sys_sync(int slot) {
 // Path sums of the edge vectors W up the tree (vertex first, root excluded), then the
 // centre-of-mass shift; returns sum m |w|^2 of the group's bodies after the shift.
 template <int WD>
-__device__ double seg_rebuild(const Seg<WD>& sg, bool live, double mv, int par, const double W[3], double w[3],
-                              double Mtot) {
+__device__ double seg_rebuild(const Seg<WD>& sg, bool live, double mv, int par, int depth, const double W[3],
+                              double w[3], double Mtot, double rM) {
   double s0 = 0.0, s1 = 0.0, s2 = 0.0;
   int u = live ? sg.l : -1;
-  for (int it = 0; it < WD; ++it) {
+  for (int it = 0; it < depth; ++it) {  // depth: the tree's largest level
     const int su = u >= 0 ? u : 0;
     const double w0 = sg.get(W[0], su), w1 = sg.get(W[1], su), w2 = sg.get(W[2], su);
     const int pu = sg.get(par, su);
@@ -924,8 +940,9 @@ __device__ double seg_rebuild(const Seg<WD>& sg, bool live, double mv, int par, 
     }
     u = (u >= 0) ? pu : -1;
   }
-  const double c0 = sg.sum(live ? __dmul_rn(mv, s0) : 0.0) / Mtot, c1 = sg.sum(live ? __dmul_rn(mv, s1) : 0.0) / Mtot,
-               c2 = sg.sum(live ? __dmul_rn(mv, s2) : 0.0) / Mtot;
+  const double c0 = quot(sg.sum(live ? __dmul_rn(mv, s0) : 0.0), Mtot, rM),
+               c1 = quot(sg.sum(live ? __dmul_rn(mv, s1) : 0.0), Mtot, rM),
+               c2 = quot(sg.sum(live ? __dmul_rn(mv, s2) : 0.0), Mtot, rM);
   w[0] = __dsub_rn(s0, c0);
   w[1] = __dsub_rn(s1, c1);
   w[2] = __dsub_rn(s2, c2);
@@ -1004,6 +1021,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
   __shared__ double s_t[PER][kMaxKfix];
   __shared__ double s_scal[PER][4];
   __shared__ double s_err[PER][4 * WD / 32];
+  __shared__ int s_dep[PER];
   const int slot = threadIdx.x / (4 * WD), lt = threadIdx.x % (4 * WD);
   Seg<WD> sg;
   sg.g = lt / WD;
@@ -1022,7 +1040,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
   double* bd = body + (size_t)o * P.body_doubles;
   double* Rg = bd + (size_t)B_R * n;
   double* Vg = bd + (size_t)B_V * n;
-  const double t0 = S->t, B = S->B, Mtot = S->M;
+  const double t0 = S->t, B = S->B, Mtot = S->M, rM = 1.0 / Mtot;
   const int l = sg.l;
   const bool live = l < n;
   const double mv = live ? m[l] : 0.0;
@@ -1065,8 +1083,16 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
       if (s_par[slot][nx] < 0) s_par[slot][nx] = root;
       u = nx;
     }
+    int dep = 0;
+    for (int w = 0; w < n; ++w) {
+      int d = 0;
+      for (int x = s_par[slot][w]; x >= 0; x = s_par[slot][x]) ++d;
+      dep = d > dep ? d : dep;
+    }
+    s_dep[slot] = dep;
   }
   sys_sync<WD>(slot);
+  const int depth = s_dep[slot];
   const int par = live ? s_par[slot][l] : -3;
   const int gpar = par >= 0 ? s_par[slot][par] : (live ? -1 : -3);
   // ---- edge coordinates and derivative information of the step start (every group)
@@ -1119,7 +1145,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
       V[c] = V0[c];
     }
     double t = t0 + f;
-    seg_rebuild<WD>(sg, live, mv, par, X, r, Mtot);
+    seg_rebuild<WD>(sg, live, mv, par, depth, X, r, Mtot, rM);
     for (int step = 0; step < steps; ++step) {
       const bool active = step < mine;
       const double U = seg_forces<WD>(sg, n, P.n_d, P.G, mv, par, gpar, r, X, a);
@@ -1128,7 +1154,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
         const double ap = sg.get(a[c], par >= 0 ? par : 0);
         if (par >= 0) V[c] = madd(V[c], fk, __dsub_rn(a[c], ap));
       }
-      const double T = 0.5 * seg_rebuild<WD>(sg, live, mv, par, V, v, Mtot);
+      const double T = 0.5 * seg_rebuild<WD>(sg, live, mv, par, depth, V, v, Mtot, rM);
       const bool last = sub == nk - 1;
       f = (last ? 0.5 * delta : delta) / (T + B);
       for (int c = 0; c < 3; ++c) X[c] = madd(X[c], f, V[c]);
@@ -1156,7 +1182,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
       } else {
         ++sub;
       }
-      if (step + 1 < steps) seg_rebuild<WD>(sg, live, mv, par, X, r, Mtot);
+      if (step + 1 < steps) seg_rebuild<WD>(sg, live, mv, par, depth, X, r, Mtot, rM);
     }
   }
   sys_sync<WD>(slot);
@@ -1214,7 +1240,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
   if (sg.g < 2) {
     double W[3], w[3];
     for (int c = 0; c < 3; ++c) W[c] = live ? s_T[slot][3 * sg.g + c][l] : 0.0;
-    seg_rebuild<WD>(sg, live, mv, par, W, w, Mtot);
+    seg_rebuild<WD>(sg, live, mv, par, depth, W, w, Mtot, rM);
     if (live)
       for (int c = 0; c < 3; ++c) (sg.g ? Vg : Rg)[3 * l + c] = w[c];
   }
