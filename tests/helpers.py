@@ -11,6 +11,21 @@ import math
 import numpy as np
 
 
+GOLDEN = __import__("os").path.join(__import__("os").path.dirname(__file__), "golden")
+
+
+def golden(name):
+    """Values the paper prints, from tests/golden/<name>.txt (each file cites its passage):
+    one `key value [unit]` per line, '#' starts a comment."""
+    out = {}
+    with open(f"{GOLDEN}/{name}.txt") as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out[line[0]] = float(line[1])
+    return out
+
+
 def two_body_invariants(m1, m2, r, v, G=1.0):
     """Energy E, angular momentum L and Laplace-Runge-Lenz vector A of the relative orbit
     (Sec. 5.1: E = mu v^2/2 - G mu M/r, L = mu r x v). A is taken with the specific angular

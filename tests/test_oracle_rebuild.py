@@ -20,7 +20,7 @@ from scipy.integrate import quad
 import oracle as O
 from paper_2001_03180_gb300 import workloads as W
 
-from tests.helpers import edge_set, mst_kruskal, sqdist
+from tests.helpers import edge_set, golden, mst_kruskal, sqdist
 
 
 def tree_length(r, parent):
@@ -73,7 +73,8 @@ def test_chain_levels_against_mst_levels():
             assert lev_c.mean() == (n - 1) / 2
             rs.append(lev_c.mean() / lev_m.mean())
         ratios.append(float(np.mean(rs)))
-    assert 1.5 < ratios[0] < 3.5, ratios
+    gd = golden("mst_claims")
+    assert 0.75 * gd["chain_over_mst_mean_level_low"] < ratios[0] < 1.75 * gd["chain_over_mst_mean_level_low"], ratios
     assert ratios[0] < ratios[1] < ratios[2], ratios
 
 
@@ -147,7 +148,9 @@ def test_rebuild_mst_accumulates_less_error_than_chain_with_root_kept():
             out = O.rebuild_run(m, r, v, coords, 1000, 500, [0, 1000], 1)
             acc.append(abs(out["E"][1] / out["E"][0] - 1))
             assert out["topo_changes"] == 0
-    assert np.mean(chn) > 3 * np.mean(mst), (np.mean(chn), np.mean(mst))
+    # the paper reads an order of magnitude at 1e5 rebuilds; at 1e3 a factor 3 is asked
+    assert np.mean(chn) > 0.3 * golden("mst_claims")["rebuild_chain_over_mst_error"] * np.mean(mst), \
+        (np.mean(chn), np.mean(mst))
 
 
 def test_chain_end_tie_joins_the_tail():
