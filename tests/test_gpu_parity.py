@@ -305,6 +305,49 @@ def test_invalid_inputs_are_rejected():
     assert e.value.code == M.MSTAR_ERR_INVALID_ARG
 
 
+def test_size_limit_and_coincident_bodies():
+    """Degenerate inputs: one body above MSTAR_MAX_N is refused; two coincident bodies make
+    the force undefined, and the step ends with NO_CONVERGENCE after max_halvings
+    rejections with the state untouched, as in the oracle (no silent non-finite state)."""
+    n = M.MSTAR_MAX_N + 1
+    st = W.Stream(3, 1)
+    m = np.full(n, 1.0 / n)
+    r = st.uniform(3 * n).reshape(n, 3)
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m, r, np.zeros_like(r))
+    assert e.value.code in (M.MSTAR_ERR_UNSUPPORTED, M.MSTAR_ERR_INVALID_ARG)
+    m = np.array([1.0, 1.0, 1.0])
+    r = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [1.0, 0.0, 0.0]])
+    v = np.zeros((3, 3))
+    v[0, 1] = 0.3
+    o = O.System(m, r, v)
+    rco, sto = o.integrate(1.0)
+    assert rco == M.MSTAR_ERR_NO_CONVERGENCE and sto["accepted"] == 0
+    g = M.Integrator(m, r, v)
+    before = g.state()
+    with pytest.raises(M.MstarError) as e:
+        g.step(1.0)
+    assert e.value.code == M.MSTAR_ERR_NO_CONVERGENCE
+    after = g.state()
+    assert np.array_equal(before["r"], after["r"]) and np.array_equal(before["v"], after["v"])
+    g.close()
+    # in a batch the degenerate system fails alone
+    good = W.plummer(20, 4)
+    b = M.Batch([good, (m, r, v), W.kepler_binary(seed=3)])
+    for _ in range(40):
+        sb = b.step(0.01, launches=5)
+        if sb["finished"] == 3:
+            break
+    S = b.state()
+    assert S["status"].tolist() == [1, -3, 1] and sb["failed"] == 1
+    assert np.isfinite(S["r"][1]).all() and np.isfinite(S["v"][1]).all()
+    for s_idx, sysd in ((0, good), (2, W.kepler_binary(seed=3))):
+        oo = O.System(*sysd)
+        assert oo.integrate(0.01)[0] == 0
+        assert relerr(S["r"][s_idx], oo.state()["r"]) < 1e-9
+    b.close()
+
+
 def test_device_pointer_inputs_and_outputs():
     m, r, v = SYS["plummer257"]
     dev = torch.device("cuda")
