@@ -75,6 +75,7 @@ size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
   t.root = c.take<int>(1);
   t.child_off = c.take<int>(np + 1);
   t.child_idx = c.take<int>(np);
+  t.bylev = c.take<int>(np);
   t.X0 = c.take<double>(n3);
   t.V0 = c.take<double>(n3);
   t.A0 = c.take<double>(n3);

@@ -30,6 +30,7 @@ struct Dev {
   int* root;        // [1]
   int* child_off;   // [npad + 1] CSR of children
   int* child_idx;   // [npad]
+  int* bylev;       // [npad] the bodies in order of tree level, then index (path-sum order)
   double* X0;       // edge vectors of the step start (3 planes)
   double* V0;
   double* A0;       // relative accelerations a_v - a_parent(v) at the step start

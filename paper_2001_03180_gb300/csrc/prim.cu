@@ -288,10 +288,12 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
   }
 }
 
-// Grandparents and the children lists (CSR, each list in ascending index) of the tree.
+// Grandparents, the children lists (CSR, each list in ascending index) and the bodies in
+// order of (level, index) of the tree. The last is a bitonic sort of the keys level * 2^14
+// + index (n <= 2^14) in shared memory.
 __global__ void __launch_bounds__(1024, 1)
-k_tree(int n, int npad, const int* __restrict__ parent, int* __restrict__ gp, int* __restrict__ child_off,
-       int* __restrict__ child_idx) {
+k_tree(int n, int npad, const int* __restrict__ parent, const int* __restrict__ level, int* __restrict__ gp,
+       int* __restrict__ child_off, int* __restrict__ child_idx, int* __restrict__ bylev) {
   extern __shared__ int sm_i[];
   int* cnt = sm_i;        // n
   int* pos = cnt + n;     // n
@@ -354,6 +356,28 @@ k_tree(int n, int npad, const int* __restrict__ parent, int* __restrict__ gp, in
       child_idx[c + 1] = x;
     }
   }
+  // (level, index) order; the keys reuse cnt and pos (P <= 2n entries)
+  __syncthreads();
+  int P = 1;
+  while (P < n) P <<= 1;
+  unsigned* key = reinterpret_cast<unsigned*>(sm_i);
+  for (int i = tid; i < P; i += nt) key[i] = i < n ? ((unsigned)level[i] << 14) | (unsigned)i : 0xffffffffu;
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < P; i += nt) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned a = key[i], b = key[l];
+          if ((a > b) == ((i & k) == 0)) {
+            key[i] = b;
+            key[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = tid; i < npad; i += nt) bylev[i] = i < n ? (int)(key[i] & 0x3fffu) : i;
 }
 
 template <int VPT>
@@ -395,7 +419,8 @@ cudaError_t launch_tree(mstar_ctx* c) {
   size_t smem = (size_t)c->n * 2 * sizeof(int);
   cudaError_t e = cudaFuncSetAttribute(k_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_tree<<<1, 1024, smem, c->stream>>>(c->n, c->npad, c->d.parent, c->d.gp, c->d.child_off, c->d.child_idx);
+  k_tree<<<1, 1024, smem, c->stream>>>(c->n, c->npad, c->d.parent, c->d.level, c->d.gp, c->d.child_off,
+                                       c->d.child_idx, c->d.bylev);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
 }

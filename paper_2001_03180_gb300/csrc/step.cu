@@ -162,13 +162,16 @@ k_drift(int npad, int slot_lo, double H, double B, int tau, double* __restrict__
 // Cartesian vector of every body from edge vectors: the path sum w_v = W_v + W_parent(v)
 // + ... up to the root (root: 0), plus block sums of m w for the centre of mass.
 __global__ void __launch_bounds__(kBlock)
-k_rebuild(int n, int npad, size_t stride, const int* __restrict__ parent, const double* __restrict__ Wb,
-          double* __restrict__ wb, const double* __restrict__ m, double* __restrict__ comblk, int nblk) {
+k_rebuild(int n, int npad, size_t stride, const int* __restrict__ parent, const int* __restrict__ bylev,
+          const double* __restrict__ Wb, double* __restrict__ wb, const double* __restrict__ m,
+          double* __restrict__ comblk, int nblk) {
   __shared__ double scratch[32];
   const int slot = blockIdx.y;
   const double* W = Wb + slot * stride;
   double* wv = wb + slot * stride;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  // thread i takes body bylev[i]: the lanes of a warp walk paths of about equal length
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = i < n ? bylev[i] : n;
   double s[3] = {0.0, 0.0, 0.0};
   if (v < n) {
     for (int u = v; parent[u] >= 0; u = parent[u]) {
@@ -380,7 +383,8 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
                            double* Tblk_base, double* comblk_base) {
   if (nsl <= 0) return cudaSuccess;
   dim3 grid(c->nblk, nsl);
-  k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, W, w, c->d.m, comblk_base, c->nblk);
+  k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w, c->d.m,
+                                            comblk_base, c->nblk);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
