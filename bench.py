@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-rebuild-test", action="store_true")
     ap.add_argument("--batched-schedule", default=None,
                     help="comma-separated schedule per size class instead of the autotuner's (profiling)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the single-system extras (small configurations, tree builders, rebuild test, adjoint)")
     ap.add_argument("--no-single-context", action="store_true",
                     help="skip timing the one-context-per-system path beside the batch")
     return ap.parse_args()
@@ -576,7 +578,7 @@ def run_mstar(args):
             batched = run_batched(args, dev, M, W, torch, world, rank)
     # the single-system extras (no data-path collective) run in single-GPU runs only, so that
     # a multi-GPU run holds its GPUs for the timed work and the sharded batch alone
-    extras = world == 1
+    extras = world == 1 and not args.no_extras
     small = None
     if extras:
         with torch.cuda.stream(stream):
