@@ -317,7 +317,12 @@ int vectors_out(mstar_ctx* c, const double* planes, double* dst) {
   return MSTAR_OK;
 }
 
-int choose_tile_warps(int n) { return n <= 512 ? 1 : 4; }
+// Pair tile of 32 W bodies by system size, from a sweep of full GBS steps on Plummer spheres
+// (pair-forces/s): below ~4000 bodies the 32-body tiles give the most CTAs per slot (+18 %
+// at N = 2050 over 128-body tiles); up to ~8000 the 64-body tiles; above, the 128-body
+// tiles keep the partial sums (slots x tiles x 4 x npad doubles) a quarter as large at the
+// same speed.
+int choose_tile_warps(int n) { return n <= 4096 ? 1 : (n <= 8192 ? 2 : 4); }
 
 size_t workspace_bytes(int n, const mstar_params& p, int* npad_out, int* W_out) {
   Shape s = shape_of(n, p);
