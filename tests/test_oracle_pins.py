@@ -203,6 +203,20 @@ def test_two_body_force_closed_form():
     assert U == pytest.approx(2.0 * 6.0 / 5.0, rel=1e-16)
 
 
+def test_kinetic_and_potential_closed_forms():
+    """Sec. 2.1: T = sum m v^2 / 2 and U = sum_{i<j} G m_i m_j / r_ij, on configurations
+    with exact values: three bodies on a 3-4-5 triangle (U = G (m0 m1/5 + m0 m2/3 + m1 m2/4))
+    and velocities of integer components; the system's E = T - U and zero P, L at rest."""
+    m = np.array([2.0, 3.0, 4.0])
+    r = np.array([[0.0, 0.0, 0.0], [3.0, 4.0, 0.0], [3.0, 0.0, 0.0]])
+    v = np.array([[1.0, 0.0, 0.0], [0.0, -2.0, 0.0], [0.0, 0.0, 3.0]])
+    assert O.kinetic(m, v) == 0.5 * (2.0 * 1.0 + 3.0 * 4.0 + 4.0 * 9.0)
+    assert O.potential(m, r, G=1.5) == pytest.approx(1.5 * (6.0 / 5.0 + 8.0 / 3.0 + 12.0 / 4.0), rel=1e-15)
+    e = O.System(m, r, np.zeros_like(v)).energy()
+    assert e["E"] == pytest.approx(-(6.0 / 5.0 + 8.0 / 3.0 + 12.0 / 4.0), rel=1e-15)
+    assert np.abs(e["P"]).max() == 0.0 and np.abs(e["L"]).max() == 0.0
+
+
 def test_forces_newton_third_law_and_near_rule_consistency():
     m, r, v = W.plummer_smbh_binary(300, 2)
     _, parent, level, _ = O.prim(r)
