@@ -51,3 +51,27 @@ def test_no_cpu_fallback_in_product_path():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "mstar_oracle" not in text, f
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the built library every entry point raises: there is no fallback path."""
+    monkeypatch.setattr(M, "_lib", None)
+    monkeypatch.setattr(M, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libmstar.so"))
+    with pytest.raises(ImportError):
+        M.load()
+    with pytest.raises(ImportError):
+        M.mstar_default_params()
+
+
+def test_no_gpu_means_no_integrator():
+    """On a machine without a CUDA GPU the integrator refuses to start instead of running
+    anything on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = [1.0, 1.0]
+    r = [[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]]
+    v = [[0.0, 0.0, 0.0], [0.0, 1.0, 0.0]]
+    for make in (lambda: M.Integrator(m, r, v), lambda: M.Batch([(m, r, v)])):
+        with pytest.raises(RuntimeError):
+            make()
