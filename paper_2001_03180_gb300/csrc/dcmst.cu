@@ -502,13 +502,23 @@ k_dc_meta_prim(int n, const int* __restrict__ ncell, int mc, const DcEdge* __res
   for (int it = 1; it < nc; ++it) {
     DcEdge bk{~0ull, INT_MAX, INT_MAX};
     int bg = INT_MAX;
-    for (int g = lane; g < nc; g += 32) {
-      if (in[g]) continue;
-      const DcEdge c = u < g ? W[(size_t)u * mc + g] : W[(size_t)g * mc + u];
-      if (key[g].i < 0 || dc_less(c, key[g])) key[g] = c;
-      if (bg == INT_MAX || dc_less(key[g], bk)) {
-        bk = key[g];
-        bg = g;
+    // four weights per lane are loaded together, then folded in ascending g
+    for (int g0 = lane; g0 < nc; g0 += 128) {
+      DcEdge cs[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int g = g0 + 32 * t;
+        cs[t] = (g < nc && !in[g]) ? (u < g ? W[(size_t)u * mc + g] : W[(size_t)g * mc + u]) : DcEdge{~0ull, -1, -1};
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int g = g0 + 32 * t;
+        if (g >= nc || in[g]) continue;
+        if (key[g].i < 0 || dc_less(cs[t], key[g])) key[g] = cs[t];
+        if (bg == INT_MAX || dc_less(key[g], bk)) {
+          bk = key[g];
+          bg = g;
+        }
       }
     }
     for (int o = 16; o > 0; o >>= 1) {
