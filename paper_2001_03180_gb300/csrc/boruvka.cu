@@ -205,23 +205,25 @@ __global__ void k_boruvka_init(int n, const double* __restrict__ X, const double
 }
 
 // Orient the tree from Prim's root: adjacency from the edge list, then a breadth-first
-// walk in one CTA (levels are tree depths, independent of the visiting order).
+// walk in one CTA (levels are tree depths, independent of the visiting order). The
+// adjacency, the visited marks and the queue live in shared memory (5n + 1 ints).
 __global__ void __launch_bounds__(1024, 1)
 k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, const double* __restrict__ Z,
          const int* __restrict__ eu, const int* __restrict__ ev, int* __restrict__ adj_off, int* __restrict__ adj,
          int* __restrict__ parent, int* __restrict__ level, int* __restrict__ root_out, int* __restrict__ queue) {
   extern __shared__ int smi[];
-  int* deg = smi;       // n
-  int* fill = deg + n;  // n
+  int* s_off = smi;           // n + 1
+  int* s_adj = s_off + n + 1; // 2 (n - 1)
+  int* s_a = s_adj + 2 * n;   // n: degrees, then the parents
+  int* s_q = s_a + n;         // n: fill counters, then the queue
   __shared__ unsigned long long rk[32];
   __shared__ int ri[32];
-  __shared__ int qhead, qtail, lvl_end;
+  __shared__ int part[1024];
+  __shared__ int qtail;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int v = tid; v < n; v += nt) {
-    deg[v] = 0;
-    fill[v] = 0;
-    parent[v] = -2;
-    level[v] = 0;
+    s_a[v] = 0;
+    s_q[v] = 0;
   }
   // root: closest to the origin (COM frame), lowest index on ties
   unsigned long long bk = ~0ull;
@@ -255,53 +257,83 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
         ri[0] = ri[w];
       }
   }
+  // (endpoints outside [0, n) cannot come from the tree builders; they are skipped so that
+  // no shared-memory index leaves its array)
   for (int e = tid; e < n - 1; e += nt) {
-    atomicAdd(&deg[eu[e]], 1);
-    atomicAdd(&deg[ev[e]], 1);
+    const int a = eu[e], b = ev[e];
+    if ((unsigned)a < (unsigned)n && (unsigned)b < (unsigned)n) {
+      atomicAdd(&s_a[a], 1);
+      atomicAdd(&s_a[b], 1);
+    }
   }
   __syncthreads();
   const int root = ri[0];
+  // exclusive scan of the degrees: contiguous chunks per thread, then the chunk sums
+  const int chunk = (n + nt - 1) / nt;
+  const int b0 = tid * chunk, b1 = min(n, b0 + chunk);
+  int sum = 0;
+  for (int v = b0; v < b1; ++v) sum += s_a[v];
+  part[tid] = sum;
+  __syncthreads();
   if (tid == 0) {
     int acc = 0;
-    for (int v = 0; v < n; ++v) {
-      adj_off[v] = acc;
-      acc += deg[v];
+    for (int t = 0; t < nt; ++t) {
+      const int x = part[t];
+      part[t] = acc;
+      acc += x;
     }
-    adj_off[n] = acc;
-    root_out[0] = root;
-    parent[root] = -1;
-    level[root] = 0;
-    queue[0] = root;
-    qhead = 0;
-    qtail = 1;
+    s_off[n] = acc;
+  }
+  __syncthreads();
+  sum = part[tid];
+  for (int v = b0; v < b1; ++v) {
+    s_off[v] = sum;
+    sum += s_a[v];
   }
   __syncthreads();
   for (int e = tid; e < n - 1; e += nt) {
     const int a = eu[e], b = ev[e];
-    adj[adj_off[a] + atomicAdd(&fill[a], 1)] = b;
-    adj[adj_off[b] + atomicAdd(&fill[b], 1)] = a;
+    if ((unsigned)a < (unsigned)n && (unsigned)b < (unsigned)n) {
+      s_adj[s_off[a] + atomicAdd(&s_q[a], 1)] = b;
+      s_adj[s_off[b] + atomicAdd(&s_q[b], 1)] = a;
+    }
   }
   __syncthreads();
+  for (int v = tid; v < n; v += nt) s_a[v] = -2;  // not yet reached
+  __syncthreads();
+  if (tid == 0) {
+    s_a[root] = -1;
+    s_q[0] = root;
+    qtail = 1;
+    root_out[0] = root;
+  }
+  __syncthreads();
+  int h = 0, depth = 0;
   while (true) {
-    const int h = qhead, t = qtail;
+    const int t = min(qtail, n);
     if (h >= t) break;
-    __syncthreads();
-    if (tid == 0) lvl_end = t;
     for (int q = h + tid; q < t; q += nt) {
-      const int u = queue[q];
-      for (int a = adj_off[u]; a < adj_off[u + 1]; ++a) {
-        const int w = adj[a];
-        if (parent[w] == -2) {
-          parent[w] = u;
-          level[w] = level[u] + 1;
-          queue[atomicAdd(&qtail, 1)] = w;
+      const int u = s_q[q];
+      level[u] = depth;
+      for (int a = s_off[u]; a < s_off[u + 1]; ++a) {
+        const int w = s_adj[a];
+        if (s_a[w] == -2) {  // a tree: w is reached from u only
+          s_a[w] = u;
+          const int slot = atomicAdd(&qtail, 1);
+          if (slot < n) s_q[slot] = w;
         }
       }
     }
-    __syncthreads();
-    if (tid == 0) qhead = lvl_end;
+    h = t;
+    ++depth;
     __syncthreads();
   }
+  for (int v = tid; v < n; v += nt) {
+    parent[v] = s_a[v];
+    queue[v] = s_q[v];
+  }
+  for (int v = tid; v <= n; v += nt) adj_off[v] = s_off[v];
+  for (int a = tid; a < 2 * (n - 1); a += nt) adj[a] = s_adj[a];
 }
 
 }  // namespace
@@ -311,7 +343,7 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
 cudaError_t launch_orient(mstar_ctx* c, const int* eu, const int* ev, int* adj_off, int* adj, int* queue) {
   const int n = c->n;
   const double* X = c->d.r;
-  const size_t smem = sizeof(int) * 2 * (size_t)n;
+  const size_t smem = sizeof(int) * (5 * (size_t)n + 1);
   cudaError_t e = cudaFuncSetAttribute(k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_orient<<<1, 1024, smem, c->stream>>>(n, X, X + c->npad, X + 2 * (size_t)c->npad, eu, ev, adj_off, adj,
@@ -388,13 +420,7 @@ cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
     *tied = true;
     return cudaSuccess;
   }
-  const size_t smem = sizeof(int) * 2 * (size_t)n;
-  if ((e = cudaFuncSetAttribute(k_orient, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
-  k_orient<<<1, 1024, smem, c->stream>>>(n, X, Y, Z, eu, ev, adj_off, adj, c->d.parent, c->d.level, c->d.root,
-                                         queue);
-  MSTAR_LAUNCHED(c);
-  return cudaGetLastError();
+  return launch_orient(c, eu, ev, adj_off, adj, queue);
 }
 
 }  // namespace mstar

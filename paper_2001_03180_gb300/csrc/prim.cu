@@ -363,17 +363,28 @@ k_tree(int n, int npad, const int* __restrict__ parent, const int* __restrict__ 
   unsigned* key = reinterpret_cast<unsigned*>(sm_i);
   for (int i = tid; i < P; i += nt) key[i] = i < n ? ((unsigned)level[i] << 14) | (unsigned)i : 0xffffffffu;
   __syncthreads();
+  // each thread takes compare-exchange pairs p = tid, tid + nt, ...: i = the p-th index with
+  // bit j clear, partner i + j; four pairs at a time so that their loads overlap
   for (int k = 2; k <= P; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < P; i += nt) {
-        const int l = i ^ j;
-        if (l > i) {
-          const unsigned a = key[i], b = key[l];
-          if ((a > b) == ((i & k) == 0)) {
-            key[i] = b;
-            key[l] = a;
+      for (int p0 = tid; p0 < P / 2; p0 += 4 * nt) {
+        unsigned a[4], b[4];
+        int ii[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int p = p0 + t * nt;
+          ii[t] = 2 * p - (p & (j - 1));
+          if (p < P / 2) {
+            a[t] = key[ii[t]];
+            b[t] = key[ii[t] + j];
           }
         }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (p0 + t * nt < P / 2 && (a[t] > b[t]) == ((ii[t] & k) == 0)) {
+            key[ii[t]] = b[t];
+            key[ii[t] + j] = a[t];
+          }
       }
       __syncthreads();
     }
