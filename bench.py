@@ -34,10 +34,10 @@ WORKLOAD_DESC = ("Plummer N=10000 (m=1e-4, r_vir=1, seed 5) + 2 SMBHs of 0.005 a
 # two mass scalings 2, force function 2, two 3-vector accumulations 12.
 FLOPS_PER_UNORDERED_PAIR = 33
 # FP64-pipe instructions the tiled kernel issues per unordered pair (3 DADD for the
-# separation, 7 DFMA for the force function and the accumulations; ncu counts
-# 3.0 DADD and 7.0 DFMA per pair). r^2, 1/r, 1/r^3 and the mass products run exactly on the
-# integer pipe, so the binding FP64 pipe caps this kernel at FP64 issue rate / 10 pairs.
-FP64_INSTR_PER_PAIR = 10
+# separation, 6 DFMA for the two force accumulations; ncu counts 3.0 DADD and 5.95 DFMA per
+# pair). r^2, 1/r, 1/r^3, the mass products and the force-function sum run on the integer
+# pipe, so the binding FP64 pipe caps this kernel at FP64 issue rate / 9 pairs.
+FP64_INSTR_PER_PAIR = 9
 # Flops of one ordered pair-force evaluated on its own, without the i<->j symmetry (3 DADD,
 # r^2 and a Newton-refined reciprocal square root, the mass scalings, 3 DFMA accumulations, U),
 # reported beside the symmetric count for comparison.
@@ -51,7 +51,7 @@ NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) of one tiled-pair force evaluation at N = 10002, from the ncu
 # capture summarised in profiles/pair_tiles_plummer10k.md; None once the kernel changes.
-PAIR_TILE_DRAM_BYTES_PER_EVAL = 436224 + 0
+PAIR_TILE_DRAM_BYTES_PER_EVAL = 440320 + 0
 
 
 def parse():
@@ -545,7 +545,7 @@ def run_mstar(args):
     achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = 2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / 1e12
-    # ceiling of this kernel: the FP64 pipe (2 instructions/clk/SM) saturated with its 10
+    # ceiling of this kernel: the FP64 pipe (2 instructions/clk/SM) saturated with its 9
     # FP64 instructions per pair, times the 33 algorithmic flops each pair carries
     peak = DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / FP64_INSTR_PER_PAIR * FLOPS_PER_UNORDERED_PAIR / 1e12
     evals_per_launch = prof.force_evals / max(prof.pair_launches, 1)
@@ -553,9 +553,9 @@ def run_mstar(args):
                if PAIR_TILE_DRAM_BYTES_PER_EVAL is not None else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_pair_tiles (symmetric pair loop: FP64 separations and accumulations, "
-                          "exact integer-pipe r^2, 1/r, m/r^3)",
-                "peak_source": ("derived: FP64 pipe 2 instr/clk/SM x 152 SMs x sampled SM clock / 10 FP64 "
+                "kernel": "k_pair_tiles (symmetric pair loop: FP64 separations and force accumulations; "
+                          "integer-pipe r^2, 1/r, m/r^3 and the exact fixed-point sum of m/r)",
+                "peak_source": ("derived: FP64 pipe 2 instr/clk/SM x 152 SMs x sampled SM clock / 9 FP64 "
                                 "instr per pair x 33 algorithmic flops per pair"),
                 "fp64_fma_peak_tflops": fp64_peak,
                 "frac_of_fp64_fma_peak": achieved / fp64_peak,

@@ -115,15 +115,21 @@ __device__ __forceinline__ unsigned long long sig_of(double x, int& e) {
   return e ? m : 0ull;
 }
 
-__device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz, const MassSplit& mj,
-                                                 const MassSplit& mi, double& rinv, double& sj, double& si) {
+// The core of the pair scalars: 1/r as Rn 2^eR (Rn in [2^63, 2^64), about 60 correct bits)
+// and the two mass scalings rounded to doubles. Coincident bodies (r = 0, force undefined)
+// give Rn = 0 and NaN scalings.
+__device__ __forceinline__ void pair_scalars_core(double dx, double dy, double dz, const MassSplit& mj,
+                                                  const MassSplit& mi, unsigned long long& Rn_out, int& eR_out,
+                                                  double& sj, double& si) {
   int ex, ey, ez;
   const unsigned long long mx = sig_of(dx, ex), my = sig_of(dy, ey), mz = sig_of(dz, ez);
   const int E = max(ex, max(ey, ez));
   // r^2 = F * 2^(2E - 2106); each aligned square is below 2^62, so F < 2^64
   const unsigned long long F = sq_top(mx, 2 + 2 * (E - ex)) + sq_top(my, 2 + 2 * (E - ey)) + sq_top(mz, 2 + 2 * (E - ez));
   if (F == 0ull) {  // coincident bodies: the force is undefined
-    rinv = sj = si = __longlong_as_double(0x7ff8000000000000LL);
+    sj = si = __longlong_as_double(0x7ff8000000000000LL);
+    Rn_out = 0ull;
+    eR_out = 0;
     return;
   }
   const int z = __clzll((long long)F);
@@ -148,7 +154,8 @@ __device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz
   const int zR = __clzll((long long)Rh);                   // 41..43
   const unsigned long long Rn = (Rh << zR) | (Rl >> (64 - zR));
   const int eR = 64 - zR + eyf - 212 - k;                  // 1/r = Rn 2^eR
-  rinv = u64_to_double(Rn, eR);
+  Rn_out = Rn;
+  eR_out = eR;
   const unsigned long long R2 = __umul64hi(Rn, Rn);        // [2^62, 2^64)
   const unsigned long long R3 = __umul64hi(R2, Rn);        // [2^61, 2^64); 1/r^3 = R3 2^(3 eR + 128)
   unsigned long long S = __umul64hi(mj.m, R3);
@@ -158,6 +165,70 @@ __device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz
   zs = __clzll((long long)S);
   si = u64_to_double(S << zs, mi.e + 3 * eR + 192 - zs);
 }
+
+__device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz, const MassSplit& mj,
+                                                 const MassSplit& mi, double& rinv, double& sj, double& si) {
+  unsigned long long Rn;
+  int eR;
+  pair_scalars_core(dx, dy, dz, mj, mi, Rn, eR, sj, si);
+  rinv = Rn ? u64_to_double(Rn, eR) : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+// ---------------------------------------------------------------------------------------
+// Exact sums of positive terms on the integer pipe.
+//
+// Each term is P 2^e with P < 2^64 (a truncated 64-bit product of significands). The sum is
+// kept as a 128-bit integer A times 2^L. The window follows the largest term: a term would
+// land above bit 120 slides it up (A shifted right, L raised), so the largest term sits at
+// bits 56..119 and 256 terms cannot overflow. Terms more than 2^120 below the largest lose
+// their low bits, far below a binary64 rounding of the sum.
+struct UAcc {
+  unsigned long long a0 = 0ull, a1 = 0ull;
+  int L = -(1 << 29);  // no term yet: the first one slides the window to it
+
+  __device__ __forceinline__ void add(unsigned long long P, int e) {
+    int s = e - L;
+    if (s > 56) {
+      const int d = s - 56;
+      if (d >= 128) {
+        a0 = 0ull;
+        a1 = 0ull;
+      } else if (d >= 64) {
+        a0 = a1 >> (d - 64);
+        a1 = 0ull;
+      } else {
+        a0 = (a0 >> d) | (a1 << (64 - d));
+        a1 >>= d;
+      }
+      L += d;
+      s = 56;
+    }
+    unsigned long long lo, hi;
+    if (s >= 0) {
+      lo = P << s;
+      hi = s ? P >> (64 - s) : 0ull;
+    } else {
+      lo = s > -64 ? P >> (-s) : 0ull;
+      hi = 0ull;
+    }
+    a0 += lo;
+    a1 += hi + (a0 < lo ? 1ull : 0ull);
+  }
+
+  // the sum to a double: the top 64 bits rounded by u64_to_double (about 2^-64 relative)
+  __device__ __forceinline__ double value() const {
+    if (a1) {
+      const int z = __clzll((long long)a1);
+      const unsigned long long top = z ? (a1 << z) | (a0 >> (64 - z)) : a1;
+      return u64_to_double(top, L + 64 - z);
+    }
+    if (a0) {
+      const int z = __clzll((long long)a0);
+      return u64_to_double(a0 << z, L - z);
+    }
+    return 0.0;
+  }
+};
 
 // Non-negative doubles order like their bit patterns.
 __device__ __forceinline__ unsigned long long key_bits(double x) {

@@ -7,9 +7,11 @@
 // GB300. Near pairs are masked out of the tiles with integer compares on parent and
 // grandparent indices and summed in a sparse pass with the edge-vector separations.
 //
-// Per pair the FP64 pipe issues only the separation (3 DADD), the force-function term
-// (1 DFMA) and the two force accumulations (6 DFMA); r^2, 1/r, 1/r^3 and the mass products
-// run on the integer pipe (pair_scalars_int), which the FP64-bound loop leaves idle.
+// Per pair the FP64 pipe issues only the separation (3 DADD) and the two force
+// accumulations (6 DFMA); r^2, 1/r, 1/r^3 and the mass products run on the integer pipe
+// (pair_scalars_core), and so does the force-function sum: m_j / r is a 64-bit product of
+// significands added exactly into a 128-bit fixed-point accumulator (UAcc) and rounded to a
+// double once per tile.
 //
 // Tiles: the N bodies form NT tiles of T = 32*W. CTA (I, J), I <= J, owns the I-tile as
 // "i" bodies (one per thread, accumulators in registers) and stages the J-tile ("j"
@@ -46,7 +48,7 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
              const int* __restrict__ parent, const int* __restrict__ gp, const double* __restrict__ sr,
              double* __restrict__ P) {
   constexpr int T = 32 * W;
-  __shared__ double sx[T], sy[T], sz[T], sm[T], sax[T], say[T], saz[T];
+  __shared__ double sx[T], sy[T], sz[T], sax[T], say[T], saz[T];
   __shared__ unsigned long long smm[T];
   __shared__ int sp[T], sg[T], sme[T];
 
@@ -61,7 +63,6 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
   sx[tid] = rx[j0 + tid];
   sy[tid] = ry[j0 + tid];
   sz[tid] = rz[j0 + tid];
-  sm[tid] = m[j0 + tid];
   {
     const MassSplit ms = mass_split(m[j0 + tid]);
     smm[tid] = ms.m;
@@ -78,7 +79,9 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
   const int pi = parent[i], gpi = gp[i];
   const bool i_pad = i >= n;
   const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
-  double axi = 0.0, ayi = 0.0, azi = 0.0, ui = 0.0;
+  double axi = 0.0, ayi = 0.0, azi = 0.0;
+  UAcc uacc;          // sum over j of m_j / r_ij
+  bool ubad = false;  // a coincident pair: the force is undefined
   const bool diag = (I == J);
   __syncthreads();
 
@@ -93,7 +96,7 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
       for (int k = kbeg; k < kend; ++k) {
         const int jl = sub * 32 + ((lane + k) & 31);
         const int j = j0 + jl;
-        const double xj = sx[jl], yj = sy[jl], zj = sz[jl], mj = sm[jl];
+        const double xj = sx[jl], yj = sy[jl], zj = sz[jl];
         const int pj = sp[jl], gj = sg[jl];
         bool masked = i_pad | (j >= n) | (self & (k == 16) & (lane >= 16));
         masked |= nd1 & ((pi == j) | (pj == i));
@@ -102,16 +105,21 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
         // keep the separations in registers: recomputing them for the accumulations would
         // cost three more FP64 instructions per pair
         asm volatile("" : "+d"(dx), "+d"(dy), "+d"(dz));
-        double rinv, sj, si;
-        pair_scalars_int(dx, dy, dz, MassSplit{smm[jl], sme[jl]}, msi, rinv, sj, si);
+        unsigned long long Rn;
+        int eR;
+        double sj, si;
+        const unsigned long long mjm = smm[jl];
+        const int mje = sme[jl];
+        pair_scalars_core(dx, dy, dz, MassSplit{mjm, mje}, msi, Rn, eR, sj, si);
         // masked pairs contribute nothing (integer selects on the bit patterns)
-        rinv = __longlong_as_double(masked ? 0ll : __double_as_longlong(rinv));
         sj = __longlong_as_double(masked ? 0ll : __double_as_longlong(sj));
         si = __longlong_as_double(masked ? 0ll : __double_as_longlong(si));
+        ubad |= !masked && Rn == 0ull;
+        // m_j / r = mjm Rn 2^(mje + eR) ~ hi64(mjm Rn) 2^(mje + eR + 64)
+        uacc.add(masked ? 0ull : __umul64hi(mjm, Rn), masked ? uacc.L : mje + eR + 64);
         axi = fma(sj, dx, axi);
         ayi = fma(sj, dy, ayi);
         azi = fma(sj, dz, azi);
-        ui = fma(mj, rinv, ui);
         // j-side sums are kept with the opposite sign and negated once when written
         sax[jl] = fma(si, dx, sax[jl]);
         say[jl] = fma(si, dy, say[jl]);
@@ -122,6 +130,7 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
     __syncthreads();
   }
 
+  const double ui = ubad ? __longlong_as_double(0x7ff8000000000000LL) : uacc.value();
   double* Ps = P + (size_t)slot * NT * 4 * npad;
   if (diag) {
     double* q = Ps + (size_t)I * 4 * npad + i;

@@ -169,6 +169,35 @@ def test_rsqrt_across_exponent_range(n_d):
             g.close()
 
 
+def test_force_function_sum_over_a_wide_range_of_terms():
+    """U = sum m_i m_j / r_ij when the terms span ~25 decades inside the same tiles: a unit
+    cluster with a 1e-9 pair at its centre, a far group at 1e6, masses from 1e-6 to 1
+    (n_d = 0, so every pair goes through the tiled loop and its fixed-point sum). Against
+    math.fsum of the float64 terms (each within ~2 ulp): GPU and oracle both to 1e-14."""
+    n = 300
+    st = W.Stream(21, 4)
+    r = (st.uniform(3 * n).reshape(n, 3) - 0.5) * 2.0
+    r[1] = r[0] + np.array([1e-9, 0.0, 0.0])
+    r[250:] = r[250:] * 10.0 + 1e6
+    m = 10.0 ** (-6.0 * st.uniform(n))
+    m[0] = m[1] = 1.0
+    v = np.zeros((n, 3))
+    g = M.Integrator(m, r, v, n_d=0)
+    _, U = g.accelerations()
+    rs = g.state()["r"]
+    g.close()
+    terms = []
+    for i in range(n):
+        d = rs[i + 1:] - rs[i]
+        rr = np.sqrt((d * d).sum(axis=1))
+        terms.extend((m[i] * m[i + 1:] / rr).tolist())
+    import math
+    U_ref = math.fsum(terms)
+    assert abs(U - U_ref) <= 1e-14 * U_ref, (U, U_ref)
+    Uo = O.potential(m, rs)
+    assert abs(Uo - U_ref) <= 1e-14 * U_ref, (Uo, U_ref)
+
+
 def check_eps(e_gpu, e_ora):
     if e_ora > 1e-11:
         assert abs(e_gpu - e_ora) <= 1e-2 * e_ora, (e_gpu, e_ora)
