@@ -358,6 +358,10 @@ struct mstar_adjoint {
   double *mu = nullptr, *nu = nullptr, *phi = nullptr, *aout = nullptr, *pf = nullptr, *pg = nullptr;
   double *lmt = nullptr, *pc = nullptr, *outr = nullptr, *outv = nullptr, *outm = nullptr;
   Weights cw{};
+  // the reverse substeps of step q of a segment, captured once as a graph (see bw_step)
+  std::vector<cudaGraphExec_t> bw_exec;
+  bool bw_off = false;
+  long long bw_launches = 0;
 };
 
 namespace {
@@ -486,6 +490,41 @@ int backward_step(mstar_ctx* c, mstar_adjoint* a, const AdjTraj& t) {
   return MSTAR_OK;
 }
 
+// backward_step for step q of a segment, as one graph launch: its launches depend only on
+// the adjoint's buffers and step q's trajectory record, so the graph captured the first
+// time serves every segment. A failed capture falls back to direct launches.
+int bw_step(mstar_ctx* c, mstar_adjoint* a, int q) {
+  if (a->bw_exec.size() != a->tr.size()) a->bw_exec.assign(a->tr.size(), nullptr);
+  if (!a->bw_exec[q] && !a->bw_off) {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    cudaGraph_t g = nullptr;
+    bool ok = c->cap || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+      c->stream = c->cap;
+      ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const int rc = backward_step(c, a, a->tr[q]);
+        ok = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && rc == MSTAR_OK && g;
+      }
+      c->stream = user;
+    }
+    a->bw_launches = c->launches - l0;
+    c->launches = l0;
+    if (ok) ok = cudaGraphInstantiate(&a->bw_exec[q], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      a->bw_exec[q] = nullptr;
+      a->bw_off = true;
+    }
+  }
+  if (!a->bw_exec[q]) return backward_step(c, a, a->tr[q]);
+  if (cudaGraphLaunch(a->bw_exec[q], c->stream) != cudaSuccess) return MSTAR_ERR_CUDA;
+  c->launches += a->bw_launches;
+  return MSTAR_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -493,6 +532,9 @@ extern "C" {
 void mstar_adjoint_free(mstar_adjoint* a) {
   if (!a) return;
   if (a->c && a->c->stream) cudaStreamSynchronize(a->c->stream);
+  if (a->c) mstar::drop_traj_graphs(a->c);
+  for (cudaGraphExec_t e : a->bw_exec)
+    if (e) cudaGraphExecDestroy(e);
   if (a->mem) cudaFree(a->mem);
   delete a;
 }
@@ -581,7 +623,7 @@ int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g_r, const 
       rc = fixed_step(c, a->H);
       c->traj = nullptr;
     }
-    for (int q = cnt - 1; q >= 0 && !rc; --q) rc = backward_step(c, a, a->tr[q]);
+    for (int q = cnt - 1; q >= 0 && !rc; --q) rc = bw_step(c, a, q);
   }
   // B = U0 - T0 and the centre-of-mass shift of the initial state, then the outputs
   if (!rc) rc = pair_state(c, a, a->ck);

@@ -231,7 +231,10 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
 
 // One attempt with fictitious step H: all divisions level by level, then the
 // extrapolation; reads eps and the extrapolated time back.
-int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
+// The launches of one attempt after the staging of H and t: all divisions level by level
+// (the divisions with n_k >= tau kick and drift at level tau), then the extrapolation.
+// With a trajectory record the states of every level are saved on the way.
+int issue_attempt(mstar_ctx* c) {
   const int K = c->K;
   const size_t st = (size_t)3 * c->npad;
   AdjTraj* tr = c->traj;
@@ -239,7 +242,7 @@ int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
   auto save = [&](double* dst, const double* src, size_t count) {
     return cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToDevice, c->stream);
   };
-  CK(launch_init_drift(c, H));
+  CK(launch_init_drift(c));
   if (tr) {
     CK(save(tr->SC, c->d.sc, nsc));
     CK(save(tr->v0, c->d.v, st));
@@ -251,10 +254,10 @@ int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
       CK(save(tr->R + (tau - 1) * lvl + lo * st, c->d.sr + lo * st, (K - lo) * st));
       CK(save(tr->A + (tau - 1) * lvl + lo * st, c->d.sa + lo * st, (K - lo) * st));
     }
-    CK(launch_kick(c, lo, K, H));
+    CK(launch_kick(c, lo, K));
     CK(launch_rebuild(c, c->d.sV + lo * st, c->d.sv + lo * st, st, K - lo, 1, c->d.Tblk + (size_t)lo * c->nblk,
                       c->d.comblk + (size_t)lo * c->nblk * 3));
-    CK(launch_drift(c, lo, K, H, tau));
+    CK(launch_drift(c, lo, K, tau));
     if (tr) {
       CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
       CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
@@ -264,7 +267,62 @@ int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
       CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
                         c->d.comblk + (size_t)lo2 * c->nblk * 3));
   }
-  CK(launch_extrapolate(c, H));
+  CK(launch_extrapolate(c));
+  return MSTAR_OK;
+}
+
+// Capture issue_attempt once on a private stream and instantiate it. The launches depend
+// only on the context's sizes and buffers and on the trajectory record (H and t are read
+// from device memory), so the graph serves every later attempt with the same record. Any
+// failure turns the graph path off for the context.
+cudaGraphExec_t build_attempt_graph(mstar_ctx* c) {
+  cudaStream_t user = c->stream;
+  const long long l0 = c->launches, f0 = c->force_evals;
+  cudaGraph_t g = nullptr;
+  bool ok = c->cap || cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) {
+    c->stream = c->cap;
+    ok = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      const int rc = issue_attempt(c);
+      ok = cudaStreamEndCapture(c->cap, &g) == cudaSuccess && rc == MSTAR_OK && g;
+    }
+    c->stream = user;
+  }
+  c->att_launches = c->launches - l0;
+  c->att_evals = c->force_evals - f0;
+  c->launches = l0;
+  c->force_evals = f0;
+  cudaGraphExec_t exec = nullptr;
+  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    c->att_graph_off = true;
+    return nullptr;
+  }
+  c->att_graphs.push_back({c->traj, exec});
+  return exec;
+}
+
+// One attempt with fictitious step H; reads eps and the extrapolated time back. Without
+// profiling the attempt is one graph launch.
+int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
+  CK(stage_attempt_scalars(c, H));
+  cudaGraphExec_t exec = nullptr;
+  if (!c->prof && !c->att_graph_off) {
+    for (const auto& ag : c->att_graphs)
+      if (ag.traj == c->traj) exec = ag.exec;
+    if (!exec) exec = build_attempt_graph(c);
+  }
+  if (exec) {
+    CK(cudaGraphLaunch(exec, c->stream));
+    c->launches += c->att_launches;
+    c->force_evals += c->att_evals;
+  } else {
+    const int rc = issue_attempt(c);
+    if (rc) return rc;
+  }
   int rc = sync_read_res(c);
   if (rc) return rc;
   prof_flush(c);
@@ -302,6 +360,16 @@ int extract_out(mstar_ctx* c, double* r_out, double* v_out, const double* Xsrc, 
 // --------------------------------------------------------------------------- internals
 
 namespace mstar {
+
+void drop_traj_graphs(mstar_ctx* c) {
+  std::vector<mstar_ctx::AttGraph> keep;
+  for (const auto& ag : c->att_graphs) {
+    if (ag.traj) cudaGraphExecDestroy(ag.exec);
+    else keep.push_back(ag);
+  }
+  c->att_graphs.swap(keep);
+}
+
 
 int step_prepare(mstar_ctx* c, double* U0, double* T0) { return prepare_step(c, U0, T0); }
 int step_attempt(mstar_ctx* c, double H, double* eps, double* tnew) { return run_attempt(c, H, eps, tnew); }
@@ -404,6 +472,8 @@ void mstar_free(mstar_ctx* c) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
+  for (auto& ag : c->att_graphs) cudaGraphExecDestroy(ag.exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->host_res) cudaFreeHost(c->host_res);
   if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -458,7 +528,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   c->ws_bytes = need;
   double* stage = nullptr;
   carve(s, c->ws, &c->d, &stage);
-  if (cudaMallocHost(&c->host_res, 8 * sizeof(double)) != cudaSuccess ||
+  if (cudaMallocHost(&c->host_res, 16 * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&c->host_buf, (size_t)c->nblk * 8 * sizeof(double) + 64) != cudaSuccess) {
     cudaGetLastError();
     mstar_free(c);
@@ -468,7 +538,8 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
     mstar_free(c);
     return code;
   };
-  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.parent, c->npad, -1);
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.gp, c->npad, -1);
   c->launches += 2;

@@ -83,7 +83,7 @@ struct mstar_ctx {
   size_t ws_bytes = 0;
   bool own_ws = false;
   mstar::Dev d{};
-  double* host_res = nullptr;  // pinned mirror of d.res (8 doubles)
+  double* host_res = nullptr;  // pinned: [0..7] mirror of d.res, [8..9] staging of the attempt's H and t
   double* host_buf = nullptr;  // pinned staging (nblk * 8 doubles)
   // host-side scalar state (the step control of Sec. 2.3-2.4 runs on the host)
   double t = 0.0, B = 0.0, H = 0.0, Mtot = 0.0;
@@ -95,6 +95,16 @@ struct mstar_ctx {
   // profiling of the tiled pair kernel: event pairs recorded around each launch, read
   // back after the next host synchronisation
   bool prof = false;
+  // an attempt's launches (without profiling) captured as a graph on a private stream and
+  // replayed on `stream`: one graph per trajectory record in use (nullptr: none)
+  struct AttGraph {
+    const mstar::AdjTraj* traj;
+    cudaGraphExec_t exec;
+  };
+  cudaStream_t cap = nullptr;
+  std::vector<AttGraph> att_graphs;
+  bool att_graph_off = false;  // capture failed once: launch directly
+  long long att_launches = 0, att_evals = 0;
   std::vector<mstar_prof_rec> prof_pool;
   size_t prof_used = 0;
   long long prof_launches = 0, prof_evals = 0;
@@ -126,12 +136,18 @@ cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d);
 // step.cu
 cudaError_t launch_prepare(mstar_ctx* c);   // X0, V0, slot K copies, T0 partials
 cudaError_t launch_start_derivs(mstar_ctx* c);  // A0 and U0, T0 into d.res
-cudaError_t launch_init_drift(mstar_ctx* c, double H);
-cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi, double H);
-cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, double H, int tau);
+// d.res[4] = H and d.res[5] = t of the attempt (written by stage_attempt_scalars) are read
+// by the drift, kick and extrapolation kernels, so that an attempt can be replayed as a graph
+cudaError_t upload_step_constants(mstar_ctx* c);
+// forget the attempt graphs that record into trajectory buffers (their owner is being freed)
+void drop_traj_graphs(mstar_ctx* c);
+cudaError_t stage_attempt_scalars(mstar_ctx* c, double H);
+cudaError_t launch_init_drift(mstar_ctx* c);
+cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi);
+cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, int tau);
 cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stride, int nsl,
                            int want_T, double* Tblk_base, double* comblk_base);
-cudaError_t launch_extrapolate(mstar_ctx* c, double H);
+cudaError_t launch_extrapolate(mstar_ctx* c);
 cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom
 // w (3 planes of the state) -= centre of mass; optionally T partials into Tblk slot 0
 cudaError_t launch_com_shift(mstar_ctx* c, double* w, double* Tblk);

@@ -85,9 +85,10 @@ k_start_derivs(int n, int npad, int K, const int* __restrict__ parent, const dou
 // First half drift D(h/2n) of every division from the step start (Sec. 2.3):
 // X = X0 + f V0, V = V0, t = t0 + f with f = (delta/2) / (T0 + B), delta = H / n_k.
 __global__ void __launch_bounds__(kBlock)
-k_init_drift(int n, int npad, int K, double H, double B, double t0, const double* __restrict__ X0,
+k_init_drift(int n, int npad, int K, const double* __restrict__ par, double B, const double* __restrict__ X0,
              const double* __restrict__ V0, double* __restrict__ sX, double* __restrict__ sV,
              double* __restrict__ sc) {
+  const double H = par[0], t0 = par[1];  // the attempt's fictitious step and start time
   const int slot = blockIdx.y;
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
   const double T0 = sc[K * kScal + SC_T_KIN];
@@ -110,9 +111,11 @@ k_init_drift(int n, int npad, int K, double H, double B, double t0, const double
 
 // K(delta): V_v += (delta / U) (a_v - a_parent(v)), delta = H / n_k (Sec. 2.2).
 __global__ void __launch_bounds__(kBlock)
-k_kick(int n, int npad, int slot_lo, double H, const int* __restrict__ parent, const double* __restrict__ sa,
-       double* __restrict__ sV, const double* __restrict__ Ublk, int nblk, double* __restrict__ sc) {
+k_kick(int n, int npad, int slot_lo, const double* __restrict__ par, const int* __restrict__ parent,
+       const double* __restrict__ sa, double* __restrict__ sV, const double* __restrict__ Ublk, int nblk,
+       double* __restrict__ sc) {
   __shared__ double sU;
+  const double H = par[0];
   const int slot = slot_lo + blockIdx.y;
   sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &sU);
   const double U = sU;
@@ -134,9 +137,10 @@ k_kick(int n, int npad, int slot_lo, double H, const int* __restrict__ parent, c
 
 // D(h): X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift.
 __global__ void __launch_bounds__(kBlock)
-k_drift(int npad, int slot_lo, double H, double B, int tau, double* __restrict__ sX,
+k_drift(int npad, int slot_lo, const double* __restrict__ par, double B, int tau, double* __restrict__ sX,
         const double* __restrict__ sV, const double* __restrict__ Tblk, int nblk, double* __restrict__ sc) {
   __shared__ double sT;
+  const double H = par[0];
   const int slot = slot_lo + blockIdx.y;
   sum_partials(Tblk + (size_t)slot * nblk, nblk, 1, &sT);
   const double T = 0.5 * sT;
@@ -241,11 +245,12 @@ __device__ __forceinline__ double norm3(double x, double y, double z) {
 // eps = max_q |T_KK - T_{K-1,K-1}|_q / |S_q(s0) + delta_K S'_q(s0)| over X_v, V_v, t with
 // S' = V / (T0 + B) for X, A0 / U0 for V, 1 / (T0 + B) for t, delta_K = H / n_K.
 __global__ void __launch_bounds__(kBlock)
-k_extrapolate(int n, int npad, int K, double H, double B, double t0, const int* __restrict__ parent,
+k_extrapolate(int n, int npad, int K, const double* __restrict__ par, double B, const int* __restrict__ parent,
               const double* __restrict__ sX, const double* __restrict__ sV, const double* __restrict__ X0,
               const double* __restrict__ V0, const double* __restrict__ A0, const double* __restrict__ sc,
               double* __restrict__ Tkk, double* __restrict__ epsblk) {
   __shared__ double scratch[32];
+  const double H = par[0], t0 = par[1];
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const double T0 = sc[K * kScal + SC_T_KIN], U0 = sc[K * kScal + SC_U];
   const double rate = 1.0 / (T0 + B);
@@ -344,37 +349,49 @@ cudaError_t launch_start_derivs(mstar_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_drift(mstar_ctx* c, double H) {
+// The Neville factors 1 / ((n_k / n_{k-j})^2 - 1) for every k < kMaxKfix (they do not
+// depend on k_fix), once per context.
+cudaError_t upload_step_constants(mstar_ctx* c) {
   double fac[kMaxKfix][kMaxKfix] = {};
-  for (int k = 0; k < c->K; ++k)
+  for (int k = 0; k < kMaxKfix; ++k)
     for (int j = 1; j <= k; ++j) {
       const double ratio = (double)(2 * (k + 1)) / (double)(2 * (k - j + 1));
       fac[k][j] = 1.0 / (ratio * ratio - 1.0);
     }
-  cudaError_t e = cudaMemcpyToSymbolAsync(c_fac, fac, sizeof(fac), 0, cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbolAsync(c_fac, fac, sizeof(fac), 0, cudaMemcpyHostToDevice, c->stream);
+}
+
+// The attempt's H and start time t into d.res[4], d.res[5] (from pinned host_res[8], [9]);
+// the host has synchronised with the previous attempt, so the staging slots are free.
+cudaError_t stage_attempt_scalars(mstar_ctx* c, double H) {
+  c->host_res[8] = H;
+  c->host_res[9] = c->t;
+  return cudaMemcpyAsync(c->d.res + 4, c->host_res + 8, 2 * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+}
+
+cudaError_t launch_init_drift(mstar_ctx* c) {
   dim3 grid(c->nblk, c->K);
-  k_init_drift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, H, c->B, c->t, c->d.X0, c->d.V0, c->d.sX,
+  k_init_drift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B, c->d.X0, c->d.V0, c->d.sX,
                                               c->d.sV, c->d.sc);
   MSTAR_LAUNCHED(c);
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t st = (size_t)3 * c->npad;
   return launch_rebuild(c, c->d.sX, c->d.sr, st, c->K, 0, nullptr, c->d.comblk);
 }
 
-cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi, double H) {
+cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi) {
   dim3 grid(c->nblk, slot_hi - slot_lo);
-  k_kick<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, slot_lo, H, c->d.parent, c->d.sa, c->d.sV, c->d.Ublk,
-                                        c->nblk, c->d.sc);
+  k_kick<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, slot_lo, c->d.res + 4, c->d.parent, c->d.sa, c->d.sV,
+                                        c->d.Ublk, c->nblk, c->d.sc);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
 }
 
-cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, double H, int tau) {
+cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, int tau) {
   dim3 grid(c->nblk, slot_hi - slot_lo);
-  k_drift<<<grid, kBlock, 0, c->stream>>>(c->npad, slot_lo, H, c->B, tau, c->d.sX, c->d.sV, c->d.Tblk, c->nblk,
-                                         c->d.sc);
+  k_drift<<<grid, kBlock, 0, c->stream>>>(c->npad, slot_lo, c->d.res + 4, c->B, tau, c->d.sX, c->d.sV, c->d.Tblk,
+                                         c->nblk, c->d.sc);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
 }
@@ -394,8 +411,8 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   return cudaGetLastError();
 }
 
-cudaError_t launch_extrapolate(mstar_ctx* c, double H) {
-  k_extrapolate<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, H, c->B, c->t, c->d.parent, c->d.sX,
+cudaError_t launch_extrapolate(mstar_ctx* c) {
+  k_extrapolate<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B, c->d.parent, c->d.sX,
                                                   c->d.sV, c->d.X0, c->d.V0, c->d.A0, c->d.sc, c->d.Tkk,
                                                   c->d.epsblk);
   MSTAR_LAUNCHED(c);
