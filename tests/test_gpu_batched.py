@@ -99,6 +99,24 @@ def test_split_attempt_is_bit_identical_to_one_cta(G):
         assert np.array_equal(out[0]["r"][s], out[1]["r"][s]) and np.array_equal(out[0]["v"][s], out[1]["v"][s]), s
 
 
+@pytest.mark.parametrize("n_d", [0, 1])
+def test_one_launch_other_near_rules(n_d):
+    """The batched kernels with N_d = 0 and 1 (Sec. 3.4) against the oracle's attempt with the
+    same rule, every system (segment kernels and CTAs)."""
+    systems = mixed_systems()
+    H = step_sizes(systems)
+    b = M.Batch(systems, eta_gbs=1.0, n_d=n_d)
+    b.set_H(H)
+    st = b.step(1e9, launches=1)
+    assert st["accepted"] == len(systems) and st["failed"] == 0
+    S = b.state()
+    for s, (m, r, v) in enumerate(systems):
+        a = O.System(m, r, v, n_d=n_d).attempt(H[s])
+        assert relerr(S["r"][s], a["r"]) < 1e-12, s
+        assert relerr(S["v"][s], a["v"]) < 1e-12, s
+    b.close()
+
+
 def test_batch_integrates_to_end_time_like_the_oracle():
     systems = mixed_systems()
     t_end = 0.05

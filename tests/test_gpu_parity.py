@@ -132,6 +132,25 @@ def test_forces_every_tile_width(n):
     g.close()
 
 
+@pytest.mark.parametrize("n_d", [0, 1, 2])
+@pytest.mark.parametrize("n", [600, 5000])
+def test_forces_every_near_rule(n_d, n):
+    """Sec. 3.4: pairs within N_d tree edges take their separation from edge vectors (N_d = 0:
+    none; 1: parent and children; 2: also grandparents, grandchildren and siblings). Forces
+    and U for each rule against the oracle's, with 32- and 64-body tiles (n = 600, 5000), on
+    a cluster with a central SMBH binary, where the near pairs matter."""
+    m, r, v = W.plummer_smbh_binary(n - 2, 3)
+    g = M.Integrator(m, r, v, n_d=n_d)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=n_d)
+    assert relerr(a, ao) < 1e-13, relerr(a, ao)
+    assert abs(U - Uo) <= 1e-13 * Uo
+    g.close()
+
+
 def test_forces_sampled_full_size():
     """N = 10002: sampled accelerations against the oracle's per-body sums."""
     m, r, v = W.workload("plummer10k_two_smbh")
