@@ -49,9 +49,14 @@ NOMINAL_FP64_TFLOPS = 1.25
 DFMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one tiled-pair force evaluation at N = 10002, from the ncu
-# capture summarised in profiles/pair_tiles_plummer10k.md; None once the kernel changes.
-PAIR_TILE_DRAM_BYTES_PER_EVAL = 440320 + 0
+# DRAM bytes (read + write) of one k_pair_tiles launch at N = 10002 by the number of
+# division slots it evaluates, from the ncu capture summarised in
+# profiles/pair_tiles_plummer10k.md (the partials of more than ~2 slots overflow L2 and
+# round-trip through HBM); None once the kernel changes. An attempt launches the kernel for
+# 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots.
+PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 446e3, 2: 714e3, 3: 14.31e6, 4: 39.64e6, 5: 65.77e6, 6: 92.18e6,
+                                 7: 117.17e6, 8: 143.36e6}
+ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 
 
 def parse():
@@ -548,11 +553,14 @@ def run_mstar(args):
     # ceiling of this kernel: the FP64 pipe (2 instructions/clk/SM) saturated with its 9
     # FP64 instructions per pair, times the 33 algorithmic flops each pair carries
     peak = DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / FP64_INSTR_PER_PAIR * FLOPS_PER_UNORDERED_PAIR / 1e12
-    evals_per_launch = prof.force_evals / max(prof.pair_launches, 1)
-    traffic = (PAIR_TILE_DRAM_BYTES_PER_EVAL * evals_per_launch
-               if PAIR_TILE_DRAM_BYTES_PER_EVAL is not None else None)
+    # per launch, averaged over an attempt's launches (the pattern of slot counts is fixed)
+    traffic = (sum(PAIR_TILE_DRAM_BYTES_BY_SLOTS[k] for k in ATTEMPT_SLOT_PATTERN) / len(ATTEMPT_SLOT_PATTERN)
+               if PAIR_TILE_DRAM_BYTES_BY_SLOTS is not None else None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch by slot count, "
+                                   "averaged over an attempt's 17 launches; the partials of more than ~2 slots "
+                                   "overflow L2"),
                 "kernel": "k_pair_tiles (symmetric pair loop: FP64 separations and force accumulations; "
                           "integer-pipe r^2, 1/r, m/r^3 and the exact fixed-point sum of m/r)",
                 "peak_source": ("derived: FP64 pipe 2 instr/clk/SM x 152 SMs x sampled SM clock / 9 FP64 "
