@@ -345,6 +345,35 @@ def test_lidov_kozai_first_cycles_match_oracle():
         assert abs(ecc(Sr, Sv) - ecc(So["r"], So["v"])) < 1e-6, (ecc(Sr, Sv), ecc(So["r"], So["v"]))
 
 
+def test_graph_replay_matches_direct_launches_and_contexts_do_not_interfere():
+    """An attempt is replayed as a captured CUDA graph; with profiling on it is launched kernel
+    by kernel. Both must give bit-identical results. Two contexts with different k_fix
+    (6 and 8), used in alternation, must each still match the oracle: they share the module's
+    constant Neville factors, which do not depend on k_fix."""
+    m, r, v = W.workload("plummer64")
+    H = 0.05
+    res = []
+    for prof in (False, True):
+        g = M.Integrator(m, r, v)
+        M.mstar_profile_enable(g.ctx, prof)
+        a1 = g.attempt(H)
+        a2 = g.attempt(0.5 * H)
+        res.append((a1, a2))
+        g.close()
+    for x, y in zip(res[0], res[1]):
+        assert np.array_equal(x["r"], y["r"]) and np.array_equal(x["v"], y["v"]) and x["t"] == y["t"]
+        assert x["eps"] == y["eps"]
+    g6 = M.Integrator(m, r, v, k_fix=6)
+    g8 = M.Integrator(m, r, v, k_fix=8)
+    for _ in range(2):
+        for g, k in ((g6, 6), (g8, 8)):
+            a = g.attempt(H)
+            o = O.System(m, r, v, k_fix=k).attempt(H)
+            assert relerr(a["r"], o["r"]) < 1e-12 and relerr(a["v"], o["v"]) < 1e-12, k
+    g6.close()
+    g8.close()
+
+
 def test_kepler_gbs_matches_analytic():
     m, r, v = W.kepler_binary(seed=4, e=0.9)
     g = M.Integrator(m, r, v)
