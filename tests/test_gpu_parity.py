@@ -165,6 +165,24 @@ def test_forces_sampled_full_size():
     g.close()
 
 
+@pytest.mark.parametrize("n", [M.MSTAR_MAX_N - 1, M.MSTAR_MAX_N])
+def test_forces_at_the_size_limit(n):
+    """The largest systems a context accepts (MSTAR_MAX_N, and one less for a ragged last
+    tile): the exact tree, the forces and U against the oracle's."""
+    m, r, v = W.plummer(n, 12)
+    g = M.Integrator(m, r, v)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    groot, gpar, glev, _ = g.mst(with_order=False)
+    assert groot == root and np.array_equal(gpar, par) and np.array_equal(glev, lev)
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=2)
+    assert relerr(a, ao) < 1e-12
+    assert abs(U - Uo) <= 1e-13 * Uo
+    g.close()
+
+
 @pytest.mark.parametrize("n_d", [0, 2])
 def test_rsqrt_across_exponent_range(n_d):
     """Two bodies at separations from 1e-100 to 1e12: the reciprocal square root (FP32 seed
