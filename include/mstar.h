@@ -230,9 +230,10 @@ MSTAR_API int mstar_batch_set_H(mstar_batch* b, const double* H);
                  system), the divisions (one CTA of G warps per system and group, so that
                  a system's groups run on up to four SMs) and the finish (extrapolation,
                  error, step control; one CTA per system);
-     0           for the classes of at most 16 bodies: four division groups of 8 (class 0)
-                 or 16 (class 1) lanes per system, one body per lane, the group's state in
-                 registers and the pair rotation and tree sums done by warp shuffles.
+     0           for the classes of at most 16 bodies: four division groups of 8 (class 0;
+                 4 for systems of at most 4 bodies, two systems per warp) or 16 (class 1)
+                 lanes per system, one body per lane, the group's state in registers and the
+                 pair rotation and tree sums done by warp shuffles.
    A new schedule rebuilds the graph (INVALID_ARG for any other value). The default is 0, 0,
    1, 1, 1, 2, 4. The schedule changes only the work split, not the arithmetic of a system
    beyond the order in which partial sums are added (a split schedule gives the same results

@@ -917,6 +917,8 @@ template <int WD>
 __device__ __forceinline__ void sys_sync(int slot) {
   if constexpr (4 * WD == 32) {
     __syncwarp();
+  } else if constexpr (4 * WD < 32) {  // two or more systems per warp: the system's lanes
+    __syncwarp(((1u << (4 * WD)) - 1u) << ((threadIdx.x & 31) & ~(4 * WD - 1)));
   } else {
     asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(4 * WD) : "memory");
   }
@@ -1020,7 +1022,7 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
   __shared__ double s_T[PER][6][WD];
   __shared__ double s_t[PER][kMaxKfix];
   __shared__ double s_scal[PER][4];
-  __shared__ double s_err[PER][4 * WD / 32];
+  __shared__ double s_err[PER][4 * WD >= 32 ? 4 * WD / 32 : 1];
   __shared__ int s_dep[PER];
   const int slot = threadIdx.x / (4 * WD), lt = threadIdx.x % (4 * WD);
   Seg<WD> sg;
@@ -1226,8 +1228,14 @@ k_batched_seg(int count, const int* __restrict__ order, const int* __restrict__ 
     e = fabs(__dsub_rn(tkk_t, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300);
     s_scal[slot][2] = tkk_t;
   }
-  for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
-  if ((threadIdx.x & 31) == 0) s_err[slot][lt / 32] = e;
+  if constexpr (4 * WD >= 32) {
+    for (int o = 16; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0) s_err[slot][lt / 32] = e;
+  } else {  // the system's 4 WD lanes of a shared warp
+    const unsigned smask = ((1u << (4 * WD)) - 1u) << ((threadIdx.x & 31) & ~(4 * WD - 1));
+    for (int o = 2 * WD; o > 0; o >>= 1) e = nanmax(e, __shfl_xor_sync(smask, e, o));
+    if (lt == 0) s_err[slot][0] = e;
+  }
   sys_sync<WD>(slot);
   if (lt == 0) {
     double eps = s_err[slot][0];
@@ -1331,7 +1339,7 @@ struct mstar_batch {
   int sched[kNumClasses] = {};
   // node kinds: one CTA per system with G = 1, 2, 4; the 8- and 16-lane segment kernels; the
   // split attempt (start, divisions, finish) with G = 1, 2, 4
-  int seg_begin[8] = {}, seg_count[8] = {};
+  int seg_begin[9] = {}, seg_count[9] = {};
   cudaGraphExec_t exec = nullptr;
   int graph_nodes = 0;
   double tend_h = NAN;
@@ -1407,10 +1415,11 @@ __global__ void k_scatter_vec(int nbody, const int* __restrict__ off, int nsys, 
 
 // Schedule values: 1, 2, 4 warps per division group (one CTA per system); -1, -2, -4 for the
 // same groups with the attempt split into three nodes (one CTA per division group); 0 for
-// the size classes of at most 16 bodies: groups of 8 (class 0) or 16 (class 1) lanes, one
-// body per lane. Node kind: 0, 1, 2 for G = 1, 2, 4; 3 and 4 for the 8- and 16-lane
-// kernels; 5, 6, 7 for the split attempt with G = 1, 2, 4.
-constexpr int kNodeKinds = 8;
+// the size classes of at most 16 bodies: groups of 8 (class 0; 4 for systems of at most 4
+// bodies) or 16 (class 1) lanes, one body per lane. Node kind: 0, 1, 2 for G = 1, 2, 4; 3
+// and 4 for the 8- and 16-lane kernels; 5, 6, 7 for the split attempt with G = 1, 2, 4; 8
+// for the 4-lane kernel.
+constexpr int kNodeKinds = 9;
 int sched_index(int cls, int G) {
   if (G == 0) return cls == 0 ? 3 : (cls == 1 ? 4 : -1);
   if (G < 0) return G == -1 ? 5 : (G == -2 ? 6 : (G == -4 ? 7 : -1));
@@ -1441,7 +1450,8 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   auto n_of = [&](int s) { return b->off_h[s + 1] - b->off_h[s]; };
   auto g_of = [&](int s) {
     const int c = mstar::size_class(n_of(s));
-    return sched_index(c, sched[c]);
+    const int k = sched_index(c, sched[c]);
+    return (k == 3 && n_of(s) <= 4) ? 8 : k;  // the 4-lane kernel for systems of at most 4 bodies
   };
   std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
     const int gx = g_of(x), gy = g_of(y);
@@ -1461,7 +1471,7 @@ int apply_schedule(mstar_batch* b, const int* sched) {
   cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
   bool ok = true;
   int nodes = 0;
-  static const int node_order[kNodeKinds] = {7, 2, 6, 1, 5, 0, 4, 3};  // widest groups first
+  static const int node_order[kNodeKinds] = {7, 2, 6, 1, 5, 0, 4, 3, 8};  // widest groups first
   auto add_node = [&](void* func, dim3 grid, dim3 block, void** args, const cudaGraphNode_t* dep, int prio,
                       cudaGraphNode_t* node) {
     cudaKernelNodeParams kp{};
@@ -1487,10 +1497,12 @@ int apply_schedule(mstar_batch* b, const int* sched) {
     const int G = qi >= 5 ? 1 << (qi - 5) : 1 << qi;  // warps per division group (not used for 3, 4)
     const int prio = G == 4 ? hi_prio : (G == 2 ? (hi_prio + lo_prio) / 2 : lo_prio);
     cudaGraphNode_t n0, n1, n2;
-    if (qi == 3 || qi == 4) {
-      const int per = mstar::kSegThreads / (4 * (qi == 3 ? 8 : 16));
-      ok = add_node(qi == 3 ? (void*)mstar::k_batched_seg<8> : (void*)mstar::k_batched_seg<16>,
-                    dim3((cnt + per - 1) / per), dim3(mstar::kSegThreads), args, nullptr, lo_prio, &n0);
+    if (qi == 3 || qi == 4 || qi == 8) {
+      const int wd = qi == 8 ? 4 : (qi == 3 ? 8 : 16);
+      const int per = mstar::kSegThreads / (4 * wd);
+      void* f = qi == 8 ? (void*)mstar::k_batched_seg<4>
+                        : (qi == 3 ? (void*)mstar::k_batched_seg<8> : (void*)mstar::k_batched_seg<16>);
+      ok = add_node(f, dim3((cnt + per - 1) / per), dim3(mstar::kSegThreads), args, nullptr, lo_prio, &n0);
     } else if (qi < 3) {
       void* f = G == 1 ? (void*)mstar::k_batched_step<1> : (G == 2 ? (void*)mstar::k_batched_step<2>
                                                                    : (void*)mstar::k_batched_step<4>);
