@@ -280,7 +280,7 @@ def run_batched(args, dev, M, W, torch, world=1, rank=0):
            "schedule": {"warps_per_division_group_by_size_class": sched.tolist(),
                         "size_classes": "[2,8] [9,16] [17,32] [33,64] [65,128] [129,256] [257,512]",
                         "values": "G > 0: one CTA per system, four division groups of G warps; -G: the same "
-                                  "groups as one CTA each (start, divisions, finish nodes); 0: 8- or 16-lane "
+                                  "groups as one CTA each (start, divisions, finish nodes); 0: 4-, 8- or 16-lane "
                                   "groups, one body per lane",
                         "autotune_launch_ms": tune_ms},
            "launch": "one CUDA graph launch per attempt (independent kernel nodes per schedule kind; a chain "
