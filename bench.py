@@ -158,6 +158,23 @@ def barrier(world):
     R.barrier(world)
 
 
+def host_cpu():
+    """The host CPU as /proc/cpuinfo names it (model name, or the Arm implementer/part codes)."""
+    import platform
+
+    desc = {"machine": platform.machine(), "nproc": os.cpu_count()}
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return desc
+    for key in ("model name", "CPU implementer", "CPU part"):
+        for line in info:
+            if line.split(":")[0].strip() == key:
+                desc[key.replace(" ", "_").lower()] = line.split(":", 1)[1].strip()
+                break
+    return desc
+
+
 def cpu_baseline_sample(n_threads):
     """The oracle, as it stands, on the host cores: one GBS step attempt of the workload."""
     import oracle
@@ -186,7 +203,8 @@ def cpu_baseline_sample(n_threads):
             "sample": f"one GBS step attempt (73 pair-loop evaluations, Prim, rebuilds, extrapolation) of "
                       f"the N={n} workload at H={H}, {dt:.2f} s wall on {n_threads} threads",
             "single_core": {"value": n * (n - 1) / dt1, "unit": "pair-forces/s", "cores": 1,
-                            "sample": f"one oracle pair-loop evaluation of the N={n} state, {dt1:.2f} s"}}
+                            "sample": f"one oracle pair-loop evaluation of the N={n} state, {dt1:.2f} s"},
+            "host": host_cpu()}
 
 
 def run_reference(args):
@@ -224,7 +242,7 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD_DESC, "n": n},
            "cpu_baseline": {"value": value, "unit": "pair-forces/s", "cores": threads, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample, "host": host_cpu()},
            "e2e": {"value": value, "unit": "pair-forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
