@@ -301,6 +301,35 @@ def test_logh_leapfrog_kepler_orbit_exact():
     assert t > 10.0  # the orbit has gone round several times
 
 
+@pytest.mark.parametrize("case", ["plummer64", "kepler", "plummer257"])
+def test_gbs_step_reverses_within_its_error(case):
+    """Sec. 2.1 / 2.3: the LogH leapfrog is time-symmetric, and extrapolating it in even powers
+    of the substep keeps the symmetry up to the extrapolated step's own truncation error (a
+    linear combination of symmetric maps is not exactly symmetric). So a step of H followed
+    by one of -H from its result returns to the start within that error: the round trip
+    misses by less than the step's error estimate eps, and by far less than the step moved.
+    A first-order (non-symmetric) drift/kick split misses by O(H)."""
+    if case == "plummer64":
+        (m, r, v), H = W.workload("plummer64"), 0.05
+    elif case == "kepler":
+        (m, r, v), H = W.kepler_binary(seed=2, e=0.7), 0.3
+    else:
+        (m, r, v), H = W.plummer(257, 8), 0.015
+    s = O.System(m, r, v)
+    st0 = s.state()
+    a = s.attempt(H)
+    back = O.System(m, r, v)
+    back.set_state(a["t"], a["r"], a["v"])
+    b = back.attempt(-H)
+    rel = lambda x, y: float(np.abs(x - y).max() / np.abs(y).max())  # noqa: E731
+    moved = rel(a["r"], st0["r"])
+    assert moved > 1e-4
+    miss_r, miss_v = rel(b["r"], st0["r"]), rel(b["v"], st0["v"])
+    assert miss_r < max(a["eps"], 1e-13) and miss_v < max(a["eps"], 1e-13), (miss_r, miss_v, a["eps"])
+    assert miss_r < 1e-6 * moved
+    assert abs(b["t"] - st0["t"]) <= max(a["eps"], 1e-13) * abs(a["t"])
+
+
 def test_gbs_kepler_matches_analytic_solution():
     """A full run with GBS (eta = 1e-12) lands on the Kepler solution at the end time."""
     m, r, v = W.kepler_binary(seed=4, e=0.9)
