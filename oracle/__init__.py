@@ -128,7 +128,10 @@ def _f64(x, shape=None):
 def default_params(**kw) -> Params:
     p = Params()
     lib().orc_params_default(C.byref(p))
+    names = {f[0] for f in Params._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"unknown oracle parameter {k!r}")
         setattr(p, k, v)
     return p
 

@@ -417,6 +417,25 @@ def test_gbs_step_reverses_like_the_oracle(name, H):
         assert miss < max(a["eps"], 1e-13), (key, miss, a["eps"])
 
 
+@pytest.mark.parametrize("k_fix,a_gbs,eta", [(8, 0.9, 1e-10), (6, 0.9, 1e-10)])
+def test_step_control_settles_like_the_oracle(k_fix, a_gbs, eta):
+    """Eq. hnext on the GPU: single accepted steps on a circular Kepler orbit settle at
+    eps = a_GBS^(2 k_fix - 1) eta, and each step's eps and H equal the oracle's to 1e-6 and 1e-12."""
+    m, r, v = W.kepler_binary(seed=2, e=0.0)
+    g = M.Integrator(m, r, v, eta_gbs=eta, k_fix=k_fix, a_gbs=a_gbs)
+    o = O.System(m, r, v, eta=eta, k_fix=k_fix, a_gbs=a_gbs)
+    ratios = []
+    for i in range(8):
+        _, st = g.step(1e3, max_steps=1)
+        rc, so = o.integrate(1e3, max_steps=1)
+        assert rc == 0 and st["rejected"] == so["rejected"] and (i == 0 or st["rejected"] == 0)
+        assert abs(st["eps_last"] / so["eps_last"] - 1) < 1e-6, (st, so)
+        assert abs(st["H"] / so["H"] - 1) < 1e-12 and abs(st["t"] / so["t"] - 1) < 1e-12, (st, so)
+        ratios.append(st["eps_last"] / eta)
+    g.close()
+    assert np.all(np.abs(np.array(ratios[3:]) / a_gbs ** (2 * k_fix - 1) - 1) < 1e-2), ratios
+
+
 def test_kepler_gbs_matches_analytic():
     m, r, v = W.kepler_binary(seed=4, e=0.9)
     g = M.Integrator(m, r, v)
