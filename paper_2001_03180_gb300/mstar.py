@@ -152,7 +152,10 @@ def mstar_strerror(code: int) -> str:
 def mstar_default_params(**overrides) -> mstar_params:
     p = mstar_params()
     load().mstar_default_params(C.byref(p))
+    names = {f[0] for f in mstar_params._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"unknown mstar_params field {k!r}")
         setattr(p, k, v)
     return p
 

@@ -40,6 +40,8 @@ def test_host_only_entry_points_without_gpu():
     assert M.mstar_workspace_bytes(100, bad) == 0
     bad = M.mstar_default_params(n_d=3)
     assert M.mstar_workspace_bytes(100, bad) == 0
+    with pytest.raises(TypeError):
+        M.mstar_default_params(eta=1e-10)       # the field is eta_gbs; a typo must not be ignored
 
 
 def test_no_cpu_fallback_in_product_path():
