@@ -420,20 +420,35 @@ def test_gbs_step_reverses_like_the_oracle(name, H):
 @pytest.mark.parametrize("k_fix,a_gbs,eta", [(8, 0.9, 1e-10), (6, 0.9, 1e-10)])
 def test_step_control_settles_like_the_oracle(k_fix, a_gbs, eta):
     """Eq. hnext on the GPU: single accepted steps on a circular Kepler orbit settle at
-    eps = a_GBS^(2 k_fix - 1) eta, and each step's eps and H equal the oracle's to 1e-6 and 1e-12."""
+    eps = a_GBS^(2 k_fix - 1) eta, as on the oracle.
+
+    The first step is rejected down from the q U dt guess (Sec. 2.4) to an H where eps is
+    at the rounding level of the extrapolants (~1e-14 for k_fix = 8). There the two sides
+    take the same H and halvings, but their eps differ by rounding (observed 1.4e-14 of
+    4.1e-14), and so the second step's H by (4.1 / 2.7)^(1/15) - 1 = 2.8 %. The controller is
+    deadbeat (eps = C H^(2k-1) gives H_next = a (eta/C)^(1/(2k-1)) whatever H was), so from the
+    third step on both take the same H (to the eps noise / 15) and settle at the same eps."""
     m, r, v = W.kepler_binary(seed=2, e=0.0)
     g = M.Integrator(m, r, v, eta_gbs=eta, k_fix=k_fix, a_gbs=a_gbs)
     o = O.System(m, r, v, eta=eta, k_fix=k_fix, a_gbs=a_gbs)
-    ratios = []
+    ratios, ratios_o = [], []
     for i in range(8):
         _, st = g.step(1e3, max_steps=1)
         rc, so = o.integrate(1e3, max_steps=1)
-        assert rc == 0 and st["rejected"] == so["rejected"] and (i == 0 or st["rejected"] == 0)
-        assert abs(st["eps_last"] / so["eps_last"] - 1) < 1e-6, (st, so)
-        assert abs(st["H"] / so["H"] - 1) < 1e-12 and abs(st["t"] / so["t"] - 1) < 1e-12, (st, so)
+        assert rc == 0 and st["accepted"] == 1
+        # H in the stats is the step proposed for the next call
+        if i == 0:
+            assert st["rejected"] == so["rejected"], (st, so)
+            assert abs(st["eps_last"] - so["eps_last"]) < 1e-13, (st, so)
+        else:
+            assert st["rejected"] == 0 and so["rejected"] == 0
+        assert abs(st["H"] / so["H"] - 1) < (0.05 if i == 0 else 1e-3), (i, st, so)
         ratios.append(st["eps_last"] / eta)
+        ratios_o.append(so["eps_last"] / eta)
     g.close()
-    assert np.all(np.abs(np.array(ratios[3:]) / a_gbs ** (2 * k_fix - 1) - 1) < 1e-2), ratios
+    target = a_gbs ** (2 * k_fix - 1)
+    for rr in (ratios, ratios_o):
+        assert np.all(np.abs(np.array(rr[3:]) / target - 1) < 1e-2), (rr, target)
 
 
 def test_kepler_gbs_matches_analytic():
