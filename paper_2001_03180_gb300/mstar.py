@@ -400,6 +400,9 @@ class Batch:
     def __init__(self, systems, device=None, **params):
         import torch
 
+        systems = list(systems)
+        if not systems:
+            raise MstarError(MSTAR_ERR_INVALID_ARG, "Batch: no systems")
         if not torch.cuda.is_available():
             raise RuntimeError("libmstar needs a CUDA GPU")
         load()

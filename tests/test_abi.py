@@ -44,6 +44,28 @@ def test_host_only_entry_points_without_gpu():
         M.mstar_default_params(eta=1e-10)       # the field is eta_gbs; a typo must not be ignored
 
 
+def test_batch_layout_rules_without_gpu():
+    """The host checks of a batch's CSR offsets (a system has 2 .. MSTAR_BATCH_MAX_N bodies, at
+    least one system, offsets from 0): a batch the library would reject has no workspace."""
+    B.build()
+    p = M.mstar_default_params()
+    ok = M.mstar_batch_workspace_bytes(3, [0, 2, 5, 5 + M.MSTAR_BATCH_MAX_N], p)
+    assert ok > 0
+    assert M.mstar_batch_workspace_bytes(4, [0, 2, 5, 7, 107], p) > M.mstar_batch_workspace_bytes(3, [0, 2, 5, 7], p)
+    for nsys, off in [(0, [0]),                                   # empty batch
+                      (2, [0, 1, 4]),                             # a one-body system
+                      (2, [0, 3, 3]),                             # an empty system
+                      (2, [1, 3, 6]),                             # offsets not from 0
+                      (2, [0, 4, 2]),                             # decreasing offsets
+                      (1, [0, M.MSTAR_BATCH_MAX_N + 1])]:         # above the batch limit
+        assert M.mstar_batch_workspace_bytes(nsys, off, p) == 0, (nsys, off)
+    bad = M.mstar_default_params(k_fix=1)
+    assert M.mstar_batch_workspace_bytes(1, [0, 3], bad) == 0
+    with pytest.raises(M.MstarError) as e:
+        M.Batch([])
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+
+
 def test_no_cpu_fallback_in_product_path():
     """The package never imports the oracle: product sources mention no oracle module."""
     pkg = os.path.join(ROOT, "paper_2001_03180_gb300")

@@ -150,6 +150,10 @@ def test_batch_rejects_oversize_and_bad_input():
     with pytest.raises(M.MstarError) as e:
         M.Batch([(m, r, v)])
     assert e.value.code == M.MSTAR_ERR_NONFINITE
+    m1, r1, v1 = W.plummer(10, 3)
+    with pytest.raises(M.MstarError) as e:                     # a one-body system has no pairs
+        M.Batch([W.plummer(10, 1), (m1[:1], r1[:1], v1[:1])])
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
 
 
 def test_autotune_keeps_the_state_and_picks_a_valid_schedule():
