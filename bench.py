@@ -462,7 +462,42 @@ def run_small_configs(args, dev, M, W, torch):
                     "t_reached": st["t"], "gbs_steps_per_s": st["accepted"] / wall,
                     "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0)}
         g.close()
+    out["plummer64_to_t1_batch_of_one"] = run_batch_of_one(dev, M, W, torch)
     return out
+
+
+def run_batch_of_one(dev, M, W, torch):
+    """Plummer 64 to t = 1 as a batch of one system: each attempt is one graph launch of the
+    batched kernels (the system in one CTA, or over four with a split schedule) in place of the
+    ~130 launches of a single-system attempt. The schedule comes from the autotuner, run
+    beforehand on a snapshot and not timed. The energy error is taken by mstar_energy on a
+    context made from the end state."""
+    m, r, v = W.workload("plummer64")
+    g = M.Integrator(m, r, v, device=dev)
+    e0 = g.energy()["E"]
+    g.close()
+    b = M.Batch([(m, r, v)], device=dev)
+    sched, tune_ms = b.autotune(1.0)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    launches = 0
+    for _ in range(4096):
+        st = b.step(1.0, launches=8)
+        launches += 8
+        if st["finished"] == 1:
+            break
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    S = b.state()
+    b.close()
+    g = M.Integrator(m, S["r"][0], S["v"][0], device=dev)
+    e1 = g.energy()["E"]
+    g.close()
+    n = len(m)
+    return {"n": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
+            "status": int(S["status"][0]), "t_reached": float(S["t"][0]), "graph_launches": launches,
+            "schedule": [int(x) for x in sched], "gbs_steps_per_s": st["accepted"] / wall,
+            "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0)}
 
 
 def run_mstar(args):
