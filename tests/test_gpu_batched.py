@@ -79,6 +79,36 @@ def test_one_launch_matches_oracle_attempt(name):
     b.close()
 
 
+def test_full_size_batch_sampled_against_oracle():
+    """The benchmark's 4096-system workload (2..199 bodies, every size class up to 256) in the
+    benchmark's launch configuration: the autotuned schedule, every node in one graph launch.
+    With eta = 1 every attempt is accepted. In each size class the largest system and eight
+    spread over the class match the oracle's attempt at the same H."""
+    systems = W.batched_systems(4096, 3)
+    trip = [(s.m, s.r, s.v) for s in systems]
+    H = step_sizes(trip)
+    b = M.Batch(trip, eta_gbs=1.0)
+    sched, _ = b.autotune(1e9, repeats=1)
+    assert list(b.schedule()) == list(sched)
+    b.set_H(H)
+    st = b.step(1e9, launches=1)
+    assert st["accepted"] == len(systems) and st["failed"] == 0
+    S = b.state()
+    b.close()
+    sizes = np.array([len(s.m) for s in systems])
+    pick = set()
+    for lo, hi in [(2, 8), (9, 16), (17, 32), (33, 64), (65, 128), (129, 256)]:
+        idx = np.flatnonzero((sizes >= lo) & (sizes <= hi))
+        assert len(idx) > 0, (lo, hi)
+        pick.add(int(idx[np.argmax(sizes[idx])]))
+        pick.update(int(i) for i in idx[np.linspace(0, len(idx) - 1, 8).astype(int)])
+    for s in sorted(pick):
+        a = O.System(*trip[s]).attempt(H[s])
+        assert relerr(S["r"][s], a["r"]) < 1e-12, (s, sizes[s])
+        assert relerr(S["v"][s], a["v"]) < 1e-12, (s, sizes[s])
+        assert abs(S["t"][s] - a["t"]) <= 1e-12 * abs(a["t"]), (s, sizes[s])
+
+
 @pytest.mark.parametrize("G", [1, 2, 4])
 def test_split_attempt_is_bit_identical_to_one_cta(G):
     """The split schedule -G runs the same arithmetic as the one-CTA schedule G: start, the
