@@ -149,6 +149,23 @@ def mstar_strerror(code: int) -> str:
     return load().mstar_strerror(int(code)).decode()
 
 
+def _system(m, r, v):
+    """Contiguous float64 m[n], r[n, 3], v[n, 3] of one system. The library reads exactly n
+    masses and 3n coordinates through each pointer, so any other shape is a ValueError
+    (r and v may also come flat, as 3n values in body order)."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    if m.ndim != 1:
+        raise ValueError(f"masses must be a vector, got shape {m.shape}")
+    return m, _vectors(r, len(m), "r"), _vectors(v, len(m), "v")
+
+
+def _vectors(x, n, name):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.shape not in ((n, 3), (3 * n,)):
+        raise ValueError(f"{name} must have shape ({n}, 3), got {x.shape}")
+    return x.reshape(n, 3)
+
+
 def mstar_default_params(**overrides) -> mstar_params:
     p = mstar_params()
     load().mstar_default_params(C.byref(p))
@@ -255,15 +272,13 @@ class Integrator:
     def __init__(self, m, r, v, device=None, **params):
         import torch
 
+        m, r, v = _system(m, r, v)
         if not torch.cuda.is_available():
             raise RuntimeError("libmstar needs a CUDA GPU")
         load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.p = mstar_default_params(**params)
-        m = np.ascontiguousarray(m, dtype=np.float64)
-        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 3)
-        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
         self.n = len(m)
         nbytes = mstar_workspace_bytes(self.n, self.p)
         if nbytes == 0:
@@ -306,7 +321,7 @@ class Integrator:
         return dict(t=t, r=r, v=v)
 
     def set_state(self, t, r, v):
-        mstar_set_state(self.ctx, t, np.ascontiguousarray(r, np.float64), np.ascontiguousarray(v, np.float64))
+        mstar_set_state(self.ctx, t, _vectors(r, self.n, "r"), _vectors(v, self.n, "v"))
 
     def set_H(self, H):
         mstar_set_H(self.ctx, H)
@@ -400,7 +415,7 @@ class Batch:
     def __init__(self, systems, device=None, **params):
         import torch
 
-        systems = list(systems)
+        systems = [_system(*sm) for sm in systems]
         if not systems:
             raise MstarError(MSTAR_ERR_INVALID_ARG, "Batch: no systems")
         if not torch.cuda.is_available():
@@ -412,9 +427,9 @@ class Batch:
         self.offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
         self.nsys = len(systems)
         self.nbody = int(self.offsets[-1])
-        m = np.ascontiguousarray(np.concatenate([np.asarray(s[0], np.float64) for s in systems]))
-        r = np.ascontiguousarray(np.concatenate([np.asarray(s[1], np.float64).reshape(-1, 3) for s in systems]))
-        v = np.ascontiguousarray(np.concatenate([np.asarray(s[2], np.float64).reshape(-1, 3) for s in systems]))
+        m = np.ascontiguousarray(np.concatenate([s[0] for s in systems]))
+        r = np.ascontiguousarray(np.concatenate([s[1] for s in systems]))
+        v = np.ascontiguousarray(np.concatenate([s[2] for s in systems]))
         nbytes = mstar_batch_workspace_bytes(self.nsys, self.offsets, self.p)
         if nbytes == 0:  # let the library name the problem (it rejects before allocating)
             self.b = mstar_batch_init(self.nsys, self.offsets, m, r, v, self.p)
@@ -452,6 +467,9 @@ class Batch:
                     v=[v[o[s]:o[s + 1]] for s in range(self.nsys)])
 
     def set_H(self, H):
+        H = np.ascontiguousarray(H, dtype=np.float64)
+        if H.shape != (self.nsys,):
+            raise ValueError(f"H must have one entry per system ({self.nsys}), got shape {H.shape}")
         mstar_batch_set_H(self.b, H)
 
     def set_schedule(self, schedule):

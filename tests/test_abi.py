@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2001_03180_gb300 import build as B
@@ -64,6 +65,19 @@ def test_batch_layout_rules_without_gpu():
     with pytest.raises(M.MstarError) as e:
         M.Batch([])
     assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+
+
+def test_binding_checks_array_shapes_before_any_device_work():
+    """The library reads n masses and 3n coordinates through each pointer: the binding refuses
+    arrays of any other shape instead of letting the copy read past them."""
+    m, r, v = np.ones(5), np.zeros((5, 3)), np.zeros((5, 3))
+    for bad in [(m, r[:4], v), (m, r, v[:, :2]), (m.reshape(5, 1), r, v), (m, r.T, v), (m, r, np.zeros(14))]:
+        with pytest.raises(ValueError):
+            M.Integrator(*bad)
+        with pytest.raises(ValueError):
+            M.Batch([(m, r, v), bad])
+    mm, rr, vv = M._system(m, r.ravel(), v)          # flat 3n coordinates in body order are accepted
+    assert rr.shape == (5, 3) and vv.shape == (5, 3) and mm.shape == (5,)
 
 
 def test_no_cpu_fallback_in_product_path():
