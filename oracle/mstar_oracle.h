@@ -119,7 +119,9 @@ void orc_free(orc_system* s);
 void orc_get_state(const orc_system* s, double* t, double* r, double* v, double* H, double* B);
 void orc_set_H(orc_system* s, double H);
 /* One GBS step attempt with fictitious step H from the current state; the state is not
-   changed. Writes eps and the extrapolated (r, v, t), plus U0 at the step start. */
+   changed. Writes eps and the extrapolated (r, v, t), plus U0 at the step start. Pinned:
+   the error estimate has order 2 k_fix - 1 in H; a step of H then -H returns within eps
+   (time symmetry); the error-norm reading itself is parity unpinned. */
 int orc_attempt(orc_system* s, double H, double* eps, double* r_out, double* v_out, double* t_out,
                 double* U0_out);
 /* One leapfrog division with nsub substeps over H from the current state, without
@@ -128,7 +130,9 @@ int orc_leapfrog(orc_system* s, int nsub, double H, double* r_out, double* v_out
 /* Overwrite the Cartesian state (keeps B, H). */
 void orc_set_state(orc_system* s, double t, const double* r, const double* v);
 /* Take accepted GBS steps towards t_end (Sec. 2.3-2.4) until |t - t_end| <= t_tol |t_end|
-   or max_steps accepted steps. */
+   or max_steps accepted steps. Pinned: the analytic Kepler solution, energy and momentum
+   conservation, the end time, and the controller's fixed point a_GBS^(2k_fix-1) eta; the
+   values of a_GBS, the growth clamp, q and t_tol are parity unpinned. */
 int orc_integrate(orc_system* s, double t_end, int max_steps, orc_stats* st);
 /* Energy diagnostics of the current state: E = T - U (Eq. 1), momentum P, angular momentum L. */
 void orc_energy(const orc_system* s, double* E, double* T, double* U, double P[3], double L[3]);
