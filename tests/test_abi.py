@@ -113,3 +113,27 @@ def test_no_gpu_means_no_integrator():
     for make in (lambda: M.Integrator(m, r, v), lambda: M.Batch([(m, r, v)])):
         with pytest.raises(RuntimeError):
             make()
+
+
+def test_c_entry_points_without_gpu_return_errors():
+    """Called directly without a GPU, mstar_init and mstar_batch_init return an error code and
+    no context: nothing is computed on the host."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import ctypes as C
+
+    B.build()
+    L = M.load()
+    m = np.ones(4)
+    r = np.random.default_rng(0).random((4, 3))
+    v = np.zeros((4, 3))
+    p = M.mstar_default_params()
+    ctx = C.c_void_p()
+    rc = L.mstar_init(C.byref(ctx), 4, m.ctypes.data, r.ctypes.data, v.ctypes.data, C.byref(p), None, 0, None)
+    assert rc in (M.MSTAR_ERR_CUDA, M.MSTAR_ERR_NOMEM) and not ctx.value
+    offs = np.array([0, 4], np.int32)
+    b = C.c_void_p()
+    rc = L.mstar_batch_init(C.byref(b), 1, offs.ctypes.data, m.ctypes.data, r.ctypes.data, v.ctypes.data,
+                            C.byref(p), None, 0, None)
+    assert rc in (M.MSTAR_ERR_CUDA, M.MSTAR_ERR_NOMEM) and not b.value
