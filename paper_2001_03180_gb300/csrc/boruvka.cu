@@ -86,7 +86,9 @@ k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* _
       const float lx = fmaxf(fmaf(dx, -0x1p-22f, dx) - e, 0.0f);
       const float ly = fmaxf(fmaf(dy, -0x1p-22f, dy) - e, 0.0f);
       const float lz = fmaxf(fmaf(dz, -0x1p-22f, dz) - e, 0.0f);
-      const float lo = ((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f);
+      // (1 - 2^-20) covers the relative rounding of normal results; 2^-144 the absolute
+      // rounding (<= 2^-150 per operation) of squares and sums that fall below 2^-126
+      const float lo = fmaxf(((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f) - 0x1p-144f, 0.0f);
       if (lo <= bhi && sc[q] != ci) {
         const int jj = t0 + q;
         const double d = d2_exact(X, Y, Z, i, jj);

@@ -302,7 +302,9 @@ __device__ __forceinline__ float dc_lower_bound(const float4& p, const float4& q
   const float lx = fmaxf(0.f, fmaf(dx, -0x1p-22f, dx) - e), ly = fmaxf(0.f, fmaf(dy, -0x1p-22f, dy) - e),
               lz = fmaxf(0.f, fmaf(dz, -0x1p-22f, dz) - e);
   const float s = fmaf(lz, lz, fmaf(ly, ly, lx * lx));
-  return fmaf(s, -0x1p-20f, s);
+  // relative rounding of normal results, and 2^-144 for the absolute rounding (<= 2^-150 per
+  // operation) of squares and sums below 2^-126
+  return fmaxf(fmaf(s, -0x1p-20f, s) - 0x1p-144f, 0.0f);
 }
 
 struct LpCand {

@@ -201,8 +201,10 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
       const float hx = ax + ex, hy = ay + ey, hz = az + ez;
       // (1 -/+ 2^-20) absorbs the float roundings of the sums of squares and the FP64
       // distance's own relative error (< 2^-50); hi is trusted only above 1e-30, where no
-      // square that matters can underflow.
-      const float lo = ((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f);
+      // square that matters can underflow. Below 2^-126 the roundings are absolute (<= 2^-150
+      // per operation), which the 2^-144 taken off lo covers; lo stays >= 0, as the
+      // bit-pattern comparisons of the keys need.
+      const float lo = fmaxf(((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f) - 0x1p-144f, 0.0f);
       const float hi = ((hx * hx + hy * hy) + hz * hz) * (1.0f + 0x1p-20f);
       if (hi < klo[s] && hi >= 1e-30f) {
         klo[s] = lo;
