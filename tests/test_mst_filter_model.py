@@ -138,3 +138,35 @@ def test_the_filter_is_not_vacuous():
     lo = _lower_plain(lx, ly, lz).astype(np.float64)
     ok = d > 1e-2
     assert np.all(lo[ok] > d[ok] * (1 - 1e-5))
+
+
+def _prim_terms(fi, fj):
+    """The Prim kernel's per-pair float terms: |differences|, their error radii
+    (|x_u| + |x_w| + |dx|) 2^-23 + 1e-37, and the bodies' own radii max|x| 2^-23 + 1e-37."""
+    ad = np.abs(fi - fj)
+    ex = ((np.abs(fi) + np.abs(fj)) + ad) * F(2.0 ** -23) + F(1e-37)
+    eu = _err_bound(fi[:, 0], fi[:, 1], fi[:, 2])
+    ew = _err_bound(fj[:, 0], fj[:, 1], fj[:, 2])
+    return ad, ex.astype(np.float32), eu, ew
+
+
+def test_prim_key_interval_and_quick_test():
+    """The Prim kernel's interval [lo, hi] of a squared distance holds the FP64 value (hi is
+    used only above 1e-30), and its quick test on the largest coordinate difference,
+    fmaf(a, -2^-22, a) - (e_u + e_w), never exceeds the FP64 distance itself."""
+    rng = np.random.default_rng(21)
+    for ri, rj in _cases(rng, 20000):
+        fi, fj = _f32_of(ri), _f32_of(rj)
+        ad, ex, eu, ew = _prim_terms(fi, fj)
+        l = np.maximum(ad - ex, F(0.0))
+        h = ad + ex
+        lo = np.maximum(((l[:, 0] * l[:, 0] + l[:, 1] * l[:, 1]) + l[:, 2] * l[:, 2]) * F(1.0 - 2.0 ** -20)
+                        - MARGIN, F(0.0)).astype(np.float64)
+        hi = (((h[:, 0] * h[:, 0] + h[:, 1] * h[:, 1]) + h[:, 2] * h[:, 2]) * F(1.0 + 2.0 ** -20)).astype(np.float64)
+        d = _d2_exact(ri[:, 0], ri[:, 1], ri[:, 2], rj[:, 0], rj[:, 1], rj[:, 2])
+        assert np.all(lo <= d)
+        used = hi >= 1e-30
+        assert np.all(hi[used] >= d[used])
+        a = ad.max(axis=1)
+        quick = ((a.astype(np.float64) * (1.0 - 2.0 ** -22)).astype(np.float32) - (eu + ew)).astype(np.float64)
+        assert np.all(quick <= np.sqrt(d) * (1 + 2.0 ** -50))
