@@ -123,11 +123,16 @@ MSTAR_API int mstar_attempt(mstar_ctx* ctx, double H, double* eps, double* r_out
    sum, total momentum P and angular momentum L about the origin. NULL outputs skipped. */
 MSTAR_API int mstar_energy(mstar_ctx* ctx, double* E, double* T, double* U, double P[3], double L[3]);
 
-/* Read / replace the current state (t, r[n x 3], v[n x 3]); set_state keeps B and H. */
+/* Read / replace the current state (t, r[n x 3], v[n x 3]). get_state returns the state in
+   the centre-of-mass frame; any output may be NULL. set_state keeps B and H and takes r and v
+   as given: the caller keeps them in the centre-of-mass frame (as get_state returns them);
+   a non-finite state makes the next step fail with NO_CONVERGENCE. Errors: INVALID_ARG (NULL
+   ctx; for set_state also NULL r or v, or a non-finite t), CUDA. */
 MSTAR_API int mstar_get_state(mstar_ctx* ctx, double* t, double* r, double* v);
 MSTAR_API int mstar_set_state(mstar_ctx* ctx, double t, const double* r, const double* v);
 
-/* Set the next fictitious step H (0 = unset: the next mstar_step uses ds = q U dt). */
+/* Set the next fictitious step H (0 = unset: the next mstar_step uses ds = q U dt).
+   Errors: INVALID_ARG (NULL ctx or a non-finite H). */
 MSTAR_API int mstar_set_H(mstar_ctx* ctx, double H);
 
 /* Prim's MST of the current positions (Sec. 3.2) and its indexing (Sec. 3.4): root
