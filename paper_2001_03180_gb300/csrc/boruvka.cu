@@ -310,9 +310,13 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
     root_out[0] = root;
   }
   __syncthreads();
+  // Level by level: [h, t) is the current level. Every thread reads the level's end t before
+  // the barrier, and no thread appends to the queue before it, so all threads see the same
+  // t, take the same number of turns and leave the loop together.
   int h = 0, depth = 0;
   while (true) {
     const int t = min(qtail, n);
+    __syncthreads();
     if (h >= t) break;
     for (int q = h + tid; q < t; q += nt) {
       const int u = s_q[q];
