@@ -86,6 +86,9 @@ def lib():
             L.orc_div_assign.restype = C.c_int
             L.orc_div_assign.argtypes = [C.c_int, C.c_int, _I]
             L.orc_gbs_harmonic.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, _D, _D]
+            L.orc_gbs_error.restype = C.c_double
+            L.orc_gbs_error.argtypes = [C.c_int, _I, _D, _D, _D, _D, _D, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_double, C.c_int]
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.c_int, _D, _D, _D, C.POINTER(Params)]
             L.orc_free.argtypes = [C.c_void_p]
@@ -239,6 +242,17 @@ def neville(nseq, S):
     Tkk = np.empty(nvar); Tprev = np.empty(nvar)
     lib().orc_neville(kf, _i(nseq), nvar, _d(S), _d(Tkk), _d(Tprev))
     return Tkk, Tprev
+
+
+def gbs_error(parent, Tkk, Tprev, X0, V0, A0, t0, T0, B, U0, H, k_fix=8) -> float:
+    """Eq. gbs-criterion (orc_gbs_error): Tkk, Tprev of length 6n+1; X0, V0, A0 edge vectors n x 3."""
+    parent = np.ascontiguousarray(parent, np.int32)
+    n = len(parent)
+    Tkk = _f64(Tkk); Tprev = _f64(Tprev)
+    X0 = _f64(X0, (-1, 3)); V0 = _f64(V0, (-1, 3)); A0 = _f64(A0, (-1, 3))
+    assert Tkk.shape == (6 * n + 1,) and Tprev.shape == (6 * n + 1,) and X0.shape == (n, 3)
+    return lib().orc_gbs_error(n, _i(parent), _d(Tkk), _d(Tprev), _d(X0), _d(V0), _d(A0), float(t0), float(T0),
+                               float(B), float(U0), float(H), int(k_fix))
 
 
 def div_assign(k_fix, n_div):

@@ -768,6 +768,41 @@ static void orc_prepare(orc_system* s) {
 
 static double vnorm(double x, double y, double z) { return sqrt((x * x + y * y) + z * z); }
 
+/* Eq. gbs-criterion in the reading R6-R8: the change between the last two extrapolants,
+   relative to the state advanced by one substep delta = H/n_kfix (n_kfix = 2 k_fix, Eq.
+   seq-deuflhard) along its derivative at the step start s0 (the LogH equations, Sec. 2.1:
+   dX/ds = V/(T+B), dV/ds = A/U, dt/ds = 1/(T+B)), as a Euclidean norm per 3-vector. */
+double orc_gbs_error(int n, const int* parent, const double* Tkk, const double* Tprev, const double* X0,
+                     const double* V0, const double* A0, double t0, double T0, double B, double U0, double H,
+                     int k_fix) {
+  double delta = H / (2 * k_fix);
+  double rate = 1.0 / (T0 + B);
+  double eps = 0.0;
+  int nan_seen = 0;
+  for (int v = 0; v < n; ++v) {
+    if (parent[v] < 0) continue;
+    const double* dX = Tkk + 3 * v; const double* pX = Tprev + 3 * v;
+    const double* dV = Tkk + 3 * (size_t)n + 3 * v; const double* pV = Tprev + 3 * (size_t)n + 3 * v;
+    const double* x0 = X0 + 3 * v; const double* v0 = V0 + 3 * v; const double* a0 = A0 + 3 * v;
+    double num = vnorm(dX[0] - pX[0], dX[1] - pX[1], dX[2] - pX[2]);
+    double den = vnorm(x0[0] + delta * (v0[0] * rate), x0[1] + delta * (v0[1] * rate),
+                       x0[2] + delta * (v0[2] * rate));
+    double q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+    num = vnorm(dV[0] - pV[0], dV[1] - pV[1], dV[2] - pV[2]);
+    den = vnorm(v0[0] + delta * (a0[0] / U0), v0[1] + delta * (a0[1] / U0), v0[2] + delta * (a0[2] / U0));
+    q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+  }
+  {
+    double num = fabs(Tkk[6 * (size_t)n] - Tprev[6 * (size_t)n]);
+    double den = fabs(t0 + delta * rate);
+    double q = num / fmax(den, 1e-300);
+    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
+  }
+  return nan_seen ? NAN : eps;
+}
+
 /* k_fix leapfrog divisions from the current state, Neville-Aitken extrapolation, and the
    error of Eq. gbs-criterion. Leaves T_{kf,kf} in s->Tkk. Returns eps (NaN if any ratio
    is not a number). */
@@ -791,36 +826,10 @@ static double orc_divisions(orc_system* s, double H) {
     Sk[6 * (size_t)n] = d.t;
   }
   orc_neville(kf, nseq, (int)nv, s->S, s->Tkk, s->Tprev);
-  /* Eq. gbs-criterion with h/n = H/n_kfix and S' taken at s0 */
-  double delta = H / nseq[kf - 1];
-  double rate = 1.0 / (s->T0 + s->B);
-  double eps = 0.0;
-  int nan_seen = 0;
-  for (int v = 0; v < n; ++v) {
-    if (s->parent[v] < 0) continue;
-    const double* dX = s->Tkk + 3 * v; const double* pX = s->Tprev + 3 * v;
-    const double* dV = s->Tkk + 3 * (size_t)n + 3 * v; const double* pV = s->Tprev + 3 * (size_t)n + 3 * v;
-    const double* X0 = s->X0 + 3 * v; const double* V0 = s->V0 + 3 * v; const double* A0 = s->A0 + 3 * v;
-    double num = vnorm(dX[0] - pX[0], dX[1] - pX[1], dX[2] - pX[2]);
-    double den = vnorm(X0[0] + delta * (V0[0] * rate), X0[1] + delta * (V0[1] * rate),
-                       X0[2] + delta * (V0[2] * rate));
-    double q = num / fmax(den, 1e-300);
-    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
-    num = vnorm(dV[0] - pV[0], dV[1] - pV[1], dV[2] - pV[2]);
-    den = vnorm(V0[0] + delta * (A0[0] / s->U0), V0[1] + delta * (A0[1] / s->U0),
-                V0[2] + delta * (A0[2] / s->U0));
-    q = num / fmax(den, 1e-300);
-    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
-  }
-  {
-    double num = fabs(s->Tkk[6 * (size_t)n] - s->Tprev[6 * (size_t)n]);
-    double den = fabs(s->t + delta * rate);
-    double q = num / fmax(den, 1e-300);
-    if (isnan(q)) nan_seen = 1; else if (q > eps) eps = q;
-  }
+  double eps = orc_gbs_error(n, s->parent, s->Tkk, s->Tprev, s->X0, s->V0, s->A0, s->t, s->T0, s->B, s->U0, H, kf);
   free(nseq);
   free(d.X); free(d.V); free(d.r); free(d.v); free(d.a);
-  return nan_seen ? NAN : eps;
+  return eps;
 }
 
 int orc_attempt(orc_system* s, double H, double* eps, double* r_out, double* v_out, double* t_out,

@@ -13,8 +13,9 @@
  * zero at the root. Built with -ffp-contract=off, so a*b+c always rounds twice.
  *
  * Parity status of each function is stated beside it: "pinned" functions are checked
- * by CPU tests against facts the paper or mathematics fix; the error-norm reading is
- * "parity unpinned" (only oracle <-> GPU agreement is checked for it).
+ * by CPU tests against facts the paper or mathematics fix. The constants the paper leaves
+ * open (a_GBS = 0.9, the growth clamp [0.2, 2], q = 0.1, t_tol = 1e-10) are "parity
+ * unpinned": only oracle <-> GPU agreement is checked for them.
  */
 #ifndef MSTAR_ORACLE_H
 #define MSTAR_ORACLE_H
@@ -113,6 +114,19 @@ int orc_div_assign(int kf, int ndiv, int* group);
    code as the N-body step. out[0]=x, out[1]=p extrapolated. Pinned (order H^(2k+1)). */
 void orc_gbs_harmonic(double w, double x0, double p0, double H, int kf, double* out, double* out_prev);
 
+/* Eq. gbs-criterion (readings R6-R8): the error of an attempt of fictitious step H from
+   the extrapolants Tkk = T_{kf,kf} and Tprev = T_{kf-1,kf-1} (each 6n+1: X, V as n x 3
+   edge vectors stored at the child vertex, then t) and the step-start state X0, V0, A0
+   (edge vectors; A0 = a_v - a_parent(v)), t0, T0, B, U0. With delta = H/(2 k_fix):
+     eps = max over non-root v of |dX_v| / |X0_v + delta V0_v/(T0+B)| and
+           |dV_v| / |V0_v + delta A0_v/U0|, and |dt| / |t0 + delta/(T0+B)|,
+   d = Tkk - Tprev, |.| the Euclidean norm of a 3-vector, every denominator floored at
+   1e-300; NaN if any ratio is NaN. Pinned on hand-worked cases (each term, the root
+   skipped, the floor, NaN). */
+double orc_gbs_error(int n, const int* parent, const double* Tkk, const double* Tprev, const double* X0,
+                     const double* V0, const double* A0, double t0, double T0, double B, double U0, double H,
+                     int k_fix);
+
 /* Systems (state owned by the oracle). */
 orc_system* orc_create(int n, const double* m, const double* r, const double* v, const orc_params* p);
 void orc_free(orc_system* s);
@@ -121,7 +135,7 @@ void orc_set_H(orc_system* s, double H);
 /* One GBS step attempt with fictitious step H from the current state; the state is not
    changed. Writes eps and the extrapolated (r, v, t), plus U0 at the step start. Pinned:
    the error estimate has order 2 k_fix - 1 in H; a step of H then -H returns within eps
-   (time symmetry); the error-norm reading itself is parity unpinned. */
+   (time symmetry); the norm itself through orc_gbs_error. */
 int orc_attempt(orc_system* s, double H, double* eps, double* r_out, double* v_out, double* t_out,
                 double* U0_out);
 /* One leapfrog division with nsub substeps over H from the current state, without

@@ -247,6 +247,28 @@ def test_neville_exact_on_polynomials(kf):
     assert Tkk[0] == pytest.approx((-1) ** (kf + 1) * np.prod(x), rel=1e-10)
 
 
+@pytest.mark.parametrize("kf", [2, 4, 8])
+def test_neville_second_output_is_the_previous_diagonal(kf):
+    """The convergence test compares successive extrapolants (Sec. 4.2, reading R7): the second
+    output is T_{kf-1,kf-1}, the extrapolation from the first kf-1 divisions alone. For
+    f = x^(kf-1), monic of degree kf-1 with kf-1 nodes x_1..x_{kf-1}, the interpolant's value at 0
+    is f(0) - prod(0 - x_i) = (-1)^kf prod_{i<kf} x_i, while T_kk is exact (0). The other
+    reading, T_{kf,kf-1} (nodes x_2..x_kf), would give (-1)^kf prod_{i>1} x_i instead."""
+    nseq = np.array([2 * (k + 1) for k in range(kf)], np.int32)
+    x = 1.0 / nseq.astype(float) ** 2
+    Tkk, Tprev = O.neville(nseq, (x ** (kf - 1))[:, None])
+    assert Tkk[0] == pytest.approx(0.0, abs=1e-15)
+    want = (-1) ** kf * np.prod(x[:-1])
+    other = (-1) ** kf * np.prod(x[1:])
+    assert Tprev[0] == pytest.approx(want, rel=1e-10)
+    assert abs(Tprev[0] - other) > 0.5 * abs(want - other)
+    # a polynomial of degree < kf-1 is reproduced exactly by both diagonals
+    st = W.Stream(kf, 4)
+    coef = st.uniform(kf - 1) - 0.5
+    Tkk, Tprev = O.neville(nseq, np.polyval(coef, x)[:, None])
+    assert Tprev[0] == pytest.approx(coef[-1], abs=1e-13)
+
+
 @pytest.mark.parametrize("kf", [2, 3])
 def test_gbs_order_on_harmonic_oscillator(kf):
     """Even-power error expansion (Sec. 2.3): with k_fix divisions the extrapolated step has
