@@ -270,9 +270,11 @@ MSTAR_API void mstar_batch_free(mstar_batch* b);
    device synchronisation cudaMalloc implies. It needs no context and calls no allocating
    routine (no cudaMalloc/cudaFree, no allocating library call).
    Computes, with every pair taken as far (Cartesian separations, as n_d = 0), the
-   accelerations a_i = G sum_j m_j (r_j - r_i)/|r_j - r_i|^3 (Eq. 2) and the force function
-   U = G sum_{i<j} m_i m_j / |r_j - r_i| (Eq. 1), with the same symmetric tiled loop and
-   reduction order as mstar_accelerations on a context created with n_d = 0.
+   accelerations a_i = G sum_j m_j (r_j - r_i)/|r_j - r_i|^3 and the force function
+   U = G sum_{i<j} m_i m_j / |r_j - r_i|. Its own kernel (128-body tiles, an FP64 reciprocal
+   square root, a plain FP64 sum of U) is not the context's pair kernel: the results agree
+   with mstar_accelerations on a context created with n_d = 0 to rounding (1e-13 relative),
+   not bit for bit, since the reduction order and the scalar arithmetic differ.
    Arguments: n in [2, MSTAR_NOALLOC_MAX_N] (larger n: MSTAR_ERR_UNSUPPORTED); m[n] and
    r[n x 3] (row-major) inputs, a[n x 3] and U[1] outputs - all four DEVICE (or managed)
    pointers owned by the caller (host pointers: MSTAR_ERR_INVALID_ARG); G > 0. The work is

@@ -1,4 +1,5 @@
-"""The allocation-free pair loop (mstar_accelerations_noalloc) against the context path.
+"""The allocation-free pair loop (mstar_accelerations_noalloc) against the context path and
+against the oracle's Cartesian (n_d = 0) pair loop.
 
 mstar_accelerations_noalloc serves callers that may not allocate device memory (a
 sub-integrator inside a code whose memory manager owns the device heap, or a loop that
@@ -9,6 +10,7 @@ tests; it also passes on its own in a fresh process.
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2001_03180_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +55,21 @@ def test_noalloc_matches_context_path_on_two_calls_in_a_row():
         a, U = noalloc(m, rc)
         assert np.abs(a - a_ref).max() <= 1e-13 * np.abs(a_ref).max()
         assert abs(U - U_ref) <= 1e-13 * U_ref
+
+
+@pytest.mark.parametrize("n", [2, 129, 333, 2047, M.MSTAR_NOALLOC_MAX_N])
+def test_noalloc_matches_oracle_cartesian_forces(n):
+    """Element by element against the oracle's pair loop with every pair Cartesian (n_d = 0),
+    on the same centre-of-mass positions: sizes with a ragged last 128-body tile (129, 333,
+    2047), the smallest system and the maximum."""
+    m, r, v = W.plummer(n, 40 + n) if n > 2 else W.kepler_binary(seed=3)
+    rc = O.com_shift(m, r)
+    root, par, lev, order = O.prim(rc)
+    X = O.to_mst(par, rc)
+    ao, Uo = O.forces(m, rc, par, lev, X, n_d=0)
+    a, U = noalloc(m, rc)
+    assert np.abs(a - ao).max() <= 1e-13 * np.abs(ao).max()
+    assert abs(U - Uo) <= 1e-13 * Uo
 
 
 def test_noalloc_rejects_oversize_and_host_pointers():
