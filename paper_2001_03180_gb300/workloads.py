@@ -316,6 +316,20 @@ def plummer_two_smbh(n_stars: int = 10000, seed: int = 5, m_bh: float = 0.005, d
     return m, r, v
 
 
+def perturbed(m, r, v, realisation: int, rel: float = 1e-15):
+    """Realisation `realisation` of an ensemble around (m, r, v): 0 is the input itself;
+    k > 0 multiplies every position and velocity component by 1 + rel (2u - 1), u uniform
+    from stream (7919, k). A rounding-level change of the start, so that the runs of an
+    ensemble sample the spread of rounding and truncation along their step sequences."""
+    if realisation == 0:
+        return m, r.copy(), v.copy()
+    st = Stream(7919, realisation)
+    n = len(m)
+    fr = 1.0 + rel * (2.0 * st.uniform(3 * n) - 1.0)
+    fv = 1.0 + rel * (2.0 * st.uniform(3 * n) - 1.0)
+    return m, r * fr.reshape(n, 3), v * fv.reshape(n, 3)
+
+
 @dataclass
 class System:
     m: np.ndarray
