@@ -29,19 +29,19 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "plummer10k_two_smbh"
 WORKLOAD_DESC = ("Plummer N=10000 (m=1e-4, r_vir=1, seed 5) + 2 SMBHs of 0.005 at +/-0.1 (N=10002); "
                  "eta_GBS=1e-12, k_fix=8 Deuflhard, N_d=2, G=1")
-# Algorithmic FP64 flops of one unordered far-pair interaction in the symmetric loop:
-# separation 3, r^2 5, reciprocal square root 7 (one DMUL, three DFMA), r^-3 2,
-# two mass scalings 2, force function 2, two 3-vector accumulations 12.
+# Algorithmic FP64 flops of one unordered far-pair interaction. The loop evaluates each
+# unordered pair once and applies it to both bodies: separation 3, r^2 5, reciprocal square
+# root 7 (one DMUL, three DFMA), r^-3 2, two mass scalings 2, force function 2, two 3-vector
+# accumulations 12; 16.5 flops per ordered pair-force.
 FLOPS_PER_UNORDERED_PAIR = 33
-# FP64-pipe instructions the tiled kernel issues per unordered pair (3 DADD for the
-# separation, 6 DFMA for the two force accumulations; ncu counts 3.0 DADD and 5.95 DFMA per
-# pair). r^2, 1/r, 1/r^3, the mass products and the force-function sum run on the integer
-# pipe, so the binding FP64 pipe caps this kernel at FP64 issue rate / 9 pairs.
-FP64_INSTR_PER_PAIR = 9
 # Flops of one ordered pair-force evaluated on its own, without the i<->j symmetry (3 DADD,
-# r^2 and a Newton-refined reciprocal square root, the mass scalings, 3 DFMA accumulations, U),
-# reported beside the symmetric count for comparison.
+# r^2 and a Newton-refined reciprocal square root, the mass scaling, 3 DFMA accumulations, U);
+# reported beside the symmetric count.
 FLOPS_PER_ORDERED_PAIR_NONSYM = 28
+# FP64-pipe instructions the tiled kernel issues per unordered pair: 3 DADD for the separation
+# and 6 DFMA for the two force accumulations (ncu counts 3.0 DADD and 5.95 DFMA per pair).
+# r^2, 1/r, 1/r^3, the mass products and the force-function sum run on the integer pipe.
+FP64_INSTR_PER_PAIR = 9
 NOMINAL_FP64_TFLOPS = 1.25
 # FP64 FMA units: 2 DFMA per clock per SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2 inst/cycle/SM), 152 SMs; the roofline peak is that rate at the SM clock
@@ -49,14 +49,30 @@ NOMINAL_FP64_TFLOPS = 1.25
 DFMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (read + write) of one k_pair_tiles launch at N = 10002 by the number of
-# division slots it evaluates, from the ncu capture summarised in
-# profiles/pair_tiles_plummer10k.md (the partials of more than ~2 slots overflow L2 and
-# round-trip through HBM); None once the kernel changes. An attempt launches the kernel for
-# 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots.
+# Figures from ncu captures of k_pair_tiles at N = 10002, valid for the kernel built from the
+# sources whose SHA-256 (csrc/pair.cu then csrc/device.cuh) starts with PAIR_TILE_SRC_SHA;
+# for any other source the bench reports them as null.
+#  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
+#    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
+#  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
+PAIR_TILE_SRC_SHA = "2e6acdc6a5f9b120"
 PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 446e3, 2: 714e3, 3: 14.31e6, 4: 39.64e6, 5: 65.77e6, 6: 92.18e6,
                                  7: 117.17e6, 8: 143.36e6}
+PAIR_TILE_FP64_PIPE_NCU = 0.870
 ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
+# Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
+# accelerations 24 written (parent and grandparent indices are another 8 read).
+ALGO_BYTES_PER_BODY_EVAL = 64
+
+
+def pair_source_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("pair.cu", "device.cuh"):
+        with open(os.path.join(ROOT, "paper_2001_03180_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def parse():
@@ -526,7 +542,7 @@ def run_mstar(args):
     n = len(m)
     g = M.Integrator(m, r, v, device=dev)
     stream = g.stream
-    fma_rate = M.mstar_fp64_fma_rate(stream.cuda_stream)
+    e_init = g.energy()["E"]
     t_end = 1.0
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -538,6 +554,12 @@ def run_mstar(args):
             flush.zero_()
             g.step(t_end, 1)
     torch.cuda.synchronize(dev)
+
+    # the FP64 FMA probe on the warm GPU (best of three), with the clock it ran at
+    probe_clk = ClockSampler(local)
+    probe_clk.start()
+    fma_rate = max(M.mstar_fp64_fma_rate(stream.cuda_stream) for _ in range(3))
+    probe_clocks = probe_clk.stop()
 
     # ---- device-resident timed region
     M.mstar_profile_enable(g.ctx, True)
@@ -568,6 +590,9 @@ def run_mstar(args):
     M.mstar_profile_enable(g.ctx, False)
     ms_max = reduce_max(ms, world, dev)
     pair_forces = float(fev) * n * (n - 1)
+    # energy error of the run so far (warm-up and timed steps from the initial state)
+    dE_c5 = abs((g.energy()["E"] - e_init) / e_init)
+    steps_c5 = args.warmup + acc
     total_pf = reduce_sum(pair_forces, world, dev)
     total_steps = reduce_sum(float(acc), world, dev)
     value = total_pf / (ms_max * 1e-3)
@@ -599,36 +624,52 @@ def run_mstar(args):
 
     # ---- roofline of the dominant kernel (tiled pair loop), CUDA events on its stream
     avg_ms = prof.pair_ms / max(prof.pair_launches, 1)
-    flops_per_launch = FLOPS_PER_UNORDERED_PAIR * prof.pair_interactions / max(prof.pair_launches, 1)
-    achieved = flops_per_launch / (avg_ms * 1e-3) / 1e12
+    pairs_per_launch = prof.pair_interactions / max(prof.pair_launches, 1)
+    achieved = FLOPS_PER_UNORDERED_PAIR * pairs_per_launch / (avg_ms * 1e-3) / 1e12
     clk_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = 2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / 1e12
-    # ceiling of this kernel: the FP64 pipe (2 instructions/clk/SM) saturated with its 9
-    # FP64 instructions per pair, times the 33 algorithmic flops each pair carries
-    peak = DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / FP64_INSTR_PER_PAIR * FLOPS_PER_UNORDERED_PAIR / 1e12
+    fp64_issue = DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6  # FP64 instructions/s the pipe takes
+    sha_ok = pair_source_sha() == PAIR_TILE_SRC_SHA
+    slots_per_launch = prof.force_evals / max(prof.pair_launches, 1)
     # per launch, averaged over an attempt's launches (the pattern of slot counts is fixed)
     traffic = (sum(PAIR_TILE_DRAM_BYTES_BY_SLOTS[k] for k in ATTEMPT_SLOT_PATTERN) / len(ATTEMPT_SLOT_PATTERN)
-               if PAIR_TILE_DRAM_BYTES_BY_SLOTS is not None else None)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch by slot count, "
-                                   "averaged over an attempt's 17 launches; the partials of more than ~2 slots "
-                                   "overflow L2"),
+               if sha_ok else None)
+    algo_bytes = ALGO_BYTES_PER_BODY_EVAL * n * slots_per_launch
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": traffic,
                 "kernel": "k_pair_tiles (symmetric pair loop: FP64 separations and force accumulations; "
                           "integer-pipe r^2, 1/r, m/r^3 and the exact fixed-point sum of m/r)",
-                "peak_source": ("derived: FP64 pipe 2 instr/clk/SM x 152 SMs x sampled SM clock / 9 FP64 "
-                                "instr per pair x 33 algorithmic flops per pair"),
-                "fp64_fma_peak_tflops": fp64_peak,
-                "frac_of_fp64_fma_peak": achieved / fp64_peak,
-                "peak_probe_tflops": 2.0 * fma_rate / 1e12,
+                "achieved_source": ("33 algorithmic FP64 flops per unordered far pair (each evaluated once and "
+                                    "applied to both bodies) x N(N-1)/2 pairs x evaluations per launch / mean "
+                                    "CUDA-event launch time on the context stream"),
+                "peak_source": ("FP64 unit peak from unit counts and clocks (no FP64 entry among the measured "
+                                "peaks): 2 DFMA/clk/SM x 152 SMs x the SM clock sampled in the timed region x "
+                                "2 flops"),
+                "frac_above_1_because": ("r^2, 1/r, r^-3, m r^-3 and the sum of m/r run on the integer pipe: the "
+                                         "FP64 pipe issues 9 instructions (3 DADD + 6 DFMA) of the 33 flops"),
+                "fp64_pipe_util": pairs_per_launch * FP64_INSTR_PER_PAIR / (avg_ms * 1e-3) / fp64_issue,
+                "fp64_pipe_util_source": ("pair rate x 9 FP64 instructions per pair / (2 per clk per SM x 152 "
+                                          "SMs x sampled clock)"),
+                "fp64_pipe_util_ncu": PAIR_TILE_FP64_PIPE_NCU if sha_ok else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch by slot count, "
+                                   "averaged over an attempt's 17 launches; null when the kernel's sources "
+                                   "differ from the captured ones" + ("" if sha_ok else " (they differ)")),
+                "algorithmic_bytes": algo_bytes,
+                "traffic_over_algorithmic": traffic / algo_bytes if traffic else None,
+                "survey_unit_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * pairs_per_launch / (avg_ms * 1e-3) / 1e12,
+                "survey_unit_frac": (FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * pairs_per_launch / (avg_ms * 1e-3) / 1e12
+                                     / fp64_peak),
+                "survey_unit_note": "28 flops per ordered pair-force as if each ordered pair were evaluated alone",
+                "probe_tflops": 2.0 * fma_rate / 1e12,
+                "probe_sm_mhz": probe_clocks.get("sm_mhz"),
+                "probe_frac_of_unit_peak": (2.0 * fma_rate / 1e12) / (
+                    2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * (probe_clocks.get("sm_mhz") or clk_mhz) * 1e6 / 1e12),
                 "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
                 "pair_kernel_share_of_step": prof.pair_ms / ms if ms > 0 else None,
                 # the whole timed step (every kernel of the hot path, rejected attempts and the
-                # L2 flush included) against the same ceiling
+                # L2 flush included) against the same peak
                 "whole_step_tflops": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12,
-                "whole_step_frac": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12 / peak,
-                "ordered_pair_28flop_equiv_tflops": FLOPS_PER_ORDERED_PAIR_NONSYM * 2 * prof.pair_interactions
-                / (prof.pair_ms * 1e-3) / 1e12 if prof.pair_ms > 0 else None}
+                "whole_step_frac": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12 / fp64_peak}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -669,6 +710,18 @@ def run_mstar(args):
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
                "adjoint": adjoint, "mst_builders": mst,
                "rebuild_test": rebuild, "small_configs": small}
+        sc = small or {}
+        # the figures of every section in a few keys at the end of the line
+        out["summary"] = {
+            "abs_dE_over_E": dE_c5, "abs_dE_over_E_steps": steps_c5,
+            "roofline_frac": roofline["frac"], "fp64_pipe_util": roofline["fp64_pipe_util"],
+            "c1_plummer64_abs_dE_over_E": sc.get("plummer64_to_t1", {}).get("abs_dE_over_E"),
+            "c1_plummer64_gbs_steps_per_s": sc.get("plummer64_to_t1", {}).get("gbs_steps_per_s"),
+            "c2_smbh2050_abs_dE_over_E": sc.get("plummer2048_smbh_binary_200_steps", {}).get("abs_dE_over_E"),
+            "c2_smbh2050_gbs_steps_per_s": sc.get("plummer2048_smbh_binary_200_steps", {}).get("gbs_steps_per_s"),
+            "batched_system_steps_per_s": (batched or {}).get("system_steps_per_s"),
+            "batched_ms_per_launch": (batched or {}).get("ms_per_launch"),
+            "adjoint_to_forward": (adjoint or {}).get("adjoint_to_forward")}
         print(json.dumps(out), flush=True)
     g.close()
     if world > 1:

@@ -3,7 +3,9 @@
 // The pair loop is bound by the FP64 pipe, whose rate on this part is far below the
 // tensor and FP32 rates and is not among the measured peaks, so the library
 // measures it on the device it runs on: every thread runs 8 independent DFMA chains,
-// the grid fills every SM with 8 warps, and the rate is timed with CUDA events.
+// the grid fills every SM with 8 CTAs of 8 warps, and the rate is timed with CUDA events
+// over a ~30 ms launch that follows a launch of the same size (so that the clocks have
+// ramped up under this load).
 #include "internal.h"
 
 namespace {
@@ -33,14 +35,14 @@ extern "C" MSTAR_API int mstar_fp64_fma_rate(double* fma_per_second, void* cuda_
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return MSTAR_ERR_CUDA;
-  const int grid = sms * 8, block = 256, iters = 256;
+  const int grid = sms * 8, block = 256, iters = 512;
   double* out = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int rc = MSTAR_ERR_CUDA;
   float ms = 0.0f;
   if (cudaMalloc(&out, sizeof(double) * grid * block) != cudaSuccess) return MSTAR_ERR_NOMEM;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
-  k_dfma_chains<<<grid, block, 0, s>>>(out, 0.9999999, 1e-9, 8);  // warm-up
+  k_dfma_chains<<<grid, block, 0, s>>>(out, 0.9999999, 1e-9, iters);  // warm-up
   cudaEventRecord(e0, s);
   k_dfma_chains<<<grid, block, 0, s>>>(out, 0.9999999, 1e-9, iters);
   cudaEventRecord(e1, s);
