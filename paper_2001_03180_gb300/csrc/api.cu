@@ -85,6 +85,8 @@ size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
   t.sv = c.take<double>(S * n3);
   t.sa = c.take<double>(S * n3);
   t.P = c.take<double>(S * (size_t)s.NT * 4 * np);
+  t.Pt = c.take<double>(S * 4 * np);
+  t.tcnt = c.take<int>(S * (size_t)s.NT);
   t.Ublk = c.take<double>(S * s.nblk);
   t.Tblk = c.take<double>(S * s.nblk);
   t.comblk = c.take<double>(S * s.nblk * 3);

@@ -41,6 +41,8 @@ struct Dev {
   double* sv;
   double* sa;
   double* P;        // pair partials: slots x NT x 4 x npad
+  double* Pt;       // their sums per body: slots x 4 x npad (ax, ay, az, sum of m/r)
+  int* tcnt;        // per slot and tile, the tile-pair CTAs counted in (0 between launches)
   double* Ublk;     // slots x nblk
   double* Tblk;     // slots x nblk
   double* comblk;   // slots x nblk x 3
@@ -75,6 +77,7 @@ struct AdjTraj {
 struct mstar_ctx {
   int n = 0, npad = 0, K = 0, nslots = 0;
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
+  int pair_defer = -1;  // trailing slots of a pair launch summed by the finishing pass (-1: unset)
   int nblk = 0;
   mstar_params p{};
   cudaStream_t stream = nullptr;

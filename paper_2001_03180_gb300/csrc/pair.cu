@@ -22,8 +22,19 @@
 //
 // Determinism: CTA (I, J) writes its i-side sums into partial slot J of the i bodies and
 // its j-side sums into slot I of the j bodies (a diagonal tile writes both into slot I).
-// Every body thus receives exactly one write per slot, and the finishing pass adds the
-// NT slots in a fixed order.
+// Every body thus receives exactly one write per slot, and the NT slots are added in a
+// fixed order.
+//
+// Reduction on chip: every tile receives exactly NT contributions (CTAs (t, J >= t) and
+// (I < t, t)). After writing its partials, a CTA counts itself in for its tiles; the CTA
+// that brings a tile's count to NT adds that tile's NT slots (ascending) while they are
+// still in L2, writes the 4 sums per body, resets the count and discards the partials'
+// L2 lines, so that they are never written back to DRAM. Nothing waits: the last CTA to
+// arrive finds everything it needs already written. The division slots of a launch run one
+// after another (blockIdx.y), so a slot's last tiles are summed while later slots' CTAs
+// compute. The trailing slots - those whose CTAs can still be resident together at the end
+// of the launch, or all whose partials fit in L2 anyway - are left to the finishing pass,
+// which reads their partials from L2 right after, so that no reduction trails the launch.
 #include "device.cuh"
 #include "internal.h"
 
@@ -42,11 +53,63 @@ __device__ __forceinline__ void tile_pair(int tp, int NT, int& I, int& J) {
   J = i + (tp - start(i));
 }
 
+// Sum of tile t's NT partial slots (ascending s) for its T bodies, one per thread, into
+// Pt (4 planes); then its count is reset and the partials' lines dropped from L2.
+template <int T>
+__device__ __forceinline__ void finish_tile(int t, int npad, int NT, const double* Ps, double* Pt, int* cnt) {
+  const int tid = threadIdx.x;
+  const double* q = Ps + (size_t)t * T + tid;
+  double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
+  // L2 loads (the slots were written by other CTAs after this SM's L1 could have seen
+  // them), four slots at a time ahead of their additions, which keep the ascending order
+  int s = 0;
+  for (; s + 4 <= NT; s += 4) {
+    double b[4][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double* qs = q + (size_t)(s + k) * 4 * npad;
+      b[k][0] = __ldcg(qs);
+      b[k][1] = __ldcg(qs + npad);
+      b[k][2] = __ldcg(qs + 2 * (size_t)npad);
+      b[k][3] = __ldcg(qs + 3 * (size_t)npad);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ax += b[k][0];
+      ay += b[k][1];
+      az += b[k][2];
+      u += b[k][3];
+    }
+  }
+  for (; s < NT; ++s) {
+    const double* qs = q + (size_t)s * 4 * npad;
+    ax += __ldcg(qs);
+    ay += __ldcg(qs + npad);
+    az += __ldcg(qs + 2 * (size_t)npad);
+    u += __ldcg(qs + 3 * (size_t)npad);
+  }
+  double* o = Pt + (size_t)t * T + tid;
+  o[0] = ax;
+  o[(size_t)npad] = ay;
+  o[2 * (size_t)npad] = az;
+  o[3 * (size_t)npad] = u;
+  __syncthreads();  // every thread has read the tile's slots
+  // the slots of tile t: NT x 4 runs of T doubles, each starting on a 256-byte boundary
+  // (npad and t T are multiples of T >= 32); T / 16 lines of 128 bytes per run
+  constexpr int kLinesPerRun = T / 16;
+  for (int l = tid; l < NT * 4 * kLinesPerRun; l += T) {
+    const int run = l / kLinesPerRun, line = l - run * kLinesPerRun;
+    const double* a = Ps + (size_t)run * npad + (size_t)t * T + 16 * line;
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+  }
+  if (tid == 0) cnt[t] = 0;
+}
+
 template <int W>
 __global__ void __launch_bounds__(32 * W)
 k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __restrict__ m,
              const int* __restrict__ parent, const int* __restrict__ gp, const double* __restrict__ sr,
-             double* __restrict__ P) {
+             double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from) {
   constexpr int T = 32 * W;
   __shared__ double sx[T], sy[T], sz[T], sax[T], say[T], saz[T];
   __shared__ unsigned long long smm[T];
@@ -150,6 +213,29 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
     qj[2 * (size_t)npad] = -saz[tid];
     qj[3 * (size_t)npad] = 0.0;
   }
+
+  // count this CTA in for tiles I and J; the last of a tile's NT contributors sums it (the
+  // trailing slots from keep_from on are summed by the finishing pass)
+  if ((int)blockIdx.y >= keep_from) return;
+  __shared__ int s_last[2];
+  __threadfence();  // this CTA's partials are visible device-wide before it is counted
+  __syncthreads();
+  if (tid == 0) {
+    int* cnt = tcnt + (size_t)slot * NT;
+    s_last[0] = atomicAdd(&cnt[I], 1) == NT - 1;
+    s_last[1] = diag ? 0 : atomicAdd(&cnt[J], 1) == NT - 1;
+    __threadfence();  // the counts seen before the other contributors' partials are read
+  }
+  __syncthreads();
+  if (s_last[0] | s_last[1]) {
+    int* cnt = tcnt + (size_t)slot * NT;
+    double* Pts = Pt + (size_t)slot * 4 * npad;
+    if (s_last[0]) finish_tile<T>(I, npad, NT, Ps, Pts, cnt);
+    if (s_last[1]) {
+      __syncthreads();
+      finish_tile<T>(J, npad, NT, Ps, Pts, cnt);
+    }
+  }
 }
 
 struct NearAcc {
@@ -166,27 +252,57 @@ struct NearAcc {
   }
 };
 
-// Sum of the tile partials plus the near pairs of Sec. 3.4 (N_d <= 2: parent, child,
-// grandparent, grandchild, sibling), times G. Writes a (3 planes) and per-block sums of
-// m_p * u_p, where u_p sums m_q / r_pq over partners q > p (each unordered pair once).
+// The tile sums plus the near pairs of Sec. 3.4 (N_d <= 2: parent, child, grandparent,
+// grandchild, sibling), times G. Writes a (3 planes) and per-block sums of m_p * u_p, where
+// u_p sums m_q / r_pq over partners q > p (each unordered pair once). The trailing slots
+// (blockIdx.y >= keep_from) sum their NT partial slots here (ascending, as the tile kernel does
+// for the other slots).
 __global__ void __launch_bounds__(kBlock)
 k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const double* __restrict__ m,
               const int* __restrict__ parent, const int* __restrict__ gp, const int* __restrict__ child_off,
               const int* __restrict__ child_idx, const double* __restrict__ sX, const double* __restrict__ P,
-              double* __restrict__ sa, double* __restrict__ Ublk, int nblk) {
+              const double* __restrict__ Pt, double* __restrict__ sa, double* __restrict__ Ublk, int nblk,
+              int keep_from) {
   __shared__ double scratch[32];
   const int slot = slot_lo + blockIdx.y;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   double um = 0.0;
   if (p < n) {
-    const double* Ps = P + (size_t)slot * NT * 4 * npad + p;
     NearAcc acc;
-    for (int s = 0; s < NT; ++s) {
-      const double* q = Ps + (size_t)s * 4 * npad;
-      acc.ax += q[0];
-      acc.ay += q[(size_t)npad];
-      acc.az += q[2 * (size_t)npad];
-      acc.u += q[3 * (size_t)npad];
+    if ((int)blockIdx.y >= keep_from) {
+      const double* q = P + (size_t)slot * NT * 4 * npad + p;
+      int s = 0;
+      for (; s + 4 <= NT; s += 4) {
+        double b[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double* qs = q + (size_t)(s + k) * 4 * npad;
+          b[k][0] = qs[0];
+          b[k][1] = qs[(size_t)npad];
+          b[k][2] = qs[2 * (size_t)npad];
+          b[k][3] = qs[3 * (size_t)npad];
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          acc.ax += b[k][0];
+          acc.ay += b[k][1];
+          acc.az += b[k][2];
+          acc.u += b[k][3];
+        }
+      }
+      for (; s < NT; ++s) {
+        const double* qs = q + (size_t)s * 4 * npad;
+        acc.ax += qs[0];
+        acc.ay += qs[(size_t)npad];
+        acc.az += qs[2 * (size_t)npad];
+        acc.u += qs[3 * (size_t)npad];
+      }
+    } else {
+      const double* q = Pt + (size_t)slot * 4 * npad + p;
+      acc.ax = q[0];
+      acc.ay = q[(size_t)npad];
+      acc.az = q[2 * (size_t)npad];
+      acc.u = q[3 * (size_t)npad];
     }
     if (n_d >= 1) {
       const double* Xx = sX + (size_t)slot * 3 * npad;
@@ -229,12 +345,32 @@ k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const dou
   if (threadIdx.x == 0) Ublk[(size_t)slot * nblk + blockIdx.x] = G * s;
 }
 
+// Partial bytes that the trailing slots of a launch may leave in L2 for the finishing pass.
+constexpr double kDeferL2Bytes = 48.0 * 1024 * 1024;
+
+// Trailing slots of a launch left to the finishing pass: the slots whose CTAs can be resident
+// together at the end of the launch (plus one), and at least as many as fit in the L2 budget.
 template <int W>
-cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d) {
+int defer_slots(const mstar_ctx* c) {
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_tiles<W>, 32 * W, 0) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    return 1 << 20;  // unknown: every slot is summed by the finishing pass
+  }
+  const long long resident = (long long)per_sm * sms;
+  const int d_wave = (int)((resident + c->ntp - 1) / c->ntp) + 1;
+  const double slot_bytes = (double)c->NT * 4.0 * c->npad * sizeof(double);
+  const int d_l2 = (int)(kDeferL2Bytes / slot_bytes);
+  return d_wave > d_l2 ? d_wave : d_l2;
+}
+
+template <int W>
+cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d, int keep_from) {
   dim3 grid(c->ntp, nsl);
   if (c->prof) prof_begin(c);
   k_pair_tiles<W><<<grid, 32 * W, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
-                                                  c->d.gp, c->d.sr, c->d.P);
+                                                  c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -247,17 +383,20 @@ cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d) {
 cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d) {
   const int nsl = slot_hi - slot_lo;
   if (nsl <= 0) return cudaSuccess;
+  if (c->pair_defer < 0)
+    c->pair_defer = c->W == 1 ? defer_slots<1>(c) : (c->W == 2 ? defer_slots<2>(c) : defer_slots<4>(c));
+  const int keep_from = nsl - c->pair_defer;  // slots below this index are summed on chip
   cudaError_t e;
   switch (c->W) {
-    case 1: e = run_tiles<1>(c, slot_lo, nsl, n_d); break;
-    case 2: e = run_tiles<2>(c, slot_lo, nsl, n_d); break;
-    default: e = run_tiles<4>(c, slot_lo, nsl, n_d); break;
+    case 1: e = run_tiles<1>(c, slot_lo, nsl, n_d, keep_from); break;
+    case 2: e = run_tiles<2>(c, slot_lo, nsl, n_d, keep_from); break;
+    default: e = run_tiles<4>(c, slot_lo, nsl, n_d, keep_from); break;
   }
   if (e != cudaSuccess) return e;
   dim3 grid(c->nblk, nsl);
   k_pair_finish<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->p.G, c->d.m, c->d.parent,
                                                 c->d.gp, c->d.child_off, c->d.child_idx, c->d.sX, c->d.P,
-                                                c->d.sa, c->d.Ublk, c->nblk);
+                                                c->d.Pt, c->d.sa, c->d.Ublk, c->nblk, keep_from);
   MSTAR_LAUNCHED(c);
   c->force_evals += nsl;
   return cudaGetLastError();

@@ -49,3 +49,52 @@ def test_every_partial_slot_written_once(NT):
             writes[I, J] += 1               # i-side sums of tile I's bodies
             writes[J, I] += 1               # j-side sums of tile J's bodies
     assert np.all(writes == 1)
+
+
+@pytest.mark.parametrize("NT", [1, 2, 3, 7, 32, 79, 128])
+def test_each_tile_counted_to_nt_once_in_any_order(NT):
+    """The on-chip reduction: every CTA counts itself in for tile I and (off the diagonal) tile
+    J; the CTA whose increment returns NT - 1 sums that tile. In any completion order of the
+    CTAs, every tile reaches NT exactly once, only after all its NT contributors have written,
+    and every count is back at 0 at the end of the launch."""
+    pairs = [tile_pair(tp, NT) for tp in range(NT * (NT + 1) // 2)]
+    rng = np.random.default_rng(NT)
+    for trial in range(5):
+        order = rng.permutation(len(pairs)) if trial else np.arange(len(pairs))
+        cnt = np.zeros(NT, np.int64)
+        written = np.zeros((NT, NT), bool)  # [tile, slot]
+        finished = np.zeros(NT, np.int64)
+        for k in order:
+            I, J = pairs[k]
+            written[I, J if I != J else I] = True
+            if I != J:
+                written[J, I] = True
+            for t in ([I] if I == J else [I, J]):
+                old = cnt[t]
+                cnt[t] += 1
+                if old == NT - 1:
+                    assert written[t].all()  # every slot of tile t is in place
+                    finished[t] += 1
+                    cnt[t] = 0
+        assert np.all(finished == 1) and np.all(cnt == 0)
+
+
+@pytest.mark.parametrize("W,n", [(1, 33), (1, 4096), (2, 4097), (2, 8192), (4, 8193), (4, 10240)])
+def test_discarded_lines_are_the_tiles_slots(W, n):
+    """finish_tile drops the L2 lines of tile t's NT x 4 runs of T doubles: every line it names
+    is 128-byte aligned, lies inside the slot's partial buffer and belongs to tile t, and the
+    lines of all tiles together cover the buffer once."""
+    T = 32 * W
+    npad = -(-n // T) * T
+    NT = npad // T
+    lines_per_run = T // 16
+    covered = np.zeros(NT * 4 * npad // 16, np.int32)  # 128-byte lines of one slot's partials
+    for t in range(NT):
+        for l in range(NT * 4 * lines_per_run):
+            run, line = divmod(l, lines_per_run)
+            off = run * npad + t * T + 16 * line   # in doubles from the slot's base
+            assert (off * 8) % 128 == 0
+            assert 0 <= off and off + 16 <= NT * 4 * npad
+            assert t * T <= off % npad < (t + 1) * T
+            covered[off // 16] += 1
+    assert np.all(covered == 1)
