@@ -182,8 +182,10 @@ def energy_comp(m, r, v, G=1.0) -> float:
 
 
 def rebuild_run(m, r, v, coords, cycles, topo_every, sample_at, deconstruct=0):
-    """Rebuild test of Sec. 3.5 (coords 0: MST, 1: chain; deconstruct 0: COM shift, 1: root
-    kept). Returns dict(r, v, E, topo_changes, mean_level); E[s] after sample_at[s] cycles."""
+    """Rebuild test of Sec. 3.5 (coords 0: MST, 1: chain; deconstruct 0: path sums and the COM
+    shift, 1: path sums and the root kept, 2: root outwards from the kept root, 3: root outwards
+    and the COM shift). Returns dict(r, v, E, topo_changes, mean_level); E[s] after sample_at[s]
+    cycles."""
     m = _f64(m); n = len(m)
     r = _f64(r, (n, 3)).copy(); v = _f64(v, (n, 3)).copy()
     sa = np.ascontiguousarray(sample_at, dtype=np.int32)

@@ -202,10 +202,21 @@ static void from_edges_keep_root(int n, const int* parent, int root, const doubl
   }
 }
 
+/* Deconstruction from the root outwards: in insertion order (every parent before its
+   children) w_v = w_parent(v) + X_v, starting from the root's kept position, so that a body
+   and its parent differ by one rounding of their edge vector. */
+static void from_edges_root_down(int n, const int* parent, const int* order, const double* W, double* w) {
+  for (int k = 0; k < n; ++k) {
+    int v = order[k], p = parent[v];
+    if (p < 0) continue;
+    for (int c = 0; c < 3; ++c) w[3 * v + c] = w[3 * p + c] + W[3 * v + c];
+  }
+}
+
 int orc_rebuild_run(int n, const double* m, double* r, double* v, int coords, int deconstruct, int cycles,
                     int topo_every, int nsample, const int* sample_at, double* E_out, int* topo_changes,
                     double* mean_level) {
-  if (n < 2 || cycles < 0 || topo_every < 1 || (coords != 0 && coords != 1) || (deconstruct != 0 && deconstruct != 1))
+  if (n < 2 || cycles < 0 || topo_every < 1 || (coords != 0 && coords != 1) || deconstruct < 0 || deconstruct > 3)
     return ORC_ERR_ARG;
   size_t b3 = sizeof(double) * 3 * (size_t)n;
   int* parent = (int*)malloc(sizeof(int) * (size_t)n);
@@ -233,9 +244,16 @@ int orc_rebuild_run(int n, const double* m, double* r, double* v, int coords, in
     if (deconstruct == 0) {
       orc_from_mst(n, m, parent, X, r);
       orc_from_mst(n, m, parent, V, v);
-    } else {
+    } else if (deconstruct == 1) {
       from_edges_keep_root(n, parent, order[0], X, r);
       from_edges_keep_root(n, parent, order[0], V, v);
+    } else {
+      from_edges_root_down(n, parent, order, X, r);
+      from_edges_root_down(n, parent, order, V, v);
+      if (deconstruct == 3) {
+        orc_com_shift(n, m, r);
+        orc_com_shift(n, m, v);
+      }
     }
     while (s < nsample && sample_at[s] == c) E_out[s++] = orc_energy_comp(n, m, r, v, 1.0);
   }

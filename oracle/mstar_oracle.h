@@ -74,7 +74,9 @@ double orc_energy_comp(int n, const double* m, const double* r, const double* v,
    MST, 1: the chain) from (r, v), i.e. the edge vectors X, V, and deconstruct them back to
    (r, v) by per-vertex path sums from the vertex up to the root, then either
    (deconstruct 0) the centre-of-mass shift, as the integrator does after every drift and
-   kick, or (deconstruct 1) adding the root's kept position. The topology is rebuilt every
+   kick, or (deconstruct 1) adding the root's kept position; or from the root outwards,
+   w_v = w_parent(v) + X_v in insertion order from the root's kept position (deconstruct 2),
+   then the centre-of-mass shift (deconstruct 3). The topology is rebuilt every
    `topo_every` cycles (the state moves only by rounding); topo_changes counts rebuilds
    that changed it. E_out[s] = the compensated energy after sample_at[s] cycles (sample_at
    ascending; 0 = the start). mean_level = the mean <L> of the topologies built. */

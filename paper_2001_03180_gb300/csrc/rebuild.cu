@@ -8,7 +8,9 @@
 //   tail on a tie), written as a path tree rooted at the tail;
 // - building: X_v = w_v - w_parent(v) (0 at the root);
 // - deconstruction: per-vertex path sums X_v + X_parent(v) + ... up to the root, then either
-//   the centre-of-mass shift (as the integrator's rebuild) or the root's kept position;
+//   the centre-of-mass shift (as the integrator's rebuild) or the root's kept position; or
+//   from the root outwards (w_v = w_parent(v) + X_v, parents first) with the root kept, then
+//   optionally the centre-of-mass shift;
 // - the topology is rebuilt every `topo_every` cycles and compared with the previous one;
 // - energies E = T - U with Neumaier-compensated sums of the FP64 terms in index order.
 // Every operation is the CPU definition's, in its order (the sums that are sequential there
@@ -198,31 +200,47 @@ __device__ void cta_chain(int n, const double* r, int* parent, int* level, int* 
 }
 
 // One deconstruction of w (3 components per body) from edge vectors W: per-vertex path
-// sums, then the centre-of-mass shift (decon 0) or the kept root position (decon 1).
-__device__ void deconstruct(int n, const double* m, const int* parent, int root, const double* W, double* w,
+// sums, then the centre-of-mass shift (decon 0) or the kept root position (decon 1); or from
+// the root outwards, w_v = w_parent(v) + W_v in insertion order with the root kept (decon 2),
+// then the centre-of-mass shift (decon 3).
+__device__ void deconstruct(int n, const double* m, const int* parent, const int* order, const double* W, double* w,
                             int decon, double* sc) {
+  const int root = order[0];
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int k = 0; k < 3; ++k) sc[k] = w[3 * root + k];
-  __syncthreads();
-  for (int v = threadIdx.x; v < n; v += kRbThreads) {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    for (int u = v; parent[u] >= 0; u = parent[u]) {
-      s0 = __dadd_rn(s0, W[3 * u]);
-      s1 = __dadd_rn(s1, W[3 * u + 1]);
-      s2 = __dadd_rn(s2, W[3 * u + 2]);
+  if (decon >= 2) {
+    // one thread per component walks the insertion order: every parent before its children
+    if (threadIdx.x < 3) {
+      const int c = threadIdx.x;
+      for (int k = 0; k < n; ++k) {
+        const int v = order[k], p = parent[v];
+        if (p >= 0) w[3 * v + c] = __dadd_rn(w[3 * p + c], W[3 * v + c]);
+      }
     }
-    if (decon) {
-      s0 = __dadd_rn(s0, sc[0]);
-      s1 = __dadd_rn(s1, sc[1]);
-      s2 = __dadd_rn(s2, sc[2]);
+    __syncthreads();
+    if (decon == 2) return;
+  } else {
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; ++k) sc[k] = w[3 * root + k];
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += kRbThreads) {
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+      for (int u = v; parent[u] >= 0; u = parent[u]) {
+        s0 = __dadd_rn(s0, W[3 * u]);
+        s1 = __dadd_rn(s1, W[3 * u + 1]);
+        s2 = __dadd_rn(s2, W[3 * u + 2]);
+      }
+      if (decon) {
+        s0 = __dadd_rn(s0, sc[0]);
+        s1 = __dadd_rn(s1, sc[1]);
+        s2 = __dadd_rn(s2, sc[2]);
+      }
+      w[3 * v] = s0;
+      w[3 * v + 1] = s1;
+      w[3 * v + 2] = s2;
     }
-    w[3 * v] = s0;
-    w[3 * v + 1] = s1;
-    w[3 * v + 2] = s2;
+    __syncthreads();
+    if (decon) return;
   }
-  __syncthreads();
-  if (decon) return;
   if (threadIdx.x == 0) {
     double M = 0.0, c[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < n; ++i) {
@@ -295,8 +313,8 @@ __global__ void __launch_bounds__(kRbThreads, 1) k_rebuild_jobs(RbArgs A) {
         V[3 * w + k] = p < 0 ? 0.0 : __dsub_rn(v[3 * w + k], v[3 * p + k]);
       }
     }
-    deconstruct(n, m, parent, order[0], X, r, decon, sc);
-    deconstruct(n, m, parent, order[0], V, v, decon, sc);
+    deconstruct(n, m, parent, order, X, r, decon, sc);
+    deconstruct(n, m, parent, order, V, v, decon, sc);
     __syncthreads();
     while (s < A.nsample && A.sample_at[s] == c) {
       energy_comp(n, m, r, v, row, &sc[6]);
@@ -332,7 +350,7 @@ extern "C" int mstar_rebuild_test(int njobs, int n, const double* m, const doubl
       !v || !coords || !deconstruct || (nsample && (!sample_at || !E_out)))
     return MSTAR_ERR_INVALID_ARG;
   for (int j = 0; j < njobs; ++j)
-    if ((coords[j] != 0 && coords[j] != 1) || (deconstruct[j] != 0 && deconstruct[j] != 1))
+    if ((coords[j] != 0 && coords[j] != 1) || deconstruct[j] < 0 || deconstruct[j] > 3)
       return MSTAR_ERR_INVALID_ARG;
   for (int s = 0; s < nsample; ++s)
     if (sample_at[s] < 0 || sample_at[s] > cycles || (s && sample_at[s] < sample_at[s - 1]))

@@ -3,7 +3,9 @@
 The transforms are pure additions, subtractions and one division per component, done in
 the CPU definition's order, and the energies are compensated sums in index order: the GPU's
 energies, final states, topology-change counts and mean levels must equal the oracle's bit
-for bit, for both coordinate systems and both deconstruction rules.
+for bit, for both coordinate systems and all four deconstruction rules (per-vertex path sums
+with the centre-of-mass shift or the root kept; from the root outwards with the root kept,
+or followed by the shift).
 """
 import numpy as np
 import pytest
@@ -37,14 +39,14 @@ def run_both(systems, jobs, cycles, topo_every, samples):
 
 def test_rebuild_test_bit_identical_to_oracle_hernquist379():
     systems = [W.hernquist(379, s)[:3] for s in (1, 2)]
-    jobs = [(s, c, d) for s in (0, 1) for c in (0, 1) for d in (0, 1)]
+    jobs = [(s, c, d) for s in (0, 1) for c in (0, 1) for d in (0, 1, 2, 3)]
     run_both(systems, jobs, 300, 100, [0, 1, 10, 100, 300])
 
 
 @pytest.mark.parametrize("n", [2, 3, 33, 600])
 def test_rebuild_test_other_sizes(n):
     systems = [W.plummer(n, n)]
-    jobs = [(0, c, d) for c in (0, 1) for d in (0, 1)]
+    jobs = [(0, c, d) for c in (0, 1) for d in (0, 1, 2, 3)]
     run_both(systems, jobs, 40, 7, [0, 3, 40])
 
 
@@ -56,5 +58,7 @@ def test_rebuild_test_rejects_bad_arguments():
     m, r, v = W.plummer(10, 1)
     with pytest.raises(M.MstarError):
         M.mstar_rebuild_test([(m, r, v)], [2], [0], 1, 1, [0])
+    with pytest.raises(M.MstarError):
+        M.mstar_rebuild_test([(m, r, v)], [0], [4], 1, 1, [0])
     with pytest.raises(M.MstarError):
         M.mstar_rebuild_test([(m, r, v)], [0], [0], 5, 1, [3, 2])

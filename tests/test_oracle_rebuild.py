@@ -122,7 +122,7 @@ def test_hernquist_has_no_hard_binary():
 
 
 @pytest.mark.parametrize("coords", [0, 1])
-@pytest.mark.parametrize("deconstruct", [0, 1])
+@pytest.mark.parametrize("deconstruct", [0, 1, 2, 3])
 def test_rebuild_exact_on_dyadic_state(coords, deconstruct):
     """Small integers times powers of two with equal power-of-two masses: every difference,
     path sum and centre-of-mass shift is exact, so the state never changes."""
@@ -151,6 +151,26 @@ def test_rebuild_mst_accumulates_less_error_than_chain_with_root_kept():
     # the paper reads an order of magnitude at 1e5 rebuilds; at 1e3 a factor 3 is asked
     assert np.mean(chn) > 0.3 * golden("mst_claims")["rebuild_chain_over_mst_error"] * np.mean(mst), \
         (np.mean(chn), np.mean(mst))
+
+
+@pytest.mark.parametrize("coords", [0, 1])
+def test_rebuild_from_the_root_outwards_does_not_accumulate(coords):
+    """Deconstruction from the root outwards (w_v = w_parent(v) + X_v, parents first, the root
+    kept) undoes the build up to one rounding per edge, and once a body's parent is unchanged
+    fl(w_p + fl(w_v - w_p)) returns w_v (the subtraction and the addition are then exact in all
+    but rare cases): after the first cycle the state stays where it is. The energy error after
+    1000 cycles therefore equals the one after 10, while the per-vertex path sums (rule 1) grow
+    by about the cycle ratio."""
+    m, r, v, _ = W.hernquist(379, 4)
+    out = O.rebuild_run(m, r, v, coords, 1000, 500, [0, 10, 1000], 2)
+    E = out["E"]
+    assert abs(E[2] / E[0] - 1) <= max(abs(E[1] / E[0] - 1), 1e-16) * 1.5
+    assert abs(E[2] / E[0] - 1) < 2e-15
+    walk = O.rebuild_run(m, r, v, coords, 1000, 500, [0, 10, 1000], 1)["E"]
+    assert abs(walk[2] / walk[0] - 1) > 10 * abs(walk[1] / walk[0] - 1)
+    # the root keeps its position exactly
+    root = O.prim(r)[0] if coords == 0 else O.chain(r)[0]
+    assert np.array_equal(out["r"][root], r[root]) and np.array_equal(out["v"][root], v[root])
 
 
 def test_chain_end_tie_joins_the_tail():
