@@ -78,6 +78,13 @@ typedef struct {
                         MST; a few per cent longer than the MST). Batches always use 0. 0 */
   int mst_nsub;      /* subgraphs of the divide-and-conquer octree, 0 = ceil(sqrt(n)), at most
                         1024. 0 */
+  int pair_tile;     /* bodies per tile of the pair loop: 32, 64 or 128, or 0 for the size rule
+                        (32 up to 4096 bodies, 64 up to 8192, 128 above); mstar_tune_pair_tile
+                        times the choices on a given system. 0 */
+  int pair_split;    /* warps that share the 32 partner steps of a tile pair, with 32-body tiles:
+                        1, 2, 4 or 8, or 0 for the size rule (4 up to 512 bodies, else 1); the
+                        other tiles take 1. Partial sums are added in warp order, so results
+                        differ from the unsplit loop by rounding only. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */
@@ -147,6 +154,18 @@ MSTAR_API int mstar_get_mst(mstar_ctx* ctx, int* root, int* parent, int* level, 
 /* One pair-loop evaluation on the current state (Eq. 2 with the near/far separation rule
    of Sec. 3.4 on the current MST): accelerations a[n x 3] and force function U. */
 MSTAR_API int mstar_accelerations(mstar_ctx* ctx, double* a, double* U);
+
+/* Tuner with no counterpart in the paper: for the system (n, m, r, v) under p, creates a
+   context for each of four pair loops - 32-body tiles with the partner steps split over 4
+   warps, and unsplit tiles of 32, 64 and 128 bodies - (allocating and freeing its
+   workspace), times `repeats` GBS step attempts of each with CUDA events on cuda_stream after
+   one untimed attempt, and returns the fastest as *tile_out and *split_out, with the mean
+   attempt time of each in ms_out[4] (in that order; may be NULL). The attempts change no
+   state; the caller sets p.pair_tile and p.pair_split to the result for its own context. An
+   attempt's work does not depend on its fictitious step, which is set to 1e-6 U. Errors as
+   mstar_init. */
+MSTAR_API int mstar_tune_pair_tile(int n, const double* m, const double* r, const double* v, const mstar_params* p,
+                                   int repeats, int* tile_out, int* split_out, double* ms_out, void* cuda_stream);
 
 MSTAR_API void mstar_free(mstar_ctx* ctx);
 MSTAR_API const char* mstar_strerror(int code);
@@ -298,7 +317,8 @@ typedef struct mstar_adjoint mstar_adjoint;
    attempt accepted: no error test, no step-size control or end-time clamp) from the state
    that mstar_init set up; the context must not have been stepped or given a new state
    since (INVALID_ARG otherwise). Keeps (r, v) of every `checkpoint_every`-th step start in
-   device memory owned by *out (NOMEM if it cannot be allocated). The context ends at the
+   device memory owned by *out (NOMEM if it cannot be allocated), and the trajectories of
+   the last segment's steps, which the reverse sweep needs first. The context ends at the
    final state. Errors as mstar_step; on error *out is NULL. */
 MSTAR_API int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int checkpoint_every, mstar_adjoint** out);
 
@@ -307,8 +327,9 @@ MSTAR_API int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int chec
    g_E = dL/dE_f (E_f = T - U of the final state, Eq. 1). Writes dL/dm (n), dL/dr, dL/dv
    (n x 3) with respect to the masses, positions and velocities given to mstar_init,
    through the centre-of-mass shift and B = U0 - T0 (any output may be NULL). Each segment
-   of checkpoint_every steps is recomputed from its checkpoint with its trajectory
-   recorded; the transposed substeps then run in reverse, one VJP pair loop per kick. The
+   of checkpoint_every steps whose trajectories are not already held (the last one, after
+   the forward) is recomputed from its checkpoint with its trajectory recorded; the
+   transposed substeps then run in reverse, one VJP pair loop per kick. The
    MST of each step is held fixed (its topology is piecewise constant). The context ends at
    the final state of the run. May be called again with other loss gradients. */
 MSTAR_API int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g_r, const double* g_v, double g_E,
@@ -328,12 +349,14 @@ MSTAR_API void mstar_adjoint_free(mstar_adjoint* a);
    coords[job]: 0 the MST (Prim, Sec. 3.2; root closest to the centre of mass), 1 the chain
    of Sec. 2.2 (shortest pair first, then the particle closest to either end, the tail on a
    tie), as a path tree rooted at its tail. Building: X_v = w_v - w_parent(v). Deconstruction:
-   per-vertex sums of the edge vectors from the vertex up to the root, then
-   deconstruct[job] 0: the centre-of-mass shift (the integrator's rebuild) or 1: plus the
-   root's kept position. The topology is rebuilt every topo_every cycles; topo_changes[job]
-   counts rebuilds that changed it and mean_level[job] is the mean level <L> of the trees
-   built. m (njobs x n), r and v (njobs x n x 3), outputs: host or device; r_out, v_out,
-   topo_changes, mean_level may be NULL. The operations and their order are those of the CPU
+   deconstruct[job] 0: per-vertex sums of the edge vectors from the vertex up to the root,
+   then the centre-of-mass shift (the integrator's rebuild); 1: the same sums plus the root's
+   kept position; 2: from the root outwards, w_v = w_parent(v) + X_v with every parent before
+   its children, from the root's kept position; 3: as 2, then the centre-of-mass shift.
+   The topology is rebuilt every topo_every cycles; topo_changes[job] counts rebuilds that
+   changed it and mean_level[job] is the mean level <L> of the trees built. m (njobs x n),
+   r and v (njobs x n x 3), outputs: host or device; r_out, v_out, topo_changes, mean_level
+   may be NULL. The operations and their order are those of the CPU
    definition, so the results are bit-identical to it. Allocates and frees device scratch;
    synchronises the stream. Errors: INVALID_ARG (n outside [2, MSTAR_REBUILD_MAX_N], other
    bad arguments), NOMEM, CUDA. */

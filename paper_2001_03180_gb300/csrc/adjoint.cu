@@ -209,8 +209,219 @@ k_adj_pair(int n, int npad, int slot_lo, double G, double H, const double* __res
   }
 }
 
+// The same VJP sums over every unordered pair once, in the tiling of the forward pair loop:
+// CTA (I, J), I <= J, holds tile I's bodies in registers and stages tile J's positions,
+// masses, adjoints and accumulators in shared memory; at step k of a 32-wide sub-tile lane l
+// pairs with partner (l + k) mod 32, so the lanes update distinct partner accumulators. For
+// d = r_j - r_i and w = m_i L_j - m_j L_i the pair gives
+//   u = w / r^3 - 3 d (d . w) / r^5:   mu_i += u, mu_j -= u   (M_ij = M_ji, w_ji = -w_ij)
+//   nu_i -= (L_j . d) / r^3,  nu_j += (L_i . d) / r^3,  phi_i += m_j / r,  phi_j += m_i / r,
+// about half the FP64 work of visiting each ordered pair. CTA (I, J) writes tile I's sums to
+// partial slot J and tile J's to slot I (a diagonal CTA writes both into slot I), so each
+// body receives one write per slot; the consumer adds the NT slots in order.
+template <int W>
+__global__ void __launch_bounds__(32 * W)
+k_adj_pair_sym(int n, int npad, int NT, int slot_lo, double G, double H, const double* __restrict__ m,
+               const double* __restrict__ Rb, size_t rs, const double* __restrict__ Lb, size_t ls,
+               const double* __restrict__ SC, double* __restrict__ mu, double* __restrict__ nu,
+               double* __restrict__ phi) {
+  constexpr int T = 32 * W;
+  __shared__ double sx[T], sy[T], sz[T], sm[T], slx[T], sly[T], slz[T];
+  __shared__ double smx[T], smy[T], smz[T], snu[T], sph[T];
+  const int s = slot_lo + blockIdx.y;
+  int I, J;
+  tile_pair(blockIdx.x, NT, I, J);
+  const double* R = Rb + s * rs;
+  const double* L = Lb + s * ls;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = J * T;
+  sx[tid] = R[j0 + tid];
+  sy[tid] = R[npad + j0 + tid];
+  sz[tid] = R[2 * (size_t)npad + j0 + tid];
+  sm[tid] = m[j0 + tid];
+  slx[tid] = L[j0 + tid];
+  sly[tid] = L[npad + j0 + tid];
+  slz[tid] = L[2 * (size_t)npad + j0 + tid];
+  smx[tid] = 0.0;
+  smy[tid] = 0.0;
+  smz[tid] = 0.0;
+  snu[tid] = 0.0;
+  sph[tid] = 0.0;
+  const int i = I * T + tid;
+  const double xi = R[i], yi = R[npad + i], zi = R[2 * (size_t)npad + i];
+  const double mi = m[i];
+  const double lxi = L[i], lyi = L[npad + i], lzi = L[2 * (size_t)npad + i];
+  const bool i_pad = i >= n;
+  const bool diag = (I == J);
+  double mux = 0.0, muy = 0.0, muz = 0.0, nui = 0.0, phi_i = 0.0;
+  __syncthreads();
+#pragma unroll 1
+  for (int sb = 0; sb < W; ++sb) {
+    const int sub = (warp + sb) & (W - 1);
+    const bool self = diag && sub == warp;
+    if (!(diag && sub < warp)) {
+      const int kbeg = self ? 1 : 0;
+      const int kend = self ? 17 : 32;
+#pragma unroll 2
+      for (int k = kbeg; k < kend; ++k) {
+        const int jl = sub * 32 + ((lane + k) & 31);
+        const bool masked = i_pad | (j0 + jl >= n) | (self & (k == 16) & (lane >= 16));
+        const double dx = sx[jl] - xi, dy = sy[jl] - yi, dz = sz[jl] - zi;
+        const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+        double ri = rsqrt_fp64(r2);
+        // masked pairs contribute nothing (an integer select on the bit pattern)
+        ri = __longlong_as_double(masked ? 0ll : __double_as_longlong(ri));
+        const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2;
+        const double mj = sm[jl], ljx = slx[jl], ljy = sly[jl], ljz = slz[jl];
+        const double wx = fma(mi, ljx, -mj * lxi), wy = fma(mi, ljy, -mj * lyi), wz = fma(mi, ljz, -mj * lzi);
+        const double t = 3.0 * fma(dz, wz, fma(dy, wy, dx * wx)) * ri5;
+        const double ux = fma(wx, ri3, -t * dx), uy = fma(wy, ri3, -t * dy), uz = fma(wz, ri3, -t * dz);
+        mux += ux;
+        muy += uy;
+        muz += uz;
+        smx[jl] -= ux;
+        smy[jl] -= uy;
+        smz[jl] -= uz;
+        nui = fma(-fma(ljz, dz, fma(ljy, dy, ljx * dx)), ri3, nui);
+        snu[jl] = fma(fma(lzi, dz, fma(lyi, dy, lxi * dx)), ri3, snu[jl]);
+        phi_i = fma(mj, ri, phi_i);
+        sph[jl] = fma(mi, ri, sph[jl]);
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  const double gg = G * (H / (double)(2 * (s + 1))) / SC[s * kScal + SC_U];
+  const size_t st = (size_t)3 * npad;
+  auto put = [&](int slot_of, int body, double ax_, double ay_, double az_, double n_, double p_) {
+    const size_t zo = (size_t)s * NT + slot_of;
+    double* muo = mu + zo * st;
+    muo[body] = gg * ax_;
+    muo[npad + body] = gg * ay_;
+    muo[2 * (size_t)npad + body] = gg * az_;
+    nu[zo * npad + body] = gg * n_;
+    phi[zo * npad + body] = G * p_;
+  };
+  if (diag) {
+    put(I, i, mux + smx[tid], muy + smy[tid], muz + smz[tid], nui + snu[tid], phi_i + sph[tid]);
+  } else {
+    put(J, i, mux, muy, muz, nui, phi_i);
+    put(I, j0 + tid, smx[tid], smy[tid], smz[tid], snu[tid], sph[tid]);
+  }
+}
+
+// k_adj_pair_sym with 32-body tiles and a tile pair's 32 partner steps split over S warps (S
+// divides 16), as in the forward pair loop of small systems: each warp keeps its own i-side
+// sums and its own copy of the partner sums, added in warp order at the end.
+template <int S>
+__global__ void __launch_bounds__(32 * S)
+k_adj_pair_sym_ks(int n, int npad, int NT, int slot_lo, double G, double H, const double* __restrict__ m,
+                  const double* __restrict__ Rb, size_t rs, const double* __restrict__ Lb, size_t ls,
+                  const double* __restrict__ SC, double* __restrict__ mu, double* __restrict__ nu,
+                  double* __restrict__ phi) {
+  constexpr int T = 32;
+  __shared__ double sx[T], sy[T], sz[T], sm[T], slx[T], sly[T], slz[T];
+  __shared__ double smx[S][T], smy[S][T], smz[S][T], snu[S][T], sph[S][T];  // partner sums per warp
+  __shared__ double rmx[S][T], rmy[S][T], rmz[S][T], rnu[S][T], rph[S][T];  // i-side sums per warp
+  const int s = slot_lo + blockIdx.y;
+  int I, J;
+  tile_pair(blockIdx.x, NT, I, J);
+  const double* R = Rb + s * rs;
+  const double* L = Lb + s * ls;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = J * T;
+  if (warp == 0) {
+    sx[lane] = R[j0 + lane];
+    sy[lane] = R[npad + j0 + lane];
+    sz[lane] = R[2 * (size_t)npad + j0 + lane];
+    sm[lane] = m[j0 + lane];
+    slx[lane] = L[j0 + lane];
+    sly[lane] = L[npad + j0 + lane];
+    slz[lane] = L[2 * (size_t)npad + j0 + lane];
+  }
+  smx[warp][lane] = 0.0;
+  smy[warp][lane] = 0.0;
+  smz[warp][lane] = 0.0;
+  snu[warp][lane] = 0.0;
+  sph[warp][lane] = 0.0;
+  const int i = I * T + lane;
+  const double xi = R[i], yi = R[npad + i], zi = R[2 * (size_t)npad + i];
+  const double mi = m[i];
+  const double lxi = L[i], lyi = L[npad + i], lzi = L[2 * (size_t)npad + i];
+  const bool i_pad = i >= n;
+  const bool diag = (I == J);
+  const int kbeg = diag ? 1 + 16 * warp / S : 32 * warp / S;
+  const int kend = diag ? 1 + 16 * (warp + 1) / S : 32 * (warp + 1) / S;
+  double mux = 0.0, muy = 0.0, muz = 0.0, nui = 0.0, phi_i = 0.0;
+  __syncthreads();
+#pragma unroll 2
+  for (int k = kbeg; k < kend; ++k) {
+    const int jl = (lane + k) & 31;
+    const bool masked = i_pad | (j0 + jl >= n) | (diag & (k == 16) & (lane >= 16));
+    const double dx = sx[jl] - xi, dy = sy[jl] - yi, dz = sz[jl] - zi;
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    double ri = rsqrt_fp64(r2);
+    ri = __longlong_as_double(masked ? 0ll : __double_as_longlong(ri));
+    const double ri2 = ri * ri, ri3 = ri2 * ri, ri5 = ri3 * ri2;
+    const double mj = sm[jl], ljx = slx[jl], ljy = sly[jl], ljz = slz[jl];
+    const double wx = fma(mi, ljx, -mj * lxi), wy = fma(mi, ljy, -mj * lyi), wz = fma(mi, ljz, -mj * lzi);
+    const double t = 3.0 * fma(dz, wz, fma(dy, wy, dx * wx)) * ri5;
+    const double ux = fma(wx, ri3, -t * dx), uy = fma(wy, ri3, -t * dy), uz = fma(wz, ri3, -t * dz);
+    mux += ux;
+    muy += uy;
+    muz += uz;
+    smx[warp][jl] -= ux;
+    smy[warp][jl] -= uy;
+    smz[warp][jl] -= uz;
+    nui = fma(-fma(ljz, dz, fma(ljy, dy, ljx * dx)), ri3, nui);
+    snu[warp][jl] = fma(fma(lzi, dz, fma(lyi, dy, lxi * dx)), ri3, snu[warp][jl]);
+    phi_i = fma(mj, ri, phi_i);
+    sph[warp][jl] = fma(mi, ri, sph[warp][jl]);
+    __syncwarp();
+  }
+  rmx[warp][lane] = mux;
+  rmy[warp][lane] = muy;
+  rmz[warp][lane] = muz;
+  rnu[warp][lane] = nui;
+  rph[warp][lane] = phi_i;
+  __syncthreads();
+  if (warp != 0) return;
+  double ax = rmx[0][lane], ay = rmy[0][lane], az = rmz[0][lane], an = rnu[0][lane], ap = rph[0][lane];
+  double bx = smx[0][lane], by = smy[0][lane], bz = smz[0][lane], bn = snu[0][lane], bp = sph[0][lane];
+#pragma unroll
+  for (int w = 1; w < S; ++w) {
+    ax += rmx[w][lane];
+    ay += rmy[w][lane];
+    az += rmz[w][lane];
+    an += rnu[w][lane];
+    ap += rph[w][lane];
+    bx += smx[w][lane];
+    by += smy[w][lane];
+    bz += smz[w][lane];
+    bn += snu[w][lane];
+    bp += sph[w][lane];
+  }
+  const double gg = G * (H / (double)(2 * (s + 1))) / SC[s * kScal + SC_U];
+  const size_t st = (size_t)3 * npad;
+  auto put = [&](int slot_of, int body, double ax_, double ay_, double az_, double n_, double p_) {
+    const size_t zo = (size_t)s * NT + slot_of;
+    double* muo = mu + zo * st;
+    muo[body] = gg * ax_;
+    muo[npad + body] = gg * ay_;
+    muo[2 * (size_t)npad + body] = gg * az_;
+    nu[zo * npad + body] = gg * n_;
+    phi[zo * npad + body] = G * p_;
+  };
+  if (diag) {
+    put(I, i, ax + bx, ay + by, az + bz, an + bn, ap + bp);
+  } else {
+    put(J, i, ax, ay, az, an, ap);
+    put(I, j0 + lane, bx, by, bz, bn, bp);
+  }
+}
+
 // Transposed kick of level tau: lU from the lv . a partials, then lr += mu + lU m a and
-// lm += nu + lU phi (mu, nu, phi summed over the nz partner ranges in order).
+// lm += nu + lU phi (mu, nu, phi summed over their nz partial slots in order).
 __global__ void __launch_bounds__(kBlock)
 k_adj_kick(int n, int npad, int slot_lo, double H, const double* __restrict__ m, const double* __restrict__ A,
            const double* __restrict__ SC, const double* __restrict__ pg, int nblk, const double* __restrict__ mu,
@@ -354,6 +565,7 @@ struct mstar_adjoint {
   double* fin = nullptr;             // final (r planes, v planes)
   double t_final = 0.0;
   std::vector<AdjTraj> tr;           // one per step of a segment
+  int tr_seg = -1;                   // the segment whose trajectories tr holds (-1: none)
   double *lr = nullptr, *lv = nullptr, *lrf = nullptr, *lvf = nullptr, *lm = nullptr, *lB = nullptr;
   double *mu = nullptr, *nu = nullptr, *phi = nullptr, *aout = nullptr, *pf = nullptr, *pg = nullptr;
   double *lmt = nullptr, *pc = nullptr, *outr = nullptr, *outv = nullptr, *outm = nullptr;
@@ -400,9 +612,11 @@ size_t adj_carve(mstar_adjoint* a, void* base) {
   a->lvf = cv.take(st);
   a->lm = cv.take(K * np);
   a->lB = cv.take(K);
-  a->mu = cv.take(K * a->nz * st);
-  a->nu = cv.take(K * a->nz * np);
-  a->phi = cv.take(K * a->nz * np);
+  // partials of the VJP pair loops: nz partner ranges (the state's a and phi) or NT tile slots
+  const size_t nzp = (size_t)(a->nz > c->NT ? a->nz : c->NT);
+  a->mu = cv.take(K * nzp * st);
+  a->nu = cv.take(K * nzp * np);
+  a->phi = cv.take(K * nzp * np);
   a->aout = cv.take((size_t)a->nz * st);
   a->pf = cv.take(K * nb);
   a->pg = cv.take(K * nb);
@@ -476,11 +690,36 @@ int backward_step(mstar_ctx* c, mstar_adjoint* a, const AdjTraj& t) {
                                                   nb, a->lm, a->lB, A, a->pg);
     c->launches += 2;
     if (tau > 0) {
-      const dim3 grid((n + kAdjI - 1) / kAdjI, nsl, a->nz);
-      k_adj_pair<<<grid, kAdjI, 0, s>>>(n, np, lo, c->p.G, a->H, c->d.m, t.R + (tau - 1) * lvl, st, a->lv, st, SC,
-                                         a->nz, a->jchunk, a->mu, a->nu, a->phi, nullptr);
+      const dim3 grid(c->ntp, nsl);
+      const double* R = t.R + (tau - 1) * lvl;
+      switch (c->W == 1 ? (c->S > 1 ? -c->S : 1) : c->W) {
+        case -2:
+          k_adj_pair_sym_ks<2><<<grid, 64, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC,
+                                                   a->mu, a->nu, a->phi);
+          break;
+        case -4:
+          k_adj_pair_sym_ks<4><<<grid, 128, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC,
+                                                    a->mu, a->nu, a->phi);
+          break;
+        case -8:
+          k_adj_pair_sym_ks<8><<<grid, 256, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC,
+                                                    a->mu, a->nu, a->phi);
+          break;
+        case 1:
+          k_adj_pair_sym<1><<<grid, 32, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC, a->mu,
+                                                a->nu, a->phi);
+          break;
+        case 2:
+          k_adj_pair_sym<2><<<grid, 64, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC, a->mu,
+                                                a->nu, a->phi);
+          break;
+        default:
+          k_adj_pair_sym<4><<<grid, 128, 0, s>>>(n, np, c->NT, lo, c->p.G, a->H, c->d.m, R, st, a->lv, st, SC,
+                                                 a->mu, a->nu, a->phi);
+          break;
+      }
       k_adj_kick<<<dim3(nb, nsl), kBlock, 0, s>>>(n, np, lo, a->H, c->d.m, A, SC, a->pg, nb, a->mu, a->nu, a->phi,
-                                                   a->nz, a->lr, a->lm);
+                                                   c->NT, a->lr, a->lm);
       c->launches += 2;
     }
   }
@@ -575,13 +814,21 @@ int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int checkpoint_eve
   adj_carve(a, a->mem);
   int rc = cudaMemsetAsync(a->mem, 0, bytes, c->stream) == cudaSuccess ? MSTAR_OK : MSTAR_ERR_CUDA;
   const size_t st = (size_t)3 * c->npad;
+  // the steps of the last segment record their trajectories on the way, so that the reverse
+  // sweep starts without recomputing that segment
+  const int last_first = (a->nck - 1) * a->every;
   for (int i = 0; i < nsteps && !rc; ++i) {
     if (i % a->every == 0) {
       a->tck[i / a->every] = c->t;
       rc = save_planes(c, a->ck + (size_t)(i / a->every) * 2 * st);
     }
-    if (!rc) rc = fixed_step(c, H);
+    if (!rc) {
+      c->traj = i >= last_first ? &a->tr[i - last_first] : nullptr;
+      rc = fixed_step(c, H);
+      c->traj = nullptr;
+    }
   }
+  if (!rc) a->tr_seg = a->nck - 1;
   if (!rc) rc = save_planes(c, a->fin);
   a->t_final = c->t;
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = MSTAR_ERR_CUDA;
@@ -617,11 +864,15 @@ int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g_r, const 
   for (int seg = a->nck - 1; seg >= 0 && !rc; --seg) {
     const int first = seg * a->every;
     const int cnt = (a->nsteps - first) < a->every ? (a->nsteps - first) : a->every;
-    rc = set_planes(c, a->ck + (size_t)seg * 2 * st, a->tck[seg]);
-    for (int q = 0; q < cnt && !rc; ++q) {
-      c->traj = &a->tr[q];
-      rc = fixed_step(c, a->H);
-      c->traj = nullptr;
+    if (a->tr_seg != seg) {  // recompute the segment from its checkpoint, recording it
+      a->tr_seg = -1;
+      rc = set_planes(c, a->ck + (size_t)seg * 2 * st, a->tck[seg]);
+      for (int q = 0; q < cnt && !rc; ++q) {
+        c->traj = &a->tr[q];
+        rc = fixed_step(c, a->H);
+        c->traj = nullptr;
+      }
+      if (!rc) a->tr_seg = seg;
     }
     for (int q = cnt - 1; q >= 0 && !rc; --q) rc = bw_step(c, a, q);
   }

@@ -49,7 +49,7 @@ struct Shape {
 Shape shape_of(int n, const mstar_params& p) {
   Shape s{};
   s.n = n;
-  s.W = choose_tile_warps(n);
+  s.W = p.pair_tile ? p.pair_tile / 32 : choose_tile_warps(n);
   s.T = 32 * s.W;
   s.npad = (n + s.T - 1) / s.T * s.T;
   s.K = p.k_fix;
@@ -114,6 +114,9 @@ bool valid_params(const mstar_params* p) {
   if (p->n_d < 0 || p->n_d > 2) return false;
   if (p->max_halvings < 0 || p->max_time_iter < 0) return false;
   if (p->mst_method < 0 || p->mst_method > 1 || p->mst_nsub < 0 || p->mst_nsub > kDcMaxSub) return false;
+  if (p->pair_tile != 0 && p->pair_tile != 32 && p->pair_tile != 64 && p->pair_tile != 128) return false;
+  if (p->pair_split != 0 && p->pair_split != 1 && p->pair_split != 2 && p->pair_split != 4 && p->pair_split != 8)
+    return false;
   return true;
 }
 
@@ -441,6 +444,8 @@ void mstar_default_params(mstar_params* p) {
   p->max_time_iter = 8;
   p->mst_method = 0;
   p->mst_nsub = 0;
+  p->pair_tile = 0;
+  p->pair_split = 0;
 }
 
 size_t mstar_workspace_bytes(int n, const mstar_params* p) {
@@ -507,6 +512,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   c->T = s.T;
   c->NT = s.NT;
   c->ntp = s.NT * (s.NT + 1) / 2;
+  c->S = s.W != 1 ? 1 : (p->pair_split ? p->pair_split : (n <= 512 ? 4 : 1));
   c->nblk = s.nblk;
   const size_t need = carve(s, nullptr, nullptr, nullptr);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -540,7 +546,8 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
     mstar_free(c);
     return code;
   };
-  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess)
+  if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
+      prepare_rebuild(c) != cudaSuccess)
     return bail(MSTAR_ERR_CUDA);
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.parent, c->npad, -1);
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.gp, c->npad, -1);
@@ -684,6 +691,57 @@ int mstar_attempt(mstar_ctx* c, double H, double* eps, double* r_out, double* v_
     if ((rc = extract_out(c, r_out, v_out, c->d.Tkk, c->d.Tkk + n3))) return rc;
   }
   return MSTAR_OK;
+}
+
+int mstar_tune_pair_tile(int n, const double* m, const double* r, const double* v, const mstar_params* p,
+                         int repeats, int* tile_out, int* split_out, double* ms_out, void* cuda_stream) {
+  if (!tile_out || !split_out || repeats < 1) return MSTAR_ERR_INVALID_ARG;
+  mstar_params q;
+  if (p) q = *p;
+  else mstar_default_params(&q);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return MSTAR_ERR_CUDA;
+  }
+  const int tiles[4] = {32, 32, 64, 128}, splits[4] = {4, 1, 1, 1};
+  double best = 0.0;
+  int best_k = -1, rc = MSTAR_OK;
+  for (int k = 0; k < 4 && !rc; ++k) {
+    q.pair_tile = tiles[k];
+    q.pair_split = splits[k];
+    mstar_ctx* c = nullptr;
+    rc = mstar_init(&c, n, m, r, v, &q, nullptr, 0, cuda_stream);
+    if (rc) break;
+    double U0, T0, e, tn;
+    rc = prepare_step(c, &U0, &T0);
+    const double H = 1e-6 * U0;
+    if (!rc) rc = run_attempt(c, H, &e, &tn);  // untimed: captures the attempt's graph
+    float ms = 0.0f;
+    if (!rc) {
+      cudaEventRecord(e0, c->stream);
+      for (int i = 0; i < repeats && !rc; ++i) rc = run_attempt(c, H, &e, &tn);
+      cudaEventRecord(e1, c->stream);
+      if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = MSTAR_ERR_CUDA;
+    }
+    mstar_free(c);
+    if (rc) break;
+    const double per = (double)ms / repeats;
+    if (ms_out) ms_out[k] = per;
+    if (best_k < 0 || per < best) {
+      best = per;
+      best_k = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!rc) {
+    *tile_out = tiles[best_k];
+    *split_out = splits[best_k];
+  }
+  return rc;
 }
 
 int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) {

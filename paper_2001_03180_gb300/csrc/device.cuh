@@ -31,6 +31,19 @@ __device__ __forceinline__ double double_of_nonneg_float(float f) {
   return e > 0 ? __hiloint2double(hi, (int)lo) : 0.0;
 }
 
+// Upper-triangle tile pair tp -> (I, J), I <= J < NT, rows of length NT - I (the tiled pair
+// loops: forces and their vector-Jacobian products).
+__device__ __forceinline__ void tile_pair(int tp, int NT, int& I, int& J) {
+  float b = (float)NT + 0.5f;
+  int i = (int)floorf(b - sqrtf(fmaxf(b * b - 2.0f * (float)tp, 0.0f)));
+  i = max(0, min(i, NT - 1));
+  auto start = [NT](int r) { return r * NT - (r * (r - 1)) / 2; };
+  while (i > 0 && start(i) > tp) --i;
+  while (i + 1 < NT && start(i + 1) <= tp) ++i;
+  I = i;
+  J = i + (tp - start(i));
+}
+
 // 1/sqrt(x) to double precision for a normal x > 0, with four FP64 instructions.
 //
 // Seed: x = 2^(2k) * mx with mx in [1, 4) assembled as a float from x's bits; CUDA's

@@ -10,9 +10,12 @@
 
 namespace mstar {
 
-constexpr int kBlock = 256;       // threads of the O(N) kernels
+constexpr int kBlock = 64;        // threads of the O(N) kernels (more CTAs per slot: their FP64 work spreads over more SMs)
 constexpr int kMaxKfix = 12;      // divisions supported (n_k = 2k <= 24)
 constexpr int kScal = 8;          // per-slot device scalars
+// Largest shared-memory staging of the rebuild walk: a slot's edge vectors and the parents,
+// 28 bytes per body (npad up to 7168).
+constexpr size_t kRebuildStageBytes = 200 * 1024;
 
 // Per-slot device scalars (sc[slot * kScal + i]).
 enum { SC_T_PHYS = 0, SC_T_KIN = 1, SC_U = 2 };
@@ -77,7 +80,9 @@ struct AdjTraj {
 struct mstar_ctx {
   int n = 0, npad = 0, K = 0, nslots = 0;
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
+  int S = 1;                          // warps sharing a tile pair's partner steps (32-body tiles)
   int pair_defer = -1;  // trailing slots of a pair launch summed by the finishing pass (-1: unset)
+  size_t rebuild_smem = 0;  // shared memory of the staged rebuild (0: the plain kernel is used)
   int nblk = 0;
   mstar_params p{};
   cudaStream_t stream = nullptr;
@@ -150,6 +155,7 @@ cudaError_t launch_kick(mstar_ctx* c, int slot_lo, int slot_hi);
 cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, int tau);
 cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stride, int nsl,
                            int want_T, double* Tblk_base, double* comblk_base);
+cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged rebuild's shared memory
 cudaError_t launch_extrapolate(mstar_ctx* c);
 cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom
 // w (3 planes of the state) -= centre of mass; optionally T partials into Tblk slot 0

@@ -41,63 +41,54 @@
 namespace mstar {
 namespace {
 
-// Upper-triangle tile pair tp -> (I, J), rows of length NT - I.
-__device__ __forceinline__ void tile_pair(int tp, int NT, int& I, int& J) {
-  float b = (float)NT + 0.5f;
-  int i = (int)floorf(b - sqrtf(fmaxf(b * b - 2.0f * (float)tp, 0.0f)));
-  i = max(0, min(i, NT - 1));
-  auto start = [NT](int r) { return r * NT - (r * (r - 1)) / 2; };
-  while (i > 0 && start(i) > tp) --i;
-  while (i + 1 < NT && start(i + 1) <= tp) ++i;
-  I = i;
-  J = i + (tp - start(i));
-}
-
-// Sum of tile t's NT partial slots (ascending s) for its T bodies, one per thread, into
-// Pt (4 planes); then its count is reset and the partials' lines dropped from L2.
-template <int T>
+// Sum of tile t's NT partial slots (ascending s) for its T bodies, one per thread of the
+// first T of the CTA's NTH threads, into Pt (4 planes); then its count is reset and the
+// partials' lines dropped from L2. Every thread of the CTA calls it (it holds a barrier).
+template <int T, int NTH = T>
 __device__ __forceinline__ void finish_tile(int t, int npad, int NT, const double* Ps, double* Pt, int* cnt) {
   const int tid = threadIdx.x;
-  const double* q = Ps + (size_t)t * T + tid;
-  double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
-  // L2 loads (the slots were written by other CTAs after this SM's L1 could have seen
-  // them), four slots at a time ahead of their additions, which keep the ascending order
-  int s = 0;
-  for (; s + 4 <= NT; s += 4) {
-    double b[4][4];
+  if (NTH == T || tid < T) {
+    const double* q = Ps + (size_t)t * T + tid;
+    double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
+    // L2 loads (the slots were written by other CTAs after this SM's L1 could have seen
+    // them), four slots at a time ahead of their additions, which keep the ascending order
+    int s = 0;
+    for (; s + 4 <= NT; s += 4) {
+      double b[4][4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const double* qs = q + (size_t)(s + k) * 4 * npad;
-      b[k][0] = __ldcg(qs);
-      b[k][1] = __ldcg(qs + npad);
-      b[k][2] = __ldcg(qs + 2 * (size_t)npad);
-      b[k][3] = __ldcg(qs + 3 * (size_t)npad);
-    }
+      for (int k = 0; k < 4; ++k) {
+        const double* qs = q + (size_t)(s + k) * 4 * npad;
+        b[k][0] = __ldcg(qs);
+        b[k][1] = __ldcg(qs + npad);
+        b[k][2] = __ldcg(qs + 2 * (size_t)npad);
+        b[k][3] = __ldcg(qs + 3 * (size_t)npad);
+      }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      ax += b[k][0];
-      ay += b[k][1];
-      az += b[k][2];
-      u += b[k][3];
+      for (int k = 0; k < 4; ++k) {
+        ax += b[k][0];
+        ay += b[k][1];
+        az += b[k][2];
+        u += b[k][3];
+      }
     }
+    for (; s < NT; ++s) {
+      const double* qs = q + (size_t)s * 4 * npad;
+      ax += __ldcg(qs);
+      ay += __ldcg(qs + npad);
+      az += __ldcg(qs + 2 * (size_t)npad);
+      u += __ldcg(qs + 3 * (size_t)npad);
+    }
+    double* o = Pt + (size_t)t * T + tid;
+    o[0] = ax;
+    o[(size_t)npad] = ay;
+    o[2 * (size_t)npad] = az;
+    o[3 * (size_t)npad] = u;
   }
-  for (; s < NT; ++s) {
-    const double* qs = q + (size_t)s * 4 * npad;
-    ax += __ldcg(qs);
-    ay += __ldcg(qs + npad);
-    az += __ldcg(qs + 2 * (size_t)npad);
-    u += __ldcg(qs + 3 * (size_t)npad);
-  }
-  double* o = Pt + (size_t)t * T + tid;
-  o[0] = ax;
-  o[(size_t)npad] = ay;
-  o[2 * (size_t)npad] = az;
-  o[3 * (size_t)npad] = u;
   __syncthreads();  // every thread has read the tile's slots
   // the slots of tile t: NT x 4 runs of T doubles, each starting on a 256-byte boundary
   // (npad and t T are multiples of T >= 32); T / 16 lines of 128 bytes per run
   constexpr int kLinesPerRun = T / 16;
-  for (int l = tid; l < NT * 4 * kLinesPerRun; l += T) {
+  for (int l = tid; l < NT * 4 * kLinesPerRun; l += NTH) {
     const int run = l / kLinesPerRun, line = l - run * kLinesPerRun;
     const double* a = Ps + (size_t)run * npad + (size_t)t * T + 16 * line;
     asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
@@ -238,6 +229,147 @@ k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __rest
   }
 }
 
+// The pair loop of small systems: the tiling and per-pair arithmetic of k_pair_tiles<1>
+// (32-body tiles), with the 32 partner steps of a tile pair split over S warps (S divides
+// 16). Warp w takes steps [32 w / S, 32 (w + 1) / S) of an off-diagonal pair and
+// [1 + 16 w / S, 1 + 16 (w + 1) / S) of a diagonal one, keeping its own i-side sums and its
+// own copy of the partner sums; the S copies are added in warp order at the end. At N ~ 10^2
+// a tile pair's 32 dependent steps in one warp bind the launch; S warps shorten them S-fold.
+template <int S>
+__global__ void __launch_bounds__(32 * S)
+k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __restrict__ m,
+                const int* __restrict__ parent, const int* __restrict__ gp, const double* __restrict__ sr,
+                double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from) {
+  constexpr int T = 32;
+  __shared__ double sx[T], sy[T], sz[T];
+  __shared__ double sax[S][T], say[S][T], saz[S][T];     // partner sums, one copy per warp
+  __shared__ double rax[S][T], ray[S][T], raz[S][T], rau[S][T];  // i-side sums per warp
+  __shared__ unsigned long long smm[T];
+  __shared__ int sp[T], sg[T], sme[T];
+  const int slot = slot_lo + blockIdx.y;
+  int I, J;
+  tile_pair(blockIdx.x, NT, I, J);
+  const double* rx = sr + (size_t)slot * 3 * npad;
+  const double* ry = rx + npad;
+  const double* rz = ry + npad;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int j0 = J * T;
+  if (warp == 0) {
+    sx[lane] = rx[j0 + lane];
+    sy[lane] = ry[j0 + lane];
+    sz[lane] = rz[j0 + lane];
+    const MassSplit ms = mass_split(m[j0 + lane]);
+    smm[lane] = ms.m;
+    sme[lane] = ms.e;
+    sp[lane] = parent[j0 + lane];
+    sg[lane] = gp[j0 + lane];
+  }
+  sax[warp][lane] = 0.0;
+  say[warp][lane] = 0.0;
+  saz[warp][lane] = 0.0;
+  const int i = I * T + lane;
+  const double xi = rx[i], yi = ry[i], zi = rz[i];
+  const MassSplit msi = mass_split(m[i]);
+  const int pi = parent[i], gpi = gp[i];
+  const bool i_pad = i >= n;
+  const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
+  double axi = 0.0, ayi = 0.0, azi = 0.0;
+  UAcc uacc;
+  bool ubad = false;
+  const bool diag = (I == J);
+  const int kbeg = diag ? 1 + 16 * warp / S : 32 * warp / S;
+  const int kend = diag ? 1 + 16 * (warp + 1) / S : 32 * (warp + 1) / S;
+  __syncthreads();
+#pragma unroll 4
+  for (int k = kbeg; k < kend; ++k) {
+    const int jl = (lane + k) & 31;
+    const int j = j0 + jl;
+    const double xj = sx[jl], yj = sy[jl], zj = sz[jl];
+    const int pj = sp[jl], gj = sg[jl];
+    bool masked = i_pad | (j >= n) | (diag & (k == 16) & (lane >= 16));
+    masked |= nd1 & ((pi == j) | (pj == i));
+    masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
+    double dx = xj - xi, dy = yj - yi, dz = zj - zi;
+    asm volatile("" : "+d"(dx), "+d"(dy), "+d"(dz));
+    unsigned long long Rn;
+    int eR;
+    double sj, si;
+    const unsigned long long mjm = smm[jl];
+    const int mje = sme[jl];
+    pair_scalars_core(dx, dy, dz, MassSplit{mjm, mje}, msi, Rn, eR, sj, si);
+    sj = __longlong_as_double(masked ? 0ll : __double_as_longlong(sj));
+    si = __longlong_as_double(masked ? 0ll : __double_as_longlong(si));
+    ubad |= !masked && Rn == 0ull;
+    uacc.add(masked ? 0ull : __umul64hi(mjm, Rn), masked ? uacc.L : mje + eR + 64);
+    axi = fma(sj, dx, axi);
+    ayi = fma(sj, dy, ayi);
+    azi = fma(sj, dz, azi);
+    sax[warp][jl] = fma(si, dx, sax[warp][jl]);
+    say[warp][jl] = fma(si, dy, say[warp][jl]);
+    saz[warp][jl] = fma(si, dz, saz[warp][jl]);
+    __syncwarp();
+  }
+  rax[warp][lane] = axi;
+  ray[warp][lane] = ayi;
+  raz[warp][lane] = azi;
+  rau[warp][lane] = ubad ? __longlong_as_double(0x7ff8000000000000LL) : uacc.value();
+  __syncthreads();
+  double* Ps = P + (size_t)slot * NT * 4 * npad;
+  if (warp == 0) {
+    double ax = rax[0][lane], ay = ray[0][lane], az = raz[0][lane], u = rau[0][lane];
+    double jx = sax[0][lane], jy = say[0][lane], jz = saz[0][lane];
+#pragma unroll
+    for (int w = 1; w < S; ++w) {
+      ax += rax[w][lane];
+      ay += ray[w][lane];
+      az += raz[w][lane];
+      u += rau[w][lane];
+      jx += sax[w][lane];
+      jy += say[w][lane];
+      jz += saz[w][lane];
+    }
+    if (diag) {
+      double* q = Ps + (size_t)I * 4 * npad + i;
+      q[0] = ax - jx;
+      q[(size_t)npad] = ay - jy;
+      q[2 * (size_t)npad] = az - jz;
+      q[3 * (size_t)npad] = u;
+    } else {
+      double* q = Ps + (size_t)J * 4 * npad + i;
+      q[0] = ax;
+      q[(size_t)npad] = ay;
+      q[2 * (size_t)npad] = az;
+      q[3 * (size_t)npad] = u;
+      double* qj = Ps + (size_t)I * 4 * npad + j0 + lane;
+      qj[0] = -jx;
+      qj[(size_t)npad] = -jy;
+      qj[2 * (size_t)npad] = -jz;
+      qj[3 * (size_t)npad] = 0.0;
+    }
+  }
+  // the on-chip reduction of k_pair_tiles (the first 32 threads sum a tile)
+  if ((int)blockIdx.y >= keep_from) return;
+  __shared__ int s_last[2];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    int* cnt = tcnt + (size_t)slot * NT;
+    s_last[0] = atomicAdd(&cnt[I], 1) == NT - 1;
+    s_last[1] = diag ? 0 : atomicAdd(&cnt[J], 1) == NT - 1;
+    __threadfence();
+  }
+  __syncthreads();
+  if (s_last[0] | s_last[1]) {
+    int* cnt = tcnt + (size_t)slot * NT;
+    double* Pts = Pt + (size_t)slot * 4 * npad;
+    if (s_last[0]) finish_tile<T, 32 * S>(I, npad, NT, Ps, Pts, cnt);
+    if (s_last[1]) {
+      __syncthreads();
+      finish_tile<T, 32 * S>(J, npad, NT, Ps, Pts, cnt);
+    }
+  }
+}
+
 struct NearAcc {
   double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
   // body p, partner q at separation d = r_q - r_p from edge-vector sums
@@ -350,10 +482,10 @@ constexpr double kDeferL2Bytes = 48.0 * 1024 * 1024;
 
 // Trailing slots of a launch left to the finishing pass: the slots whose CTAs can be resident
 // together at the end of the launch (plus one), and at least as many as fit in the L2 budget.
-template <int W>
-int defer_slots(const mstar_ctx* c) {
+template <typename K>
+int defer_slots(const mstar_ctx* c, K kernel, int threads) {
   int per_sm = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_tiles<W>, 32 * W, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
     return 1 << 20;  // unknown: every slot is summed by the finishing pass
@@ -365,12 +497,16 @@ int defer_slots(const mstar_ctx* c) {
   return d_wave > d_l2 ? d_wave : d_l2;
 }
 
-template <int W>
+template <int W, int S>
 cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d, int keep_from) {
   dim3 grid(c->ntp, nsl);
   if (c->prof) prof_begin(c);
-  k_pair_tiles<W><<<grid, 32 * W, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
-                                                  c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
+  if constexpr (S == 1)
+    k_pair_tiles<W><<<grid, 32 * W, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
+                                                    c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
+  else
+    k_pair_tiles_ks<S><<<grid, 32 * S, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
+                                                       c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -383,14 +519,29 @@ cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d, int keep_from
 cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d) {
   const int nsl = slot_hi - slot_lo;
   if (nsl <= 0) return cudaSuccess;
-  if (c->pair_defer < 0)
-    c->pair_defer = c->W == 1 ? defer_slots<1>(c) : (c->W == 2 ? defer_slots<2>(c) : defer_slots<4>(c));
+  if (c->pair_defer < 0) {
+    if (c->W == 1) {
+      switch (c->S) {
+        case 2: c->pair_defer = defer_slots(c, k_pair_tiles_ks<2>, 64); break;
+        case 4: c->pair_defer = defer_slots(c, k_pair_tiles_ks<4>, 128); break;
+        case 8: c->pair_defer = defer_slots(c, k_pair_tiles_ks<8>, 256); break;
+        default: c->pair_defer = defer_slots(c, k_pair_tiles<1>, 32); break;
+      }
+    } else {
+      c->pair_defer = c->W == 2 ? defer_slots(c, k_pair_tiles<2>, 64) : defer_slots(c, k_pair_tiles<4>, 128);
+    }
+  }
   const int keep_from = nsl - c->pair_defer;  // slots below this index are summed on chip
   cudaError_t e;
-  switch (c->W) {
-    case 1: e = run_tiles<1>(c, slot_lo, nsl, n_d, keep_from); break;
-    case 2: e = run_tiles<2>(c, slot_lo, nsl, n_d, keep_from); break;
-    default: e = run_tiles<4>(c, slot_lo, nsl, n_d, keep_from); break;
+  if (c->W == 1) {
+    switch (c->S) {
+      case 2: e = run_tiles<1, 2>(c, slot_lo, nsl, n_d, keep_from); break;
+      case 4: e = run_tiles<1, 4>(c, slot_lo, nsl, n_d, keep_from); break;
+      case 8: e = run_tiles<1, 8>(c, slot_lo, nsl, n_d, keep_from); break;
+      default: e = run_tiles<1, 1>(c, slot_lo, nsl, n_d, keep_from); break;
+    }
+  } else {
+    e = c->W == 2 ? run_tiles<2, 1>(c, slot_lo, nsl, n_d, keep_from) : run_tiles<4, 1>(c, slot_lo, nsl, n_d, keep_from);
   }
   if (e != cudaSuccess) return e;
   dim3 grid(c->nblk, nsl);

@@ -194,6 +194,55 @@ k_rebuild(int n, int npad, size_t stride, const int* __restrict__ parent, const 
   }
 }
 
+// k_rebuild with the slot's edge vectors (3 planes) and the parents staged in shared memory
+// first, for systems whose 28 npad bytes fit: every hop of a root path then costs a
+// shared-memory load instead of an L2 round trip. Each thread issues its 16-byte cp.async
+// copies back to back and waits for its own; the additions and their order are k_rebuild's.
+__global__ void __launch_bounds__(kBlock)
+k_rebuild_staged(int n, int npad, size_t stride, const int* __restrict__ parent, const int* __restrict__ bylev,
+                 const double* __restrict__ Wb, double* __restrict__ wb, const double* __restrict__ m,
+                 double* __restrict__ comblk, int nblk) {
+  extern __shared__ __align__(16) double sW[];  // 3 npad doubles, then npad parents
+  int* sP = reinterpret_cast<int*>(sW + 3 * (size_t)npad);
+  __shared__ double scratch[32];
+  const int slot = blockIdx.y;
+  const double* W = Wb + slot * stride;
+  double* wv = wb + slot * stride;
+  {
+    const char* gW = reinterpret_cast<const char*>(W);
+    const char* gP = reinterpret_cast<const char*>(parent);
+    const unsigned dW = (unsigned)__cvta_generic_to_shared(sW);
+    const unsigned dP = (unsigned)__cvta_generic_to_shared(sP);
+    const int qW = 3 * npad * 8 / 16, qP = npad * 4 / 16;  // npad is a multiple of 32
+    for (int q = threadIdx.x; q < qW; q += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dW + 16 * q), "l"(gW + 16 * (size_t)q)
+                   : "memory");
+    for (int q = threadIdx.x; q < qP; q += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dP + 16 * q), "l"(gP + 16 * (size_t)q)
+                   : "memory");
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+  }
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = i < n ? bylev[i] : n;
+  double s[3] = {0.0, 0.0, 0.0};
+  if (v < n) {
+    for (int u = v; sP[u] >= 0; u = sP[u]) {
+      s[0] = __dadd_rn(s[0], sW[u]);
+      s[1] = __dadd_rn(s[1], sW[npad + u]);
+      s[2] = __dadd_rn(s[2], sW[2 * (size_t)npad + u]);
+    }
+    wv[v] = s[0];
+    wv[(size_t)npad + v] = s[1];
+    wv[2 * (size_t)npad + v] = s[2];
+  }
+  const double mv = v < n ? m[v] : 0.0;
+  for (int c = 0; c < 3; ++c) {
+    const double b = block_sum(__dmul_rn(mv, s[c]), scratch);
+    if (threadIdx.x == 0) comblk[((size_t)slot * nblk + blockIdx.x) * 3 + c] = b;
+  }
+}
+
 // Shift to the centre-of-mass frame: w -= (sum m w) / M; optionally block sums of m w^2.
 __global__ void __launch_bounds__(kBlock)
 k_shift(int n, int npad, size_t stride, double Mtot, double* __restrict__ wb, const double* __restrict__ m,
@@ -400,15 +449,35 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
                            double* Tblk_base, double* comblk_base) {
   if (nsl <= 0) return cudaSuccess;
   dim3 grid(c->nblk, nsl);
-  k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w, c->d.m,
-                                            comblk_base, c->nblk);
+  const size_t staged = (size_t)c->npad * (3 * sizeof(double) + sizeof(int));
+  cudaError_t e;
+  if (staged <= c->rebuild_smem) {
+    k_rebuild_staged<<<grid, kBlock, staged, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w,
+                                                           c->d.m, comblk_base, c->nblk);
+  } else {
+    k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w, c->d.m,
+                                              comblk_base, c->nblk);
+  }
   MSTAR_LAUNCHED(c);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_shift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->Mtot, w, c->d.m, comblk_base,
                                          want_T ? Tblk_base : nullptr, c->nblk);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
+}
+
+// Allows the staged rebuild kernel the shared memory a context of this size needs (at
+// context creation, outside any stream capture); larger systems keep k_rebuild.
+cudaError_t prepare_rebuild(mstar_ctx* c) {
+  const size_t staged = (size_t)c->npad * (3 * sizeof(double) + sizeof(int));
+  c->rebuild_smem = 0;
+  if (staged > kRebuildStageBytes) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_rebuild_staged, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)staged);
+  if (e != cudaSuccess) return e;
+  c->rebuild_smem = staged;
+  return cudaSuccess;
 }
 
 cudaError_t launch_extrapolate(mstar_ctx* c) {

@@ -28,7 +28,7 @@ MSTAR_MAX_N = 10240
 EXPORTS = [
     "mstar_default_params", "mstar_workspace_bytes", "mstar_init", "mstar_step", "mstar_attempt",
     "mstar_energy", "mstar_get_state", "mstar_set_state", "mstar_set_H", "mstar_get_mst",
-    "mstar_accelerations", "mstar_free", "mstar_strerror", "mstar_launch_count",
+    "mstar_accelerations", "mstar_tune_pair_tile", "mstar_free", "mstar_strerror", "mstar_launch_count",
     "mstar_profile_enable", "mstar_profile_read", "mstar_fp64_fma_rate", "mstar_accelerations_noalloc",
     "mstar_batch_workspace_bytes", "mstar_batch_init", "mstar_step_batched", "mstar_batch_get_state",
     "mstar_batch_set_H", "mstar_batch_set_schedule", "mstar_batch_get_schedule", "mstar_batch_autotune",
@@ -44,7 +44,8 @@ class mstar_params(C.Structure):
     _fields_ = [("eta_gbs", C.c_double), ("a_gbs", C.c_double), ("fac_min", C.c_double),
                 ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
                 ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int), ("max_halvings", C.c_int),
-                ("max_time_iter", C.c_int), ("mst_method", C.c_int), ("mst_nsub", C.c_int)]
+                ("max_time_iter", C.c_int), ("mst_method", C.c_int), ("mst_nsub", C.c_int),
+                ("pair_tile", C.c_int), ("pair_split", C.c_int)]
 
 
 class mstar_stats(C.Structure):
@@ -94,6 +95,8 @@ def load():
     L.mstar_set_H.argtypes = [vp, C.c_double]
     L.mstar_get_mst.argtypes = [vp, ip, ip, ip, ip]
     L.mstar_accelerations.argtypes = [vp, dp, C.POINTER(C.c_double)]
+    L.mstar_tune_pair_tile.argtypes = [C.c_int, dp, dp, dp, C.POINTER(mstar_params), C.c_int, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), dp, vp]
     L.mstar_free.argtypes = [vp]
     L.mstar_free.restype = None
     L.mstar_strerror.argtypes = [C.c_int]
@@ -232,6 +235,21 @@ def mstar_accelerations(ctx, a=None):
     U = C.c_double()
     _check(load().mstar_accelerations(ctx, _ptr(a), C.byref(U)), "mstar_accelerations")
     return U.value
+
+
+def mstar_tune_pair_tile(m, r, v, repeats=3, cuda_stream=None, **params):
+    """The pair loop whose GBS step attempts run fastest on the system (m, r, v) under the given
+    parameters: returns ((tile, split), {(tile, split): ms per attempt}) over (32, 4), (32, 1),
+    (64, 1) and (128, 1)."""
+    m, r, v = _system(m, r, v)
+    p = mstar_default_params(**params)
+    tile, split = C.c_int(), C.c_int()
+    ms = np.zeros(4)
+    rc = load().mstar_tune_pair_tile(len(m), _ptr(m), _ptr(r), _ptr(v), C.byref(p), int(repeats), C.byref(tile),
+                                     C.byref(split), _ptr(ms), cuda_stream)
+    _check(rc, "mstar_tune_pair_tile")
+    keys = [(32, 4), (32, 1), (64, 1), (128, 1)]
+    return (tile.value, split.value), {k: float(x) for k, x in zip(keys, ms)}
 
 
 def mstar_free(ctx):
@@ -597,7 +615,9 @@ MSTAR_REBUILD_MAX_N = 1024
 
 
 def mstar_rebuild_test(systems, coords, deconstruct, cycles, topo_every, sample_at, cuda_stream=None):
-    """Jobs j = (systems[j] = (m, r, v), coords[j], deconstruct[j]), all with the same n.
+    """Jobs j = (systems[j] = (m, r, v), coords[j] (0 MST, 1 chain), deconstruct[j] (0 path sums
+    and the COM shift, 1 path sums and the root kept, 2 from the root outwards, 3 from the root
+    outwards and the COM shift)), all with the same n.
     Returns dict(E (jobs x samples), r, v (jobs x n x 3), topo_changes, mean_level)."""
     nj = len(systems)
     n = len(systems[0][0])
