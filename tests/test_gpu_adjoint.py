@@ -9,7 +9,8 @@ positions and velocities is checked against
 - exact identities: translation invariance (the position and velocity gradients sum to 0)
   and rotation equivariance (sum r x dL/dr + v x dL/dv over the initial state equals
   sum r_f x w_r + v_f x w_v over the final state);
-- linearity in the loss (two calls with different loss gradients add up).
+- linearity in the loss (two calls with different loss gradients add up), and a repeated call
+  (which recomputes the segment the forward recorded) giving bit-identical gradients.
 """
 import numpy as np
 import pytest
@@ -94,6 +95,11 @@ def test_adjoint_symmetries_and_linearity():
     g12 = [x.cpu().numpy() for x in run.backward(w["r"], w2["v"], 1.3)]
     for a, b, c in zip(g1, g2, g12):
         assert np.abs(a + b - c).max() <= 1e-12 * np.abs(c).max()
+    # the first call swept the last segment from the trajectories the forward recorded; this
+    # call recomputes every segment from its checkpoint: the gradients are bit-identical
+    again = [x.cpu().numpy() for x in run.backward(w["r"], w["v"], w["E"])]
+    for a, b in zip((d_m, d_r, d_v), again):
+        assert np.array_equal(a, b)
     run.close()
 
 

@@ -101,21 +101,26 @@ def test_invalid_subgraph_count_rejected():
 
 def test_run_to_t1_on_dc_tree_matches_oracle():
     """Plummer 64 (8 subgraphs) to t = 1 with the divide-and-conquer tree in every step: the
-    end state agrees with the oracle's run on the same trees, and the energy error stays in
-    the regime the oracle's own pin allows on this tree (5e-13), or within 10x of the
-    oracle's error when that is larger (one realisation each; see the Plummer-64 test of the
-    exact tree for the spread)."""
+    end state agrees with the oracle's run on the same trees, and over 7 realisations (the start
+    and six starts perturbed at the 1e-15 level) the GPU's energy errors are within 10x of the
+    oracle's, median and maximum."""
     m, r, v = W.workload("plummer64")
-    g = M.Integrator(m, r, v, mst_method=1)
-    o = O.System(m, r, v, mst_method=1)
-    e0g, e0o = g.energy()["E"], o.energy()["E"]
-    rc, st = g.step(1.0)
-    rco, sto = o.integrate(1.0)
-    assert rc == 0 and rco == 0
-    S, So = g.state(), o.state()
-    rel = lambda x, y: float(np.abs(x - y).max() / np.abs(y).max())  # noqa: E731
-    assert rel(S["r"], So["r"]) < 1e-9 and rel(S["v"], So["v"]) < 1e-9
-    dEg = abs((g.energy()["E"] - e0g) / e0g)
-    dEo = abs((o.energy()["E"] - e0o) / e0o)
-    assert dEg <= max(10 * dEo, 5e-13), (dEg, dEo)
-    g.close()
+    dg, do = [], []
+    for k in range(7):
+        mk, rk, vk = W.perturbed(m, r, v, k)
+        g = M.Integrator(mk, rk, vk, mst_method=1)
+        o = O.System(mk, rk, vk, mst_method=1)
+        e0g, e0o = g.energy()["E"], o.energy()["E"]
+        rc, st = g.step(1.0)
+        rco, sto = o.integrate(1.0)
+        assert rc == 0 and rco == 0
+        if k == 0:
+            S, So = g.state(), o.state()
+            rel = lambda x, y: float(np.abs(x - y).max() / np.abs(y).max())  # noqa: E731
+            assert rel(S["r"], So["r"]) < 1e-9 and rel(S["v"], So["v"]) < 1e-9
+        dg.append(abs((g.energy()["E"] - e0g) / e0g))
+        do.append(abs((o.energy()["E"] - e0o) / e0o))
+        g.close()
+    dg, do = np.asarray(dg), np.asarray(do)
+    assert np.median(dg) <= 10 * np.median(do), (dg.tolist(), do.tolist())
+    assert dg.max() <= 10 * do.max(), (dg.tolist(), do.tolist())

@@ -132,6 +132,67 @@ def test_forces_every_tile_width(n):
     g.close()
 
 
+@pytest.mark.parametrize("n,tile", [(600, 128), (2050, 64), (5000, 32), (8193, 64), (10002, 32)])
+def test_forces_forced_tile(n, tile):
+    """A pair tile set by the caller (mstar_params.pair_tile) in place of the size rule: forces
+    and U against the oracle, ragged last tiles included."""
+    m, r, v = W.plummer(n, 12)
+    g = M.Integrator(m, r, v, pair_tile=tile)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=2)
+    assert relerr(a, ao) < 1e-13
+    assert abs(U - Uo) <= 1e-13 * Uo
+    # one attempt on the forced tile agrees with the size rule's to rounding
+    H = 1e-4
+    a1 = g.attempt(H)
+    g.close()
+    g = M.Integrator(m, r, v)
+    a0 = g.attempt(H)
+    g.close()
+    assert relerr(a1["r"], a0["r"]) < 1e-13 and relerr(a1["v"], a0["v"]) < 1e-13
+
+
+@pytest.mark.parametrize("name", ["plummer64", "plummer2048_smbh_binary"])
+def test_tune_pair_tile(name):
+    """The tuner times attempts with each pair loop and returns the fastest; a tile outside 32,
+    64, 128 or a split outside 1, 2, 4, 8 is refused."""
+    m, r, v = W.workload(name)
+    best, ms = M.mstar_tune_pair_tile(m, r, v, repeats=2)
+    assert set(ms) == {(32, 4), (32, 1), (64, 1), (128, 1)} and best in ms
+    assert all(x > 0 for x in ms.values()) and ms[best] == min(ms.values())
+    with pytest.raises(M.MstarError) as e:
+        M.Integrator(m, r, v, pair_tile=48)
+    assert e.value.code == M.MSTAR_ERR_INVALID_ARG
+    with pytest.raises(M.MstarError):
+        M.Integrator(m, r, v, pair_split=3)
+
+
+@pytest.mark.parametrize("n,split", [(2, 4), (33, 2), (64, 4), (97, 8), (600, 4), (2050, 4)])
+def test_forces_split_partner_steps(n, split):
+    """32-body tiles with a tile pair's partner steps split over 2, 4 or 8 warps: forces and U
+    against the oracle (ragged last tiles and the smallest system included), and one attempt
+    against the unsplit loop's to rounding."""
+    m, r, v = W.plummer(n, 13) if n > 2 else W.kepler_binary(seed=5)
+    g = M.Integrator(m, r, v, pair_tile=32, pair_split=split)
+    a, U = g.accelerations()
+    st = g.state()
+    root, par, lev, order = O.prim(st["r"])
+    X = O.to_mst(par, st["r"])
+    ao, Uo = O.forces(m, st["r"], par, lev, X, n_d=2)
+    assert relerr(a, ao) < 1e-13
+    assert abs(U - Uo) <= 1e-13 * Uo
+    H = 1e-4
+    a1 = g.attempt(H)
+    g.close()
+    g = M.Integrator(m, r, v, pair_tile=32, pair_split=1)
+    a0 = g.attempt(H)
+    g.close()
+    assert relerr(a1["r"], a0["r"]) < 1e-13 and relerr(a1["v"], a0["v"]) < 1e-13
+
+
 @pytest.mark.parametrize("n_d", [0, 1, 2])
 @pytest.mark.parametrize("n", [600, 5000])
 def test_forces_every_near_rule(n_d, n):
@@ -270,53 +331,96 @@ def test_one_attempt_full_size_plummer10k():
     g.close()
 
 
+def energy_error(sysobj, t_end, steps):
+    """|dE/E| of one run through the given integrator (GPU context or oracle system)."""
+    e0 = sysobj.energy()["E"]
+    if hasattr(sysobj, "integrate"):
+        rc, st = sysobj.integrate(t_end, steps)
+    else:
+        rc, st = sysobj.step(t_end, steps)
+    assert rc == 0, rc
+    return abs((sysobj.energy()["E"] - e0) / e0), st
+
+
+def assert_within_10x(dg, do):
+    """The bar on the energy error after a full run: within 10x of the oracle's. Each run's
+    |dE/E| is one realisation of rounding and truncation along its own step sequence (a
+    start perturbed at the 1e-15 level moves it over two decades), so the bar is applied to
+    ensembles of perturbed starts: the GPU's median within 10x of the oracle's median, and
+    the GPU's largest error within 10x of the oracle's largest."""
+    dg, do = np.asarray(dg), np.asarray(do)
+    assert np.median(dg) <= 10 * np.median(do), (dg.tolist(), do.tolist())
+    assert dg.max() <= 10 * do.max(), (dg.tolist(), do.tolist())
+
+
+def golden_ensemble(key, k):
+    g = Hh.golden("energy_ensemble")
+    return [g[f"{key}_dE_r{i}"] for i in range(k)], [g[f"{key}_t_r{i}"] for i in range(k)]
+
+
 def test_plummer64_run_to_t1_matches_oracle():
-    """The configuration integrated to t = 1: the end state agrees with the oracle's, and the
-    energy error stays in the paper's accuracy regime: below 3e-13, or within 10x of the
-    oracle's when that is larger. The oracle's own error for this run is one realisation:
-    perturbing one coordinate by 1e-15 spreads it over 1.2e-15 ... 1.2e-13."""
+    """The configuration integrated to t = 1: the end state agrees with the oracle's, both land
+    on t = 1, and over 7 realisations (workloads.perturbed: the start, and six starts perturbed at
+    the 1e-15 level) the GPU's energy errors are within 10x of the oracle's (median and max)."""
     m, r, v = SYS["plummer64"]
     g = M.Integrator(m, r, v)
     o = O.System(m, r, v)
-    e0g = g.energy()["E"]
-    e0o = o.energy()["E"]
-    rc, st = g.step(1.0)
-    rco, sto = o.integrate(1.0)
-    assert rc == 0 and rco == 0
+    dEg, st = energy_error(g, 1.0, 1 << 30)
+    dEo, sto = energy_error(o, 1.0, 1 << 30)
     assert abs(st["t"] - 1.0) <= 1e-10 and abs(sto["t"] - 1.0) <= 1e-10
     S, So = g.state(), o.state()
     assert relerr(S["r"], So["r"]) < 1e-9
     assert relerr(S["v"], So["v"]) < 1e-9
-    dEg = abs((g.energy()["E"] - e0g) / e0g)
-    dEo = abs((o.energy()["E"] - e0o) / e0o)
-    assert dEg <= max(10 * dEo, 3e-13), (dEg, dEo)
     # accept/reject decisions compare eps (rounding-noise level near eta) with eta, so the
     # two step sequences may differ by a few steps; both land on t = 1 with the same state
     assert abs(st["accepted"] - sto["accepted"]) <= max(3, sto["accepted"] // 10)
     g.close()
+    dg, do = [dEg], [dEo]
+    for k in range(1, 7):
+        mk, rk, vk = W.perturbed(m, r, v, k)
+        g = M.Integrator(mk, rk, vk)
+        dg.append(energy_error(g, 1.0, 1 << 30)[0])
+        g.close()
+        do.append(energy_error(O.System(mk, rk, vk), 1.0, 1 << 30)[0])
+    assert_within_10x(dg, do)
 
 
 def test_smbh_binary_2050_200_steps_energy_within_10x_of_oracle():
-    """Plummer 2048 with a central SMBH binary, 200 accepted GBS steps: the energy error of
-    the GPU run stays in the paper's accuracy regime (|dE/E| of order 1e-14, abstract and
-    Sec. 6): below 3e-13, or within 10x of the oracle's when that is larger. Both runs reach
-    comparable times (their step sequences may differ where eps sits at eta).
-    Each run's error is one realisation of rounding and truncation along its own step
-    sequence. Initial conditions perturbed by 1e-15 in one coordinate gave 8e-16 ... 8.6e-14
-    over eight GPU runs and 1.7e-15 ... 4.8e-14 over four oracle runs."""
+    """Plummer 2048 with a central SMBH binary, 200 accepted GBS steps towards t_end = 10: over
+    five realisations (the start and four starts perturbed at the 1e-15 level) the GPU's
+    |dE/E| is within 10x of the oracle's, median and maximum. The oracle's five runs take
+    minutes, so their errors and end times are read from tests/golden/energy_ensemble.txt
+    (written by tests/golden/make_energy_ensemble.py, which runs only the oracle). Both reach
+    comparable times (their step sequences may differ where eps sits at eta)."""
+    do, to = golden_ensemble("c2", 5)
     m, r, v = W.workload("plummer2048_smbh_binary")
-    g = M.Integrator(m, r, v)
-    o = O.System(m, r, v)
-    e0g = g.energy()["E"]
-    e0o = o.energy()["E"]
-    rc, st = g.step(10.0, 200)
-    rco, sto = o.integrate(10.0, 200)
-    assert rc == 0 and rco == 0 and st["accepted"] == 200 and sto["accepted"] == 200
-    dEg = abs((g.energy()["E"] - e0g) / e0g)
-    dEo = abs((o.energy()["E"] - e0o) / e0o)
-    assert dEg <= max(10 * dEo, 3e-13), (dEg, dEo)
-    assert abs(st["t"] - sto["t"]) <= 0.05 * sto["t"], (st["t"], sto["t"])
-    g.close()
+    dg = []
+    for k in range(5):
+        g = M.Integrator(*W.perturbed(m, r, v, k))
+        dE, st = energy_error(g, 10.0, 200)
+        g.close()
+        assert st["accepted"] == 200
+        assert abs(st["t"] - to[k]) <= 0.05 * to[k], (st["t"], to[k])
+        dg.append(dE)
+    assert_within_10x(dg, do)
+
+
+def test_plummer10k_two_smbh_20_steps_energy_within_10x_of_oracle():
+    """The benchmark workload (Plummer 10^4 + two SMBHs, N = 10002), 20 accepted GBS steps from
+    the start towards t_end = 1 (the first step from ds = q U dt, as the benchmark takes them):
+    over five realisations the GPU's |dE/E| is within 10x of the oracle's, median and maximum.
+    The oracle's runs (~6 min each) are read from tests/golden/energy_ensemble.txt."""
+    do, to = golden_ensemble("c5", 5)
+    m, r, v = W.workload("plummer10k_two_smbh")
+    dg = []
+    for k in range(5):
+        g = M.Integrator(*W.perturbed(m, r, v, k))
+        dE, st = energy_error(g, 1.0, 20)
+        g.close()
+        assert st["accepted"] == 20
+        assert abs(st["t"] - to[k]) <= 0.05 * to[k], (st["t"], to[k])
+        dg.append(dE)
+    assert_within_10x(dg, do)
 
 
 def test_lidov_kozai_first_cycles_match_oracle():
