@@ -49,15 +49,15 @@ NOMINAL_FP64_TFLOPS = 1.25
 DFMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
-# Figures from ncu captures of k_pair_tiles at N = 10002, valid for the kernel built from the
-# sources whose SHA-256 (csrc/pair.cu then csrc/device.cuh) starts with PAIR_TILE_SRC_SHA;
+# Figures from ncu captures of k_pair_tiles at N = 10002, each valid for the kernel built from
+# the sources whose SHA-256 (csrc/pair.cu then csrc/device.cuh) starts with the given prefix;
 # for any other source the bench reports them as null.
 #  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
 #    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
 #  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
-PAIR_TILE_SRC_SHA = "2e6acdc6a5f9b120"
-PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 446e3, 2: 714e3, 3: 14.31e6, 4: 39.64e6, 5: 65.77e6, 6: 92.18e6,
-                                 7: 117.17e6, 8: 143.36e6}
+PAIR_TILE_SRC_SHA = "23e8af75ea0546f9"
+PAIR_TILE_PIPE_SRC_SHA = "2e6acdc6a5f9b120"
+PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 3.669e6, 2: 0.762e6, 3: 15.006e6, 4: 21.056e6, 5: 25.432e6, 6: 29.190e6, 7: 34.097e6, 8: 41.687e6}
 PAIR_TILE_FP64_PIPE_NCU = 0.870
 ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 # Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-subsystems measurement and print its object")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the adjoint measurement and print its object (profiling)")
     ap.add_argument("--no-rebuild-test", action="store_true")
     ap.add_argument("--batched-schedule", default=None,
                     help="comma-separated schedule per size class instead of the autotuner's (profiling)")
@@ -428,9 +430,10 @@ def run_mst_builders(args, dev, M, m, r, v, torch):
 
 
 REBUILD_DESC = ("rebuild test of Sec. 3.5: Hernquist N=379 (r_half=1, G=M=1; seeds 1..10, clusters with a hard "
-                "binary redrawn), 1e5 build/deconstruct cycles per system, MST and chain coordinates, "
-                "deconstruction with the centre-of-mass shift (the integrator's) and with the root position kept; "
-                "topology rebuilt every 1000 cycles; energies with compensated sums")
+                "binary redrawn), 1e5 build/deconstruct cycles per system, MST and chain coordinates; "
+                "deconstruction by per-vertex path sums with the centre-of-mass shift (the integrator's) or the "
+                "root position kept, or from the root outwards (w_v = w_parent + X_v) with the root kept or "
+                "followed by the shift; topology rebuilt every 1000 cycles; energies with compensated sums")
 
 
 def run_rebuild_test(args, dev, M, W, O_unused=None):
@@ -440,13 +443,14 @@ def run_rebuild_test(args, dev, M, W, O_unused=None):
 
     systems = [W.hernquist(379, s)[:3] for s in range(1, 11)]
     samples = [0, 1, 3, 10, 30, 100, 300, 1000, 3000, 10000, 30000, 100000]
-    jobs = [(s, c, d) for d in (0, 1) for c in (0, 1) for s in range(10)]
+    rules = ((0, "com_shift"), (1, "root_kept"), (2, "root_outwards"), (3, "root_outwards_com_shift"))
+    jobs = [(s, c, d) for d, _ in rules for c in (0, 1) for s in range(10)]
     t0 = time.perf_counter()
     g = M.mstar_rebuild_test([systems[s] for s, _, _ in jobs], [c for _, c, _ in jobs], [d for _, _, d in jobs],
                              samples[-1], 1000, samples)
     wall = time.perf_counter() - t0
     out = {"workload": REBUILD_DESC, "samples": samples, "wall_s": wall, "jobs": len(jobs)}
-    for d, dname in ((0, "com_shift"), (1, "root_kept")):
+    for d, dname in rules:
         for c, cname in ((0, "mst"), (1, "chain")):
             idx = [k for k, (s, cc, dd) in enumerate(jobs) if cc == c and dd == d]
             E = g["E"][idx]
@@ -454,7 +458,8 @@ def run_rebuild_test(args, dev, M, W, O_unused=None):
             out[f"{cname}_{dname}_mean_dE"] = rel.mean(axis=0).tolist()
             out[f"{cname}_{dname}_mean_level"] = float(np.mean(g["mean_level"][idx]))
             out[f"{cname}_{dname}_topo_changes"] = int(np.sum(g["topo_changes"][idx]))
-        out[f"chain_over_mst_{dname}_at_1e5"] = out[f"chain_{dname}_mean_dE"][-1] / out[f"mst_{dname}_mean_dE"][-1]
+        mst_e = out[f"mst_{dname}_mean_dE"][-1]
+        out[f"chain_over_mst_{dname}_at_1e5"] = out[f"chain_{dname}_mean_dE"][-1] / mst_e if mst_e > 0 else None
     return out
 
 
@@ -537,6 +542,9 @@ def run_mstar(args):
     M.load()
     if args.batched_only:
         print(json.dumps(run_batched(args, dev, M, W, torch)), flush=True)
+        return
+    if args.adjoint_only:
+        print(json.dumps(run_adjoint(args, dev, M, W, torch)), flush=True)
         return
     m, r, v = W.workload(WORKLOAD)
     n = len(m)
@@ -650,7 +658,8 @@ def run_mstar(args):
                 "fp64_pipe_util": pairs_per_launch * FP64_INSTR_PER_PAIR / (avg_ms * 1e-3) / fp64_issue,
                 "fp64_pipe_util_source": ("pair rate x 9 FP64 instructions per pair / (2 per clk per SM x 152 "
                                           "SMs x sampled clock)"),
-                "fp64_pipe_util_ncu": PAIR_TILE_FP64_PIPE_NCU if sha_ok else None,
+                "fp64_pipe_util_ncu": (PAIR_TILE_FP64_PIPE_NCU if pair_source_sha() == PAIR_TILE_PIPE_SRC_SHA
+                                       else None),
                 "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch by slot count, "
                                    "averaged over an attempt's 17 launches; null when the kernel's sources "
                                    "differ from the captured ones" + ("" if sha_ok else " (they differ)")),
