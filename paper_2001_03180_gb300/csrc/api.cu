@@ -259,6 +259,17 @@ int issue_attempt(mstar_ctx* c) {
       CK(save(tr->R + (tau - 1) * lvl + lo * st, c->d.sr + lo * st, (K - lo) * st));
       CK(save(tr->A + (tau - 1) * lvl + lo * st, c->d.sa + lo * st, (K - lo) * st));
     }
+    const int lo2 = tau / 2;  // divisions with n_k > tau need positions for the next kick
+    if (c->npad <= kLevelCtaMax) {
+      // one CTA per division: the whole level in one launch (the position rebuild leaves the
+      // velocities and scalars that the trajectory record takes below as they were)
+      CK(launch_level_cta(c, lo, lo2, tau));
+      if (tr) {
+        CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
+        CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
+      }
+      continue;
+    }
     CK(launch_kick(c, lo, K));
     CK(launch_rebuild(c, c->d.sV + lo * st, c->d.sv + lo * st, st, K - lo, 1, c->d.Tblk + (size_t)lo * c->nblk,
                       c->d.comblk + (size_t)lo * c->nblk * 3));
@@ -267,7 +278,6 @@ int issue_attempt(mstar_ctx* c) {
       CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
       CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
     }
-    const int lo2 = tau / 2;  // divisions with n_k > tau need positions for the next kick
     if (lo2 < K)
       CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
                         c->d.comblk + (size_t)lo2 * c->nblk * 3));

@@ -156,6 +156,13 @@ cudaError_t launch_drift(mstar_ctx* c, int slot_lo, int slot_hi, int tau);
 cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stride, int nsl,
                            int want_T, double* Tblk_base, double* comblk_base);
 cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged rebuild's shared memory
+// kick, velocity rebuild, drift and position rebuild of one level in one CTA per division
+// (systems with npad <= kLevelCtaMax: up to 256 bodies, where it beats the multi-CTA path by
+// launches saved; above, one SM per division binds its path sums); the divisions >= pos_lo get
+// their positions rebuilt
+constexpr int kLevelCtaMax = 256;
+cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int pos_lo, int tau);
+
 cudaError_t launch_extrapolate(mstar_ctx* c);
 cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom
 // w (3 planes of the state) -= centre of mass; optionally T partials into Tblk slot 0

@@ -243,6 +243,101 @@ k_rebuild_staged(int n, int npad, size_t stride, const int* __restrict__ parent,
   }
 }
 
+// Sum over the CTA, returned to every thread (block_sum leaves it in thread 0).
+__device__ __forceinline__ double cta_sum(double x, double* scratch, double* out) {
+  const double b = block_sum(x, scratch);
+  if (threadIdx.x == 0) *out = b;
+  __syncthreads();
+  return *out;
+}
+
+// One substep level of every active division of a system that one CTA holds (npad <= 1024,
+// one body per thread): the kick K(delta) of k_kick, the velocities rebuilt by path sums and
+// shifted to the centre-of-mass frame with their kinetic energy (k_rebuild, k_shift), the
+// drift of k_drift, and, for the divisions that kick again (slot >= pos_lo), the positions
+// rebuilt and shifted - six launches of the multi-CTA path in one, with the CTA's barriers in
+// place of the kernel boundaries. The edge vectors are staged in shared memory for the
+// walks. The operations are those of the multi-CTA kernels; the centre-of-mass and kinetic
+// sums are CTA-wide instead of per 64-body block, so they round in another order.
+__global__ void __launch_bounds__(1024)
+k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__ par, double B, double Mtot,
+            int tau, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ bylev,
+            const double* __restrict__ sa, double* __restrict__ sV, double* __restrict__ sv, double* __restrict__ sX,
+            double* __restrict__ sr, const double* __restrict__ Ublk, int nblk, double* __restrict__ sc) {
+  extern __shared__ __align__(16) double lvl_sh[];  // 3 npad staged edge vectors, then npad parents
+  double* sW = lvl_sh;
+  int* sP = reinterpret_cast<int*>(lvl_sh + 3 * (size_t)npad);
+  __shared__ double scratch[32];
+  __shared__ double s_bc[8];
+  const int slot = slot_lo + blockIdx.x;
+  const int tid = threadIdx.x;
+  const size_t st = (size_t)3 * npad;
+  double* V = sV + slot * st;
+  double* X = sX + slot * st;
+  const double* a = sa + slot * st;
+  const double H = par[0];
+  for (int u = tid; u < npad; u += blockDim.x) sP[u] = u < n ? parent[u] : -1;
+  sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &s_bc[0]);  // ends with a barrier
+  const double U = s_bc[0];
+  // K(delta): V_w += (delta / U) (a_w - a_parent(w))
+  const double fk = (H / (double)(2 * (slot + 1))) / U;
+  for (int w = tid; w < npad; w += blockDim.x) {
+    const int p = sP[w];
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad + w;
+      double x = V[o];
+      if (p >= 0) x = madd(x, fk, __dsub_rn(a[o], a[(size_t)c * npad + p]));
+      V[o] = x;
+      sW[o] = x;
+    }
+  }
+  if (tid == 0) sc[slot * kScal + SC_U] = U;
+  __syncthreads();
+  // the Cartesian vectors of the edge vectors in sW by path sums, shifted to the COM frame;
+  // returns sum m w^2 over the bodies
+  auto rebuild = [&](double* w_out) {
+    const int v = tid < n ? bylev[tid] : n;
+    double q[3] = {0.0, 0.0, 0.0};
+    if (v < n)
+      for (int u = v; sP[u] >= 0; u = sP[u]) {
+        q[0] = __dadd_rn(q[0], sW[u]);
+        q[1] = __dadd_rn(q[1], sW[npad + u]);
+        q[2] = __dadd_rn(q[2], sW[2 * (size_t)npad + u]);
+      }
+    const double mv = v < n ? m[v] : 0.0;
+    double com[3];
+    for (int c = 0; c < 3; ++c) com[c] = cta_sum(__dmul_rn(mv, q[c]), scratch, &s_bc[1 + c]);
+    double t2 = 0.0;
+    if (v < n) {
+      for (int c = 0; c < 3; ++c) {
+        q[c] = __dsub_rn(q[c], com[c] / Mtot);
+        w_out[(size_t)c * npad + v] = q[c];
+      }
+      t2 = __dmul_rn(mv, __dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
+    }
+    return t2;
+  };
+  const double T = 0.5 * cta_sum(rebuild(sv + slot * st), scratch, &s_bc[4]);
+  // D(h): X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift
+  const int nk = 2 * (slot + 1);
+  const double delta = H / (double)nk;
+  const double h = (tau == nk) ? 0.5 * delta : delta;
+  const double fd = h / (T + B);
+  for (int w = tid; w < npad; w += blockDim.x)
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad + w;
+      const double x = madd(X[o], fd, V[o]);
+      X[o] = x;
+      sW[o] = x;
+    }
+  if (tid == 0) {
+    sc[slot * kScal + SC_T_PHYS] += fd;
+    sc[slot * kScal + SC_T_KIN] = T;
+  }
+  __syncthreads();
+  if (slot >= pos_lo) rebuild(sr + slot * st);
+}
+
 // Shift to the centre-of-mass frame: w -= (sum m w) / M; optionally block sums of m w^2.
 __global__ void __launch_bounds__(kBlock)
 k_shift(int n, int npad, size_t stride, double Mtot, double* __restrict__ wb, const double* __restrict__ m,
@@ -463,6 +558,18 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   if (e != cudaSuccess) return e;
   k_shift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->Mtot, w, c->d.m, comblk_base,
                                          want_T ? Tblk_base : nullptr, c->nblk);
+  MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// One substep level (kick, velocity rebuild, drift, position rebuild) of the divisions
+// [slot_lo, K) in one launch, for systems with npad <= kLevelCtaMax.
+cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int pos_lo, int tau) {
+  const size_t smem = (size_t)c->npad * (3 * sizeof(double) + sizeof(int));
+  k_level_cta<<<c->K - slot_lo, c->npad, smem, c->stream>>>(c->n, c->npad, slot_lo, pos_lo, c->d.res + 4, c->B,
+                                                            c->Mtot, tau, c->d.m, c->d.parent, c->d.bylev, c->d.sa,
+                                                            c->d.sV, c->d.sv, c->d.sX, c->d.sr, c->d.Ublk, c->nblk,
+                                                            c->d.sc);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
 }
