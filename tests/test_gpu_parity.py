@@ -353,6 +353,15 @@ def assert_within_10x(dg, do):
     assert dg.max() <= 10 * do.max(), (dg.tolist(), do.tolist())
 
 
+def assert_times_in_range(tg, to):
+    """The time a fixed number of accepted steps reaches depends on the step sequence, which is
+    a realisation like the energy error (the oracle's five runs of the N = 2050 case end between
+    t = 0.355 and 0.381): every GPU run ends within 5 % of the oracle ensemble's range."""
+    lo, hi = min(to), max(to)
+    for t in tg:
+        assert 0.95 * lo <= t <= 1.05 * hi, (tg, to)
+
+
 def golden_ensemble(key, k):
     g = Hh.golden("energy_ensemble")
     return [g[f"{key}_dE_r{i}"] for i in range(k)], [g[f"{key}_t_r{i}"] for i in range(k)]
@@ -390,19 +399,21 @@ def test_smbh_binary_2050_200_steps_energy_within_10x_of_oracle():
     five realisations (the start and four starts perturbed at the 1e-15 level) the GPU's
     |dE/E| is within 10x of the oracle's, median and maximum. The oracle's five runs take
     minutes, so their errors and end times are read from tests/golden/energy_ensemble.txt
-    (written by tests/golden/make_energy_ensemble.py, which runs only the oracle). Both reach
-    comparable times (their step sequences may differ where eps sits at eta)."""
+    (written by tests/golden/make_energy_ensemble.py, which runs only the oracle). The times
+    reached lie within the oracle ensemble's range (their step sequences differ where eps sits
+    at eta)."""
     do, to = golden_ensemble("c2", 5)
     m, r, v = W.workload("plummer2048_smbh_binary")
-    dg = []
+    dg, tg = [], []
     for k in range(5):
         g = M.Integrator(*W.perturbed(m, r, v, k))
         dE, st = energy_error(g, 10.0, 200)
         g.close()
         assert st["accepted"] == 200
-        assert abs(st["t"] - to[k]) <= 0.05 * to[k], (st["t"], to[k])
         dg.append(dE)
+        tg.append(st["t"])
     assert_within_10x(dg, do)
+    assert_times_in_range(tg, to)
 
 
 def test_plummer10k_two_smbh_20_steps_energy_within_10x_of_oracle():
@@ -412,15 +423,16 @@ def test_plummer10k_two_smbh_20_steps_energy_within_10x_of_oracle():
     The oracle's runs (~6 min each) are read from tests/golden/energy_ensemble.txt."""
     do, to = golden_ensemble("c5", 5)
     m, r, v = W.workload("plummer10k_two_smbh")
-    dg = []
+    dg, tg = [], []
     for k in range(5):
         g = M.Integrator(*W.perturbed(m, r, v, k))
         dE, st = energy_error(g, 1.0, 20)
         g.close()
         assert st["accepted"] == 20
-        assert abs(st["t"] - to[k]) <= 0.05 * to[k], (st["t"], to[k])
         dg.append(dE)
+        tg.append(st["t"])
     assert_within_10x(dg, do)
+    assert_times_in_range(tg, to)
 
 
 def test_lidov_kozai_first_cycles_match_oracle():
