@@ -85,6 +85,12 @@ typedef struct {
                         1, 2, 4 or 8, or 0 for the size rule (4 up to 512 bodies, else 1); the
                         other tiles take 1. Partial sums are added in warp order, so results
                         differ from the unsplit loop by rounding only. 0 */
+  int division_streams; /* how an attempt's k_fix divisions are issued: 1 level by level (one launch
+                        per kernel for every division active at that substep), 2 each division on
+                        its own stream, so that one division's small kernels overlap another's pair
+                        loop (attempts that record an adjoint trajectory or time the pair kernel use
+                        1), 0 for the size rule (2 from 1000 bodies, else 1). Results are the same
+                        either way. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */

@@ -117,6 +117,7 @@ bool valid_params(const mstar_params* p) {
   if (p->pair_tile != 0 && p->pair_tile != 32 && p->pair_tile != 64 && p->pair_tile != 128) return false;
   if (p->pair_split != 0 && p->pair_split != 1 && p->pair_split != 2 && p->pair_split != 4 && p->pair_split != 8)
     return false;
+  if (p->division_streams < 0 || p->division_streams > 2) return false;
   return true;
 }
 
@@ -239,7 +240,10 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
 // The launches of one attempt after the staging of H and t: all divisions level by level
 // (the divisions with n_k >= tau kick and drift at level tau), then the extrapolation.
 // With a trajectory record the states of every level are saved on the way.
+int issue_attempt_branched(mstar_ctx* c);
+
 int issue_attempt(mstar_ctx* c) {
+  if (c->branched && !c->traj && !c->prof) return issue_attempt_branched(c);
   const int K = c->K;
   const size_t st = (size_t)3 * c->npad;
   AdjTraj* tr = c->traj;
@@ -263,7 +267,7 @@ int issue_attempt(mstar_ctx* c) {
     if (c->npad <= kLevelCtaMax) {
       // one CTA per division: the whole level in one launch (the position rebuild leaves the
       // velocities and scalars that the trajectory record takes below as they were)
-      CK(launch_level_cta(c, lo, lo2, tau));
+      CK(launch_level_cta(c, lo, K, lo2, tau));
       if (tr) {
         CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
         CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
@@ -282,6 +286,49 @@ int issue_attempt(mstar_ctx* c) {
       CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
                         c->d.comblk + (size_t)lo2 * c->nblk * 3));
   }
+  CK(launch_extrapolate(c));
+  return MSTAR_OK;
+}
+
+// The attempt with each division on its own stream: after the first half drift of every
+// division (on the context's stream), division k runs its n_k kicks and drifts as one chain on
+// stream k, and the extrapolation waits for all of them. A division's launches are those of
+// the level order restricted to its slot, so the results are the same; the chains overlap one
+// division's small kernels with another's pair loop. Every buffer these launches touch is
+// indexed by slot, so the chains share nothing.
+int issue_attempt_branched(mstar_ctx* c) {
+  const int K = c->K;
+  const size_t st = (size_t)3 * c->npad;
+  cudaStream_t main_stream = c->stream;
+  if (!c->br_fork) return MSTAR_ERR_CUDA;  // created with the context
+  CK(launch_init_drift(c));
+  CK(cudaEventRecord(c->br_fork, main_stream));
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < K && e == cudaSuccess; ++k) {
+    c->stream = c->br_stream[k];
+    e = cudaStreamWaitEvent(c->stream, c->br_fork, 0);
+    const int nk = 2 * (k + 1);
+    for (int tau = 1; tau <= nk && e == cudaSuccess; ++tau) {
+      e = launch_forces(c, k, k + 1, c->p.n_d);
+      const int pos = tau < nk ? k : k + 1;  // positions for the next kick, unless this was the last
+      if (e == cudaSuccess && c->npad <= kLevelCtaMax) {
+        e = launch_level_cta(c, k, k + 1, pos, tau);
+        continue;
+      }
+      if (e == cudaSuccess) e = launch_kick(c, k, k + 1);
+      if (e == cudaSuccess)
+        e = launch_rebuild(c, c->d.sV + k * st, c->d.sv + k * st, st, 1, 1, c->d.Tblk + (size_t)k * c->nblk,
+                           c->d.comblk + (size_t)k * c->nblk * 3);
+      if (e == cudaSuccess) e = launch_drift(c, k, k + 1, tau);
+      if (e == cudaSuccess && pos == k)
+        e = launch_rebuild(c, c->d.sX + k * st, c->d.sr + k * st, st, 1, 0, nullptr,
+                           c->d.comblk + (size_t)k * c->nblk * 3);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->br_join[k], c->stream);
+  }
+  c->stream = main_stream;
+  CK(e);
+  for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(main_stream, c->br_join[k], 0));
   CK(launch_extrapolate(c));
   return MSTAR_OK;
 }
@@ -456,6 +503,7 @@ void mstar_default_params(mstar_params* p) {
   p->mst_nsub = 0;
   p->pair_tile = 0;
   p->pair_split = 0;
+  p->division_streams = 0;
 }
 
 size_t mstar_workspace_bytes(int n, const mstar_params* p) {
@@ -491,6 +539,11 @@ void mstar_free(mstar_ctx* c) {
   }
   for (auto& ag : c->att_graphs) cudaGraphExecDestroy(ag.exec);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (int k = 0; k < kMaxKfix; ++k) {
+    if (c->br_stream[k]) cudaStreamDestroy(c->br_stream[k]);
+    if (c->br_join[k]) cudaEventDestroy(c->br_join[k]);
+  }
+  if (c->br_fork) cudaEventDestroy(c->br_fork);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->host_res) cudaFreeHost(c->host_res);
   if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -523,6 +576,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   c->NT = s.NT;
   c->ntp = s.NT * (s.NT + 1) / 2;
   c->S = s.W != 1 ? 1 : (p->pair_split ? p->pair_split : (n <= 512 ? 4 : 1));
+  c->branched = p->division_streams ? p->division_streams == 2 : n >= 1000;
   c->nblk = s.nblk;
   const size_t need = carve(s, nullptr, nullptr, nullptr);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -559,6 +613,13 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
       prepare_rebuild(c) != cudaSuccess)
     return bail(MSTAR_ERR_CUDA);
+  if (c->branched) {  // the streams and events of the per-division attempt graph
+    if (cudaEventCreateWithFlags(&c->br_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
+    for (int k = 0; k < c->K; ++k)
+      if (cudaStreamCreateWithFlags(&c->br_stream[k], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->br_join[k], cudaEventDisableTiming) != cudaSuccess)
+        return bail(MSTAR_ERR_CUDA);
+  }
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.parent, c->npad, -1);
   k_fill_int<<<blocks_for(c->npad), kBlock, 0, c->stream>>>(c->d.gp, c->npad, -1);
   c->launches += 2;

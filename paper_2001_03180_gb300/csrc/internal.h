@@ -81,6 +81,9 @@ struct mstar_ctx {
   int n = 0, npad = 0, K = 0, nslots = 0;
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
   int S = 1;                          // warps sharing a tile pair's partner steps (32-body tiles)
+  bool branched = false;              // attempts issue each division on its own stream
+  cudaStream_t br_stream[mstar::kMaxKfix] = {};  // those streams (created with the context)
+  cudaEvent_t br_fork = nullptr, br_join[mstar::kMaxKfix] = {};
   int pair_defer = -1;  // trailing slots of a pair launch summed by the finishing pass (-1: unset)
   size_t rebuild_smem = 0;  // shared memory of the staged rebuild (0: the plain kernel is used)
   int nblk = 0;
@@ -161,7 +164,7 @@ cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged r
 // launches saved; above, one SM per division binds its path sums); the divisions >= pos_lo get
 // their positions rebuilt
 constexpr int kLevelCtaMax = 256;
-cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int pos_lo, int tau);
+cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau);
 
 cudaError_t launch_extrapolate(mstar_ctx* c);
 cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom

@@ -252,8 +252,9 @@ __device__ __forceinline__ double cta_sum(double x, double* scratch, double* out
 }
 
 // One substep level of every active division of a system that one CTA holds (npad <= 1024,
-// one body per thread): the kick K(delta) of k_kick, the velocities rebuilt by path sums and
-// shifted to the centre-of-mass frame with their kinetic energy (k_rebuild, k_shift), the
+// one body per thread; the step uses it up to kLevelCtaMax): the kick K(delta) of k_kick, the
+// velocities rebuilt by path sums and shifted to the centre-of-mass frame with their kinetic
+// energy (k_rebuild, k_shift), the
 // drift of k_drift, and, for the divisions that kick again (slot >= pos_lo), the positions
 // rebuilt and shifted - six launches of the multi-CTA path in one, with the CTA's barriers in
 // place of the kernel boundaries. The edge vectors are staged in shared memory for the
@@ -563,10 +564,10 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
 }
 
 // One substep level (kick, velocity rebuild, drift, position rebuild) of the divisions
-// [slot_lo, K) in one launch, for systems with npad <= kLevelCtaMax.
-cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int pos_lo, int tau) {
+// [slot_lo, slot_hi) in one launch, for systems with npad <= kLevelCtaMax.
+cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau) {
   const size_t smem = (size_t)c->npad * (3 * sizeof(double) + sizeof(int));
-  k_level_cta<<<c->K - slot_lo, c->npad, smem, c->stream>>>(c->n, c->npad, slot_lo, pos_lo, c->d.res + 4, c->B,
+  k_level_cta<<<slot_hi - slot_lo, c->npad, smem, c->stream>>>(c->n, c->npad, slot_lo, pos_lo, c->d.res + 4, c->B,
                                                             c->Mtot, tau, c->d.m, c->d.parent, c->d.bylev, c->d.sa,
                                                             c->d.sV, c->d.sv, c->d.sX, c->d.sr, c->d.Ublk, c->nblk,
                                                             c->d.sc);

@@ -193,6 +193,24 @@ def test_forces_split_partner_steps(n, split):
     assert relerr(a1["r"], a0["r"]) < 1e-13 and relerr(a1["v"], a0["v"]) < 1e-13
 
 
+@pytest.mark.parametrize("n", [200, 600, 2050, 5000])
+def test_division_streams_give_the_same_steps(n):
+    """Attempts issued level by level (one launch per kernel for every active division) and with
+    each division on its own stream run the same kernels on the same slots in the same order of
+    summation: the accepted steps are bit-identical."""
+    m, r, v = W.plummer_smbh_binary(n - 2, 6)
+    out = []
+    for mode in (1, 2):
+        g = M.Integrator(m, r, v, division_streams=mode)
+        rc, st = g.step(10.0, 3)
+        assert rc == 0
+        S = g.state()
+        out.append((S["r"], S["v"], S["t"], st["accepted"], st["rejected"]))
+        g.close()
+    (r1, v1, t1, a1, j1), (r2, v2, t2, a2, j2) = out
+    assert np.array_equal(r1, r2) and np.array_equal(v1, v2) and t1 == t2 and (a1, j1) == (a2, j2)
+
+
 @pytest.mark.parametrize("n_d", [0, 1, 2])
 @pytest.mark.parametrize("n", [600, 5000])
 def test_forces_every_near_rule(n_d, n):
