@@ -49,9 +49,9 @@ NOMINAL_FP64_TFLOPS = 1.25
 DFMA_PER_CLK_PER_SM = 2
 NUM_SMS = 152
 L2_FLUSH_BYTES = 256 << 20
-# Figures from ncu captures of k_pair_tiles at N = 10002, each valid for the kernel built from
-# the sources whose SHA-256 (csrc/pair.cu then csrc/device.cuh) starts with the given prefix;
-# for any other source the bench reports them as null.
+# Figures from ncu captures of k_pair_tiles<4> (128-body tiles) at N = 10002, each valid for the
+# kernel built from the sources whose SHA-256 (csrc/pair.cu then csrc/device.cuh) starts with
+# the given prefix; for other sources or another tile the bench reports them as null.
 #  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
 #    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
 #  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
@@ -63,6 +63,16 @@ ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 # Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
 # accelerations 24 written (parent and grandparent indices are another 8 read).
 ALGO_BYTES_PER_BODY_EVAL = 64
+
+
+def tuned_pair_loop(M, m, r, v, repeats):
+    """The pair loop for this system: the tuner's fastest, when it beats the size rule's (the
+    library's default) by more than 2 %, the spread of single attempts; else the size rule's."""
+    best, ms = M.mstar_tune_pair_tile(m, r, v, repeats=repeats)
+    n = len(m)
+    rule = (32, 4) if n <= 512 else ((32, 1) if n <= 4096 else ((64, 1) if n <= 8192 else (128, 1)))
+    pick = best if ms[best] < 0.98 * ms[rule] else rule
+    return pick, {f"{k[0]}x{k[1]}": x for k, x in ms.items()}
 
 
 def pair_source_sha():
@@ -470,7 +480,8 @@ def run_small_configs(args, dev, M, W, torch):
     for key, name, t_end, steps in (("plummer64_to_t1", "plummer64", 1.0, 1 << 30),
                                     ("plummer2048_smbh_binary_200_steps", "plummer2048_smbh_binary", 10.0, 200)):
         m, r, v = W.workload(name)
-        g = M.Integrator(m, r, v, device=dev)
+        (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=3)
+        g = M.Integrator(m, r, v, device=dev, pair_tile=tile, pair_split=split)
         e0 = g.energy()["E"]
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
@@ -481,7 +492,8 @@ def run_small_configs(args, dev, M, W, torch):
         n = len(m)
         out[key] = {"n": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
                     "t_reached": st["t"], "gbs_steps_per_s": st["accepted"] / wall,
-                    "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0)}
+                    "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0),
+                    "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms}
         g.close()
     out["plummer64_to_t1_batch_of_one"] = run_batch_of_one(dev, M, W, torch)
     return out
@@ -548,7 +560,9 @@ def run_mstar(args):
         return
     m, r, v = W.workload(WORKLOAD)
     n = len(m)
-    g = M.Integrator(m, r, v, device=dev)
+    # the pair loop's tiling, timed on this system before anything is measured (setup)
+    (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=2)
+    g = M.Integrator(m, r, v, device=dev, pair_tile=tile, pair_split=split)
     stream = g.stream
     e_init = g.energy()["E"]
     t_end = 1.0
@@ -569,38 +583,50 @@ def run_mstar(args):
     fma_rate = max(M.mstar_fp64_fma_rate(stream.cuda_stream) for _ in range(3))
     probe_clocks = probe_clk.stop()
 
-    # ---- device-resident timed region
-    M.mstar_profile_enable(g.ctx, True)
-    launches0 = M.mstar_launch_count(g.ctx)
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    with torch.cuda.stream(stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    def run_steps(profile):
+        """args.steps steps bracketed by a barrier and a device synchronisation, timed with CUDA
+        events on the context's stream, the SM clock sampled meanwhile."""
+        if profile:
+            M.mstar_profile_enable(g.ctx, True)
+        launches0 = M.mstar_launch_count(g.ctx)
+        sampler = ClockSampler(local)
+        sampler.start()
+        time.sleep(0.3)
+        barrier(world)
+        torch.cuda.synchronize(dev)
         acc = rej = fev = 0
-        for _ in range(args.steps):
-            flush.zero_()
-            rc, st = g.step(t_end, 1)
-            acc += st["accepted"]
-            rej += st["rejected"]
-            fev += st["force_evals"]
-        e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    launches = M.mstar_launch_count(g.ctx) - launches0
-    prof = M.mstar_profile_read(g.ctx)
-    M.mstar_profile_enable(g.ctx, False)
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                flush.zero_()
+                rc, st = g.step(t_end, 1)
+                acc += st["accepted"]
+                rej += st["rejected"]
+                fev += st["force_evals"]
+            e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        clk = sampler.stop()
+        prof = None
+        if profile:
+            prof = M.mstar_profile_read(g.ctx)
+            M.mstar_profile_enable(g.ctx, False)
+        return e0.elapsed_time(e1), acc, rej, fev, M.mstar_launch_count(g.ctx) - launches0, clk, prof
+
+    # ---- device-resident timed region: the steps as the library runs them (each attempt one
+    # graph launch; from 1000 bodies each division on its own stream)
+    ms, acc, rej, fev, launches, clocks, _ = run_steps(False)
+    # ---- the same number of steps again with CUDA events around every pair-loop launch (the
+    # attempts issued kernel by kernel, level by level, so that each event pair times one
+    # launch alone): the pair kernel's mean launch time for the roofline
+    ms_prof, acc_p, rej_p, fev_p, _, clocks_prof, prof = run_steps(True)
     ms_max = reduce_max(ms, world, dev)
     pair_forces = float(fev) * n * (n - 1)
-    # energy error of the run so far (warm-up and timed steps from the initial state)
+    # energy error of the run so far (warm-up and both timed runs from the initial state)
     dE_c5 = abs((g.energy()["E"] - e_init) / e_init)
-    steps_c5 = args.warmup + acc
+    steps_c5 = args.warmup + acc + acc_p
     total_pf = reduce_sum(pair_forces, world, dev)
     total_steps = reduce_sum(float(acc), world, dev)
     value = total_pf / (ms_max * 1e-3)
@@ -634,10 +660,10 @@ def run_mstar(args):
     avg_ms = prof.pair_ms / max(prof.pair_launches, 1)
     pairs_per_launch = prof.pair_interactions / max(prof.pair_launches, 1)
     achieved = FLOPS_PER_UNORDERED_PAIR * pairs_per_launch / (avg_ms * 1e-3) / 1e12
-    clk_mhz = clocks.get("sm_mhz") or 2070.0
+    clk_mhz = clocks_prof.get("sm_mhz") or 2070.0
     fp64_peak = 2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6 / 1e12
     fp64_issue = DFMA_PER_CLK_PER_SM * NUM_SMS * clk_mhz * 1e6  # FP64 instructions/s the pipe takes
-    sha_ok = pair_source_sha() == PAIR_TILE_SRC_SHA
+    sha_ok = pair_source_sha() == PAIR_TILE_SRC_SHA and (tile, split) == (128, 1)
     slots_per_launch = prof.force_evals / max(prof.pair_launches, 1)
     # per launch, averaged over an attempt's launches (the pattern of slot counts is fixed)
     traffic = (sum(PAIR_TILE_DRAM_BYTES_BY_SLOTS[k] for k in ATTEMPT_SLOT_PATTERN) / len(ATTEMPT_SLOT_PATTERN)
@@ -649,7 +675,8 @@ def run_mstar(args):
                           "integer-pipe r^2, 1/r, m/r^3 and the exact fixed-point sum of m/r)",
                 "achieved_source": ("33 algorithmic FP64 flops per unordered far pair (each evaluated once and "
                                     "applied to both bodies) x N(N-1)/2 pairs x evaluations per launch / mean "
-                                    "CUDA-event launch time on the context stream"),
+                                    "CUDA-event launch time on the context stream, over a second run of the "
+                                    "timed steps with events around every pair launch (profiled_steps)"),
                 "peak_source": ("FP64 unit peak from unit counts and clocks (no FP64 entry among the measured "
                                 "peaks): 2 DFMA/clk/SM x 152 SMs x the SM clock sampled in the timed region x "
                                 "2 flops"),
@@ -658,7 +685,8 @@ def run_mstar(args):
                 "fp64_pipe_util": pairs_per_launch * FP64_INSTR_PER_PAIR / (avg_ms * 1e-3) / fp64_issue,
                 "fp64_pipe_util_source": ("pair rate x 9 FP64 instructions per pair / (2 per clk per SM x 152 "
                                           "SMs x sampled clock)"),
-                "fp64_pipe_util_ncu": (PAIR_TILE_FP64_PIPE_NCU if pair_source_sha() == PAIR_TILE_PIPE_SRC_SHA
+                "fp64_pipe_util_ncu": (PAIR_TILE_FP64_PIPE_NCU
+                                       if pair_source_sha() == PAIR_TILE_PIPE_SRC_SHA and (tile, split) == (128, 1)
                                        else None),
                 "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch by slot count, "
                                    "averaged over an attempt's 17 launches; null when the kernel's sources "
@@ -674,7 +702,10 @@ def run_mstar(args):
                 "probe_frac_of_unit_peak": (2.0 * fma_rate / 1e12) / (
                     2.0 * DFMA_PER_CLK_PER_SM * NUM_SMS * (probe_clocks.get("sm_mhz") or clk_mhz) * 1e6 / 1e12),
                 "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
-                "pair_kernel_share_of_step": prof.pair_ms / ms if ms > 0 else None,
+                "pair_kernel_share_of_step": prof.pair_ms / ms_prof if ms_prof > 0 else None,
+                "profiled_steps": {"ms": ms_prof, "accepted": acc_p, "rejected": rej_p,
+                                   "pair_forces_per_s": float(fev_p) * n * (n - 1) / (ms_prof * 1e-3),
+                                   "sm_mhz": clocks_prof.get("sm_mhz")},
                 # the whole timed step (every kernel of the hot path, rejected attempts and the
                 # L2 flush included) against the same peak
                 "whole_step_tflops": FLOPS_PER_UNORDERED_PAIR * 0.5 * pair_forces / (ms * 1e-3) / 1e12,
@@ -713,7 +744,8 @@ def run_mstar(args):
                "data": "synthetic",
                "config": {"workload": WORKLOAD_DESC, "n": n, "gbs_steps_per_bench_step": 1,
                           "l2": "flushed between steps (256 MiB write)",
-                          "parallelism": "replicas" if world > 1 else "single"},
+                          "parallelism": "replicas" if world > 1 else "single",
+                          "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms},
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
