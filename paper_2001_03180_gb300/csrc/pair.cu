@@ -473,6 +473,23 @@ k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const dou
     a[2 * (size_t)npad] = G * acc.az;
     um = m[p] * acc.u;
   }
+  if ((int)blockIdx.y >= keep_from) {
+    // the block's bodies' partials are read: drop their L2 lines, so that they are not
+    // written back to DRAM when later launches' partials evict them (every slot is written
+    // again before it is next read). NT x 4 runs of kBlock doubles, each starting on a
+    // 512-byte boundary; a line is dropped only where it lies below npad.
+    __syncthreads();
+    constexpr int kLinesPerRun = kBlock / 16;
+    const int b0 = blockIdx.x * kBlock;
+    const double* base = P + (size_t)slot * NT * 4 * npad + b0;
+    for (int l = threadIdx.x; l < NT * 4 * kLinesPerRun; l += kBlock) {
+      const int run = l / kLinesPerRun, line = l - run * kLinesPerRun;
+      if (b0 + 16 * line < npad) {
+        const double* a = base + (size_t)run * npad + 16 * line;
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
+      }
+    }
+  }
   const double s = block_sum(um, scratch);
   if (threadIdx.x == 0) Ublk[(size_t)slot * nblk + blockIdx.x] = G * s;
 }

@@ -98,3 +98,29 @@ def test_discarded_lines_are_the_tiles_slots(W, n):
             assert t * T <= off % npad < (t + 1) * T
             covered[off // 16] += 1
     assert np.all(covered == 1)
+
+
+@pytest.mark.parametrize("W,n", [(1, 33), (1, 2050), (2, 4097), (4, 10002), (4, 10239)])
+def test_finishing_pass_drops_only_its_blocks_lines(W, n):
+    """k_pair_finish drops the L2 lines of a deferred slot's partials once its 64-thread block
+    has read them: every line it names is 128-byte aligned, lies in the slot's partial buffer
+    and holds only bodies of that block, and the blocks together cover each run's first npad
+    bodies exactly once (no line is dropped twice or left behind)."""
+    T, kBlock = 32 * W, 64
+    npad = -(-n // T) * T
+    NT = npad // T
+    nblk = -(-npad // kBlock)
+    lines_per_run = kBlock // 16
+    covered = np.zeros(NT * 4 * npad // 16, np.int32)
+    for b in range(nblk):
+        b0 = b * kBlock
+        for l in range(NT * 4 * lines_per_run):
+            run, line = divmod(l, lines_per_run)
+            if b0 + 16 * line >= npad:
+                continue
+            off = run * npad + b0 + 16 * line
+            assert (off * 8) % 128 == 0
+            assert 0 <= off and off + 16 <= NT * 4 * npad
+            assert b0 <= off % npad and off % npad + 16 <= min(b0 + kBlock, npad)
+            covered[off // 16] += 1
+    assert np.all(covered == 1)
