@@ -85,12 +85,17 @@ typedef struct {
                         1, 2, 4 or 8, or 0 for the size rule (4 up to 512 bodies, else 1); the
                         other tiles take 1. Partial sums are added in warp order, so results
                         differ from the unsplit loop by rounding only. 0 */
-  int division_streams; /* how an attempt's k_fix divisions are issued: 1 level by level (one launch
-                        per kernel for every division active at that substep), 2 each division on
-                        its own stream, so that one division's small kernels overlap another's pair
-                        loop (attempts that record an adjoint trajectory or time the pair kernel use
-                        1), 0 for the size rule (2 from 1000 bodies, else 1). Results are the same
-                        either way. 0 */
+  int division_schedule; /* how an attempt's k_fix divisions are issued: 1 level by level (one
+                        launch per kernel for every division active at that substep), 2 each
+                        division on its own stream, so that one division's small kernels overlap
+                        another's pair loop, 3 each division in one CTA from its first drift to
+                        its last, pair sums included, all divisions in one launch (systems of at
+                        most 160 padded bodies; larger ones take the size rule), 0 for the size
+                        rule (3 up to 96 padded bodies, 2 from 1000 bodies, else 1). 1 and 2
+                        give bit-identical results; 3 sums the pair forces in another order, so
+                        its results differ from theirs by rounding. Attempts that record an
+                        adjoint trajectory or time the pair kernel, and the forward runs of the
+                        adjoint, use 1. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */
@@ -166,7 +171,9 @@ MSTAR_API int mstar_accelerations(mstar_ctx* ctx, double* a, double* U);
    warps, and unsplit tiles of 32, 64 and 128 bodies - (allocating and freeing its
    workspace), times `repeats` GBS step attempts of each with CUDA events on cuda_stream after
    one untimed attempt, and returns the fastest as *tile_out and *split_out, with the mean
-   attempt time of each in ms_out[4] (in that order; may be NULL). The attempts change no
+   attempt time of each in ms_out[4] (in that order; may be NULL). The attempts are those of
+   the multi-kernel schedules (division_schedule 1, or 2 from 1000 bodies, unless p asks for 1
+   or 2): one CTA per division has no tiles. The attempts change no
    state; the caller sets p.pair_tile and p.pair_split to the result for its own context. An
    attempt's work does not depend on its fictitious step, which is set to 1e-6 U. Errors as
    mstar_init. */

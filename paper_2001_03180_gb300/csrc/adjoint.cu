@@ -823,8 +823,12 @@ int mstar_adjoint_forward(mstar_ctx* c, double H, int nsteps, int checkpoint_eve
       rc = save_planes(c, a->ck + (size_t)(i / a->every) * 2 * st);
     }
     if (!rc) {
+      // every step level by level: the reverse sweep's recomputations, which record
+      // trajectories, then reproduce the checkpoints bit for bit
       c->traj = i >= last_first ? &a->tr[i - last_first] : nullptr;
+      c->levelled = true;
       rc = fixed_step(c, H);
+      c->levelled = false;
       c->traj = nullptr;
     }
   }
@@ -869,7 +873,9 @@ int mstar_step_adjoint(mstar_ctx* c, mstar_adjoint* a, const double* g_r, const 
       rc = set_planes(c, a->ck + (size_t)seg * 2 * st, a->tck[seg]);
       for (int q = 0; q < cnt && !rc; ++q) {
         c->traj = &a->tr[q];
+        c->levelled = true;
         rc = fixed_step(c, a->H);
+        c->levelled = false;
         c->traj = nullptr;
       }
       if (!rc) a->tr_seg = seg;

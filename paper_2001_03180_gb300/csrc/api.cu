@@ -117,7 +117,7 @@ bool valid_params(const mstar_params* p) {
   if (p->pair_tile != 0 && p->pair_tile != 32 && p->pair_tile != 64 && p->pair_tile != 128) return false;
   if (p->pair_split != 0 && p->pair_split != 1 && p->pair_split != 2 && p->pair_split != 4 && p->pair_split != 8)
     return false;
-  if (p->division_streams < 0 || p->division_streams > 2) return false;
+  if (p->division_schedule < 0 || p->division_schedule > 3) return false;
   return true;
 }
 
@@ -243,7 +243,14 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
 int issue_attempt_branched(mstar_ctx* c);
 
 int issue_attempt(mstar_ctx* c) {
-  if (c->branched && !c->traj && !c->prof) return issue_attempt_branched(c);
+  // attempts that record a trajectory, time the pair kernel or serve the adjoint go level by level
+  const bool plain = !c->traj && !c->prof && !c->levelled;
+  if (plain && c->div_cta) {
+    CK(launch_division_cta(c));
+    CK(launch_extrapolate(c));
+    return MSTAR_OK;
+  }
+  if (plain && c->branched) return issue_attempt_branched(c);
   const int K = c->K;
   const size_t st = (size_t)3 * c->npad;
   AdjTraj* tr = c->traj;
@@ -363,7 +370,7 @@ cudaGraphExec_t build_attempt_graph(mstar_ctx* c) {
     c->att_graph_off = true;
     return nullptr;
   }
-  c->att_graphs.push_back({c->traj, exec});
+  c->att_graphs.push_back({c->traj, c->levelled, exec});
   return exec;
 }
 
@@ -374,7 +381,7 @@ int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
   cudaGraphExec_t exec = nullptr;
   if (!c->prof && !c->att_graph_off) {
     for (const auto& ag : c->att_graphs)
-      if (ag.traj == c->traj) exec = ag.exec;
+      if (ag.traj == c->traj && ag.levelled == c->levelled) exec = ag.exec;
     if (!exec) exec = build_attempt_graph(c);
   }
   if (exec) {
@@ -503,7 +510,7 @@ void mstar_default_params(mstar_params* p) {
   p->mst_nsub = 0;
   p->pair_tile = 0;
   p->pair_split = 0;
-  p->division_streams = 0;
+  p->division_schedule = 0;
 }
 
 size_t mstar_workspace_bytes(int n, const mstar_params* p) {
@@ -576,7 +583,11 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   c->NT = s.NT;
   c->ntp = s.NT * (s.NT + 1) / 2;
   c->S = s.W != 1 ? 1 : (p->pair_split ? p->pair_split : (n <= 512 ? 4 : 1));
-  c->branched = p->division_streams ? p->division_streams == 2 : n >= 1000;
+  // how an attempt's divisions are issued: one CTA per division (pair sums included) for small
+  // systems, else a stream per division from 1000 bodies, else level by level
+  const int ds = p->division_schedule;
+  c->div_cta = (ds == 3 && c->npad <= kDivisionCtaMax) || (ds == 0 && c->npad <= kDivisionCtaRule);
+  c->branched = ds == 2 || ((ds == 0 || ds == 3) && !c->div_cta && n >= 1000);
   c->nblk = s.nblk;
   const size_t need = carve(s, nullptr, nullptr, nullptr);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -776,6 +787,9 @@ int mstar_tune_pair_tile(int n, const double* m, const double* r, const double* 
     cudaGetLastError();
     return MSTAR_ERR_CUDA;
   }
+  // the tiles serve the multi-kernel attempt (one CTA per division has no tiles): that is the
+  // one timed, on streams from 1000 bodies unless the parameters ask for levels
+  if (q.division_schedule != 1 && q.division_schedule != 2) q.division_schedule = n >= 1000 ? 2 : 1;
   const int tiles[4] = {32, 32, 64, 128}, splits[4] = {4, 1, 1, 1};
   double best = 0.0;
   int best_k = -1, rc = MSTAR_OK;

@@ -187,6 +187,58 @@ __device__ __forceinline__ void pair_scalars_int(double dx, double dy, double dz
   rinv = Rn ? u64_to_double(Rn, eR) : __longlong_as_double(0x7ff8000000000000LL);
 }
 
+struct NearAcc {
+  double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
+  // body p, partner q at separation d = r_q - r_p from edge-vector sums
+  __device__ __forceinline__ void add(int p, int q, double dx, double dy, double dz, double mq) {
+    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+    const double rinv = rsqrt_fp64(r2);
+    const double s = mq * ((rinv * rinv) * rinv);
+    ax = fma(s, dx, ax);
+    ay = fma(s, dy, ay);
+    az = fma(s, dz, az);
+    if (q > p) u = fma(mq, rinv, u);
+  }
+};
+
+// The near pairs of body p (Sec. 3.4, N_d <= 2: parent, children, grandparent, grandchildren,
+// siblings), each from the edge vectors X (3 planes) summed along the tree path between the
+// two bodies, added to acc.
+__device__ __forceinline__ void near_terms(int p, int npad, int n_d, const double* __restrict__ X,
+                                           const double* __restrict__ m, const int* __restrict__ parent,
+                                           const int* __restrict__ gp, const int* __restrict__ child_off,
+                                           const int* __restrict__ child_idx, NearAcc& acc) {
+  if (n_d < 1) return;
+  const double* Xx = X;
+  const double* Xy = Xx + npad;
+  const double* Xz = Xy + npad;
+  const int pp = parent[p];
+  const double xp = Xx[p], yp = Xy[p], zp = Xz[p];
+  if (pp >= 0) acc.add(p, pp, -xp, -yp, -zp, m[pp]);
+  const int c0 = child_off[p], c1 = child_off[p + 1];
+  for (int a = c0; a < c1; ++a) {
+    const int c = child_idx[a];
+    acc.add(p, c, Xx[c], Xy[c], Xz[c], m[c]);
+  }
+  if (n_d < 2) return;
+  const int g = gp[p];
+  if (g >= 0) acc.add(p, g, -(xp + Xx[pp]), -(yp + Xy[pp]), -(zp + Xz[pp]), m[g]);
+  for (int a = c0; a < c1; ++a) {
+    const int c = child_idx[a];
+    const double xc = Xx[c], yc = Xy[c], zc = Xz[c];
+    for (int b = child_off[c]; b < child_off[c + 1]; ++b) {
+      const int gc = child_idx[b];
+      acc.add(p, gc, Xx[gc] + xc, Xy[gc] + yc, Xz[gc] + zc, m[gc]);
+    }
+  }
+  if (pp >= 0) {
+    for (int b = child_off[pp]; b < child_off[pp + 1]; ++b) {
+      const int sib = child_idx[b];
+      if (sib != p) acc.add(p, sib, Xx[sib] - xp, Xy[sib] - yp, Xz[sib] - zp, m[sib]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------
 // Exact sums of positive terms on the integer pipe.
 //

@@ -81,7 +81,9 @@ struct mstar_ctx {
   int n = 0, npad = 0, K = 0, nslots = 0;
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
   int S = 1;                          // warps sharing a tile pair's partner steps (32-body tiles)
+  bool div_cta = false;               // attempts run each division in one CTA, in one launch
   bool branched = false;              // attempts issue each division on its own stream
+  bool levelled = false;              // attempts go level by level (the adjoint's forward runs)
   cudaStream_t br_stream[mstar::kMaxKfix] = {};  // those streams (created with the context)
   cudaEvent_t br_fork = nullptr, br_join[mstar::kMaxKfix] = {};
   int pair_defer = -1;  // trailing slots of a pair launch summed by the finishing pass (-1: unset)
@@ -110,6 +112,7 @@ struct mstar_ctx {
   // replayed on `stream`: one graph per trajectory record in use (nullptr: none)
   struct AttGraph {
     const mstar::AdjTraj* traj;
+    bool levelled;
     cudaGraphExec_t exec;
   };
   cudaStream_t cap = nullptr;
@@ -165,6 +168,16 @@ cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged r
 // their positions rebuilt
 constexpr int kLevelCtaMax = 256;
 cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau);
+// a whole attempt's divisions in one launch, one CTA of kDivisionCtaThreads threads each (pair
+// sums included): systems with npad <= kDivisionCtaMax (three tasks of 32 bodies per warp)
+constexpr int kDivisionCtaThreads = 512;
+constexpr int kDivisionCtaMax = 160;
+constexpr int kDivisionCtaRule = 96;   // the size rule's limit (division_schedule 0)
+constexpr size_t division_cta_smem(int npad) {
+  return (size_t)npad * (13 * sizeof(double) + sizeof(unsigned long long) + 5 * sizeof(int)) + sizeof(int) +
+         (size_t)(kDivisionCtaThreads / npad) * 4 * npad * sizeof(double);
+}
+cudaError_t launch_division_cta(mstar_ctx* c);
 
 cudaError_t launch_extrapolate(mstar_ctx* c);
 cudaError_t launch_moments(mstar_ctx* c);   // T, P, L partials of the state into d.mom

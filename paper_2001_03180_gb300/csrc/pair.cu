@@ -370,20 +370,6 @@ k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __r
   }
 }
 
-struct NearAcc {
-  double ax = 0.0, ay = 0.0, az = 0.0, u = 0.0;
-  // body p, partner q at separation d = r_q - r_p from edge-vector sums
-  __device__ __forceinline__ void add(int p, int q, double dx, double dy, double dz, double mq) {
-    const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-    const double rinv = rsqrt_fp64(r2);
-    const double s = mq * ((rinv * rinv) * rinv);
-    ax = fma(s, dx, ax);
-    ay = fma(s, dy, ay);
-    az = fma(s, dz, az);
-    if (q > p) u = fma(mq, rinv, u);
-  }
-};
-
 // The tile sums plus the near pairs of Sec. 3.4 (N_d <= 2: parent, child, grandparent,
 // grandchild, sibling), times G. Writes a (3 planes) and per-block sums of m_p * u_p, where
 // u_p sums m_q / r_pq over partners q > p (each unordered pair once). The trailing slots
@@ -436,37 +422,7 @@ k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const dou
       acc.az = q[2 * (size_t)npad];
       acc.u = q[3 * (size_t)npad];
     }
-    if (n_d >= 1) {
-      const double* Xx = sX + (size_t)slot * 3 * npad;
-      const double* Xy = Xx + npad;
-      const double* Xz = Xy + npad;
-      const int pp = parent[p];
-      const double xp = Xx[p], yp = Xy[p], zp = Xz[p];
-      if (pp >= 0) acc.add(p, pp, -xp, -yp, -zp, m[pp]);
-      const int c0 = child_off[p], c1 = child_off[p + 1];
-      for (int a = c0; a < c1; ++a) {
-        const int c = child_idx[a];
-        acc.add(p, c, Xx[c], Xy[c], Xz[c], m[c]);
-      }
-      if (n_d >= 2) {
-        const int g = gp[p];
-        if (g >= 0) acc.add(p, g, -(xp + Xx[pp]), -(yp + Xy[pp]), -(zp + Xz[pp]), m[g]);
-        for (int a = c0; a < c1; ++a) {
-          const int c = child_idx[a];
-          const double xc = Xx[c], yc = Xy[c], zc = Xz[c];
-          for (int b = child_off[c]; b < child_off[c + 1]; ++b) {
-            const int gc = child_idx[b];
-            acc.add(p, gc, Xx[gc] + xc, Xy[gc] + yc, Xz[gc] + zc, m[gc]);
-          }
-        }
-        if (pp >= 0) {
-          for (int b = child_off[pp]; b < child_off[pp + 1]; ++b) {
-            const int sib = child_idx[b];
-            if (sib != p) acc.add(p, sib, Xx[sib] - xp, Xy[sib] - yp, Xz[sib] - zp, m[sib]);
-          }
-        }
-      }
-    }
+    near_terms(p, npad, n_d, sX + (size_t)slot * 3 * npad, m, parent, gp, child_off, child_idx, acc);
     double* a = sa + (size_t)slot * 3 * npad + p;
     a[0] = G * acc.ax;
     a[(size_t)npad] = G * acc.ay;

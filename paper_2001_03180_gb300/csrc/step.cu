@@ -251,35 +251,47 @@ __device__ __forceinline__ double cta_sum(double x, double* scratch, double* out
   return *out;
 }
 
-// One substep level of every active division of a system that one CTA holds (npad <= 1024,
-// one body per thread; the step uses it up to kLevelCtaMax): the kick K(delta) of k_kick, the
-// velocities rebuilt by path sums and shifted to the centre-of-mass frame with their kinetic
-// energy (k_rebuild, k_shift), the
-// drift of k_drift, and, for the divisions that kick again (slot >= pos_lo), the positions
-// rebuilt and shifted - six launches of the multi-CTA path in one, with the CTA's barriers in
-// place of the kernel boundaries. The edge vectors are staged in shared memory for the
-// walks. The operations are those of the multi-CTA kernels; the centre-of-mass and kinetic
-// sums are CTA-wide instead of per 64-body block, so they round in another order.
-__global__ void __launch_bounds__(1024)
-k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__ par, double B, double Mtot,
-            int tau, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ bylev,
-            const double* __restrict__ sa, double* __restrict__ sV, double* __restrict__ sv, double* __restrict__ sX,
-            double* __restrict__ sr, const double* __restrict__ Ublk, int nblk, double* __restrict__ sc) {
-  extern __shared__ __align__(16) double lvl_sh[];  // 3 npad staged edge vectors, then npad parents
-  double* sW = lvl_sh;
-  int* sP = reinterpret_cast<int*>(lvl_sh + 3 * (size_t)npad);
-  __shared__ double scratch[32];
-  __shared__ double s_bc[8];
-  const int slot = slot_lo + blockIdx.x;
+// The Cartesian vectors of the edge vectors in sW (3 planes, shared) by path sums over the
+// staged parents sP, shifted to the centre-of-mass frame and written to w_out; returns
+// m w^2 of the thread's body (0 for none). One body per thread (blockDim >= n), in tree-level
+// order; every thread of the CTA calls it (it holds barriers).
+__device__ __forceinline__ double rebuild_cta(int n, int npad, double Mtot, const double* __restrict__ m,
+                                              const int* sP, const int* __restrict__ bylev, const double* sW,
+                                              double* w_out, double* scratch, double* s_bc) {
   const int tid = threadIdx.x;
-  const size_t st = (size_t)3 * npad;
-  double* V = sV + slot * st;
-  double* X = sX + slot * st;
-  const double* a = sa + slot * st;
-  const double H = par[0];
-  for (int u = tid; u < npad; u += blockDim.x) sP[u] = u < n ? parent[u] : -1;
-  sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &s_bc[0]);  // ends with a barrier
-  const double U = s_bc[0];
+  const int v = tid < n ? bylev[tid] : n;
+  double q[3] = {0.0, 0.0, 0.0};
+  if (v < n)
+    for (int u = v; sP[u] >= 0; u = sP[u]) {
+      q[0] = __dadd_rn(q[0], sW[u]);
+      q[1] = __dadd_rn(q[1], sW[npad + u]);
+      q[2] = __dadd_rn(q[2], sW[2 * (size_t)npad + u]);
+    }
+  const double mv = v < n ? m[v] : 0.0;
+  double com[3];
+  for (int c = 0; c < 3; ++c) com[c] = cta_sum(__dmul_rn(mv, q[c]), scratch, &s_bc[1 + c]);
+  double t2 = 0.0;
+  if (v < n) {
+    for (int c = 0; c < 3; ++c) {
+      q[c] = __dsub_rn(q[c], com[c] / Mtot);
+      w_out[(size_t)c * npad + v] = q[c];
+    }
+    t2 = __dmul_rn(mv, __dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
+  }
+  return t2;
+}
+
+// One substep level tau of division `slot` on the CTA: the kick K(delta) of k_kick with the
+// accelerations a (3 planes) and force function U, the velocities rebuilt by path sums and
+// shifted to the centre-of-mass frame with their kinetic energy (k_rebuild, k_shift), the
+// drift of k_drift, and, when `pos` (the division kicks again), the positions rebuilt and
+// shifted into r_out. Every thread of the CTA calls it; sW is 3 npad doubles of scratch.
+__device__ __forceinline__ void level_body(int n, int npad, int slot, bool pos, double H, double B, double Mtot,
+                                           int tau, double U, const double* a, const double* __restrict__ m,
+                                           const int* sP, const int* __restrict__ bylev, double* V, double* X,
+                                           double* sW, double* v_out, double* r_out, double* scratch, double* s_bc,
+                                           double* __restrict__ sc) {
+  const int tid = threadIdx.x;
   // K(delta): V_w += (delta / U) (a_w - a_parent(w))
   const double fk = (H / (double)(2 * (slot + 1))) / U;
   for (int w = tid; w < npad; w += blockDim.x) {
@@ -294,31 +306,8 @@ k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__
   }
   if (tid == 0) sc[slot * kScal + SC_U] = U;
   __syncthreads();
-  // the Cartesian vectors of the edge vectors in sW by path sums, shifted to the COM frame;
-  // returns sum m w^2 over the bodies
-  auto rebuild = [&](double* w_out) {
-    const int v = tid < n ? bylev[tid] : n;
-    double q[3] = {0.0, 0.0, 0.0};
-    if (v < n)
-      for (int u = v; sP[u] >= 0; u = sP[u]) {
-        q[0] = __dadd_rn(q[0], sW[u]);
-        q[1] = __dadd_rn(q[1], sW[npad + u]);
-        q[2] = __dadd_rn(q[2], sW[2 * (size_t)npad + u]);
-      }
-    const double mv = v < n ? m[v] : 0.0;
-    double com[3];
-    for (int c = 0; c < 3; ++c) com[c] = cta_sum(__dmul_rn(mv, q[c]), scratch, &s_bc[1 + c]);
-    double t2 = 0.0;
-    if (v < n) {
-      for (int c = 0; c < 3; ++c) {
-        q[c] = __dsub_rn(q[c], com[c] / Mtot);
-        w_out[(size_t)c * npad + v] = q[c];
-      }
-      t2 = __dmul_rn(mv, __dadd_rn(__dadd_rn(__dmul_rn(q[0], q[0]), __dmul_rn(q[1], q[1])), __dmul_rn(q[2], q[2])));
-    }
-    return t2;
-  };
-  const double T = 0.5 * cta_sum(rebuild(sv + slot * st), scratch, &s_bc[4]);
+  const double T = 0.5 * cta_sum(rebuild_cta(n, npad, Mtot, m, sP, bylev, sW, v_out, scratch, s_bc), scratch,
+                                 &s_bc[4]);
   // D(h): X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift
   const int nk = 2 * (slot + 1);
   const double delta = H / (double)nk;
@@ -336,7 +325,320 @@ k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__
     sc[slot * kScal + SC_T_KIN] = T;
   }
   __syncthreads();
-  if (slot >= pos_lo) rebuild(sr + slot * st);
+  if (pos) rebuild_cta(n, npad, Mtot, m, sP, bylev, sW, r_out, scratch, s_bc);
+}
+
+// One substep level of every active division of a system that one CTA holds (npad <= 1024,
+// one body per thread; the step uses it up to kLevelCtaMax): level_body with the
+// accelerations and force-function partials of the pair kernels - six launches of the
+// multi-CTA path in one, with the CTA's barriers in place of the kernel boundaries. The
+// edge vectors are staged in shared memory for the walks. The operations are those of the
+// multi-CTA kernels; the centre-of-mass and kinetic sums are CTA-wide instead of per 64-body
+// block, so they round in another order.
+__global__ void __launch_bounds__(1024)
+k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__ par, double B, double Mtot,
+            int tau, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ bylev,
+            const double* __restrict__ sa, double* __restrict__ sV, double* __restrict__ sv, double* __restrict__ sX,
+            double* __restrict__ sr, const double* __restrict__ Ublk, int nblk, double* __restrict__ sc) {
+  extern __shared__ __align__(16) double lvl_sh[];  // 3 npad staged edge vectors, then npad parents
+  double* sW = lvl_sh;
+  int* sP = reinterpret_cast<int*>(lvl_sh + 3 * (size_t)npad);
+  __shared__ double scratch[32];
+  __shared__ double s_bc[8];
+  const int slot = slot_lo + blockIdx.x;
+  const size_t st = (size_t)3 * npad;
+  for (int u = threadIdx.x; u < npad; u += blockDim.x) sP[u] = u < n ? parent[u] : -1;
+  sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &s_bc[0]);  // ends with a barrier
+  level_body(n, npad, slot, slot >= pos_lo, par[0], B, Mtot, tau, s_bc[0], sa + slot * st, m, sP, bylev,
+             sV + slot * st, sX + slot * st, sW, sv + slot * st, sr + slot * st, scratch, s_bc, sc);
+}
+
+// Sum over a warp (lane 0 holds it): a fixed shuffle tree.
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// A whole attempt's divisions, one CTA each (systems with npad <= kDivisionCtaMax): the first
+// half drift of k_init_drift, then the division's n_k substeps, each the pair sums of Sec. 3.4
+// followed by the kick, velocity rebuild, drift and position rebuild of the multi-kernel path.
+// One launch replaces the 3 + 3 n_k launches of the level-by-level path.
+//
+// The division's state stays in shared memory for the whole attempt. An FP64 instruction
+// occupies its SM sub-partition's FP64 unit for about 64 cycles however few of the warp's lanes
+// are active, so the serial parts give each warp one component of 32 bodies (thread
+// (c, i) = (t / npad, t % npad) for t < 3 npad): the tree walks, kicks, drifts and
+// centre-of-mass sums of the three components run on different warps, and the per-warp
+// shuffle sums are added in warp order by one thread.
+//
+// Pair sums: thread (chunk ch, body i) sums i's far partners j in the ch-th of nch equal ranges
+// (each ordered far pair is evaluated on its own side, with the integer-pipe scalars of
+// k_pair_tiles) and the near partners of i (parent, children, grandparent, grandchildren,
+// siblings for N_d = 2, from the edge vectors) whose place in that list is ch modulo nch, with
+// the same scalars; the chunks are added in order ch = 0, 1, ... The sum of m_j / r over
+// partners j > i is exact within a chunk (UAcc).
+__global__ void __launch_bounds__(kDivisionCtaThreads)
+k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double* __restrict__ par, double B,
+               double Mtot, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ gp,
+               const int* __restrict__ child_off, const int* __restrict__ child_idx, const int* __restrict__ bylev,
+               const double* __restrict__ X0, const double* __restrict__ V0, double* __restrict__ sX,
+               double* __restrict__ sV, double* __restrict__ sc) {
+  // shared: edge positions X and velocities V, Cartesian positions sx, accelerations sA (3 npad
+  // each), masses (npad), chunk partials (nch x 4 x npad), mass significands (npad), then mass
+  // exponents, parents, grandparents, children offsets (npad + 1) and children (npad)
+  extern __shared__ __align__(16) double div_sh[];
+  double* X = div_sh;
+  double* V = X + 3 * (size_t)npad;
+  double* sx = V + 3 * (size_t)npad;
+  double* sA = sx + 3 * (size_t)npad;
+  double* sm = sA + 3 * (size_t)npad;
+  double* part = sm + npad;
+  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)nch * 4 * npad);
+  int* sme = reinterpret_cast<int*>(smm + npad);
+  int* sP = sme + npad;
+  int* sG = sP + npad;
+  int* sCo = sG + npad;
+  int* sCi = sCo + npad + 1;
+  __shared__ double red[kDivisionCtaThreads / 32];
+  __shared__ double s_val[4];
+  const int slot = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nb = npad >> 5;  // warps per component
+  const size_t st = (size_t)3 * npad;
+  const double H = par[0], t0 = par[1];
+  const double T0 = sc[K * kScal + SC_T_KIN];
+  const int nk = 2 * (slot + 1);
+  const double delta = H / (double)nk;
+  for (int u = tid; u < npad; u += blockDim.x) {
+    const bool body = u < n;
+    sP[u] = body ? parent[u] : -1;
+    sG[u] = body ? gp[u] : -1;
+    sCi[u] = body ? child_idx[u] : 0;
+    const double mu = m[u];
+    sm[u] = mu;
+    const MassSplit ms = mass_split(mu);
+    smm[u] = ms.m;
+    sme[u] = ms.e;
+    if (!body)  // the padding's positions, which no rebuild writes
+      for (int c = 0; c < 3; ++c) sx[(size_t)c * npad + u] = 0.0;
+  }
+  for (int u = tid; u <= npad; u += blockDim.x) sCo[u] = child_off[u < n ? u : n];
+  // the serial phases' task: component c of the body v at tree-level rank i
+  const bool task = tid < 3 * npad;
+  const int c = tid / npad, ti = tid - (tid / npad) * npad;
+  const int v = (task && ti < n) ? bylev[ti] : n;
+  const double mv = v < n ? m[v] : 0.0;
+  // D(delta/2) from the step start (k_init_drift): X = X0 + f V0, V = V0
+  const double f0 = (0.5 * delta) / (T0 + B);
+  if (task) {
+    const size_t o = (size_t)c * npad + ti;
+    X[o] = madd(X0[o], f0, V0[o]);
+    V[o] = V0[o];
+  }
+  double t_phys = t0 + f0, T = T0, U = 0.0;
+  __syncthreads();
+
+  // Cartesian vectors of the edge vectors W (one component per task) by path sums, shifted to
+  // the centre-of-mass frame; returns the task's m v q^2 term (0 for none)
+  auto rebuild = [&](const double* W, double* out) {
+    double q = 0.0;
+    if (v < n)
+      for (int u = v; sP[u] >= 0; u = sP[u]) q = __dadd_rn(q, W[(size_t)c * npad + u]);
+    if (task) {  // warp-uniform (3 npad is a multiple of 32)
+      const double s = warp_sum(__dmul_rn(mv, q));
+      if (lane == 0) red[warp] = s;
+    }
+    __syncthreads();
+    if (tid < 3) {
+      double com = red[tid * nb];
+      for (int w = 1; w < nb; ++w) com += red[tid * nb + w];
+      s_val[tid] = com / Mtot;
+    }
+    __syncthreads();
+    double t2 = 0.0;
+    if (v < n) {
+      q = __dsub_rn(q, s_val[c]);
+      if (out) out[(size_t)c * npad + v] = q;
+      t2 = __dmul_rn(mv, __dmul_rn(q, q));
+    }
+    __syncthreads();  // s_val and red are free again
+    return t2;
+  };
+  // T = sum of the tasks' m v^2 terms (warp order) / 2, and the drift factor f = h / (T + B)
+  // of substep tau, to every thread (s_val[3], s_val[0])
+  auto kinetic = [&](double x, int tau) {
+    if (task) {
+      const double s = warp_sum(x);
+      if (lane == 0) red[warp] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = red[0];
+      for (int w = 1; w < 3 * nb; ++w) a += red[w];
+      const double Tk = 0.5 * a;
+      s_val[3] = Tk;
+      s_val[0] = ((tau == nk) ? 0.5 * delta : delta) / (Tk + B);
+    }
+    __syncthreads();
+    return s_val[3];
+  };
+
+  rebuild(X, sx);
+  const int pi_ch = tid / npad, i = tid - pi_ch * npad;
+  const bool pair_thread = pi_ch < nch;
+  const int j_lo = (pi_ch * npad) / nch, j_hi = ((pi_ch + 1) * npad) / nch;
+  const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
+  for (int tau = 1; tau <= nk; ++tau) {
+    __syncthreads();  // sx holds the rebuilt positions
+    if (pair_thread) {
+      const double xi = sx[i], yi = sx[npad + i], zi = sx[2 * npad + i];
+      const MassSplit msi{smm[i], sme[i]};
+      const int pi = sP[i], gpi = sG[i];
+      const bool i_pad = i >= n;
+      double ax = 0.0, ay = 0.0, az = 0.0;
+      UAcc uacc;
+      bool ubad = false;
+      unsigned long long Rn;
+      int eR;
+      double sj, si;
+      // far partners of the chunk
+      for (int j = j_lo; j < j_hi; ++j) {
+        const int pj = sP[j], gj = sG[j];
+        bool masked = i_pad | (j >= n) | (j == i);
+        masked |= nd1 & ((pi == j) | (pj == i));
+        masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
+        const double dx = sx[j] - xi, dy = sx[npad + j] - yi, dz = sx[2 * npad + j] - zi;
+        const unsigned long long mjm = smm[j];
+        const int mje = sme[j];
+        pair_scalars_core(dx, dy, dz, MassSplit{mjm, mje}, msi, Rn, eR, sj, si);
+        if (!masked) {
+          ubad |= Rn == 0ull;
+          ax = fma(sj, dx, ax);
+          ay = fma(sj, dy, ay);
+          az = fma(sj, dz, az);
+          if (j > i) uacc.add(__umul64hi(mjm, Rn), mje + eR + 64);
+        }
+      }
+      // near partners number k = ch, ch + nch, ... of the list parent, children, grandparent,
+      // grandchildren, siblings; separation d = r_q - r_i from the edge vectors
+      if (nd1 && !i_pad) {
+        int kc = 0;  // partners seen so far, mod nch
+        const double* Xx = X;
+        const double* Xy = X + npad;
+        const double* Xz = X + 2 * (size_t)npad;
+        // partner q at r_q - r_i = (+-X_a) + (+-X_b) (no second term for b < 0); the signs are
+        // flipped on the bit patterns
+        auto flip = [](double x, bool neg) {
+          return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
+        };
+        auto near = [&](int q, int a, bool na, int b, bool nb) {
+          const bool mine = kc == pi_ch;
+          kc = kc + 1 == nch ? 0 : kc + 1;
+          if (!mine) return;
+          double dx = flip(Xx[a], na), dy = flip(Xy[a], na), dz = flip(Xz[a], na);
+          if (b >= 0) {
+            dx = __dadd_rn(dx, flip(Xx[b], nb));
+            dy = __dadd_rn(dy, flip(Xy[b], nb));
+            dz = __dadd_rn(dz, flip(Xz[b], nb));
+          }
+          pair_scalars_core(dx, dy, dz, MassSplit{smm[q], sme[q]}, msi, Rn, eR, sj, si);
+          ubad |= Rn == 0ull;
+          ax = fma(sj, dx, ax);
+          ay = fma(sj, dy, ay);
+          az = fma(sj, dz, az);
+          if (q > i) uacc.add(__umul64hi(smm[q], Rn), sme[q] + eR + 64);
+        };
+        if (pi >= 0) near(pi, i, true, -1, false);
+        const int c0 = sCo[i], c1 = sCo[i + 1];
+        for (int a = c0; a < c1; ++a) {
+          const int ch = sCi[a];
+          near(ch, ch, false, -1, false);
+        }
+        if (nd2) {
+          if (gpi >= 0) near(gpi, i, true, pi, true);
+          for (int a = c0; a < c1; ++a) {
+            const int ch = sCi[a];
+            for (int b = sCo[ch]; b < sCo[ch + 1]; ++b) {
+              const int gc = sCi[b];
+              near(gc, gc, false, ch, false);
+            }
+          }
+          if (pi >= 0)
+            for (int b = sCo[pi]; b < sCo[pi + 1]; ++b) {
+              const int sb = sCi[b];
+              if (sb != i) near(sb, sb, false, i, true);
+            }
+        }
+      }
+      double* q = part + (size_t)pi_ch * 4 * npad + i;
+      q[0] = ax;
+      q[npad] = ay;
+      q[2 * (size_t)npad] = az;
+      q[3 * (size_t)npad] = ubad ? __longlong_as_double(0x7ff8000000000000LL) : uacc.value();
+    }
+    __syncthreads();
+    // chunk sums: component c of the accelerations (times G) and, on the c = 0 tasks, the
+    // body's m_i u_i
+    double um = 0.0;
+    if (task) {
+      const double* q = part + (size_t)c * npad + ti;
+      double s = q[0];
+      for (int k = 1; k < nch; ++k) s += q[(size_t)k * 4 * npad];
+      sA[(size_t)c * npad + ti] = G * s;
+      if (c == 0 && ti < n) {
+        const double* qu = part + 3 * (size_t)npad + ti;
+        double u = qu[0];
+        for (int k = 1; k < nch; ++k) u += qu[(size_t)k * 4 * npad];
+        um = sm[ti] * u;
+      }
+    }
+    {
+      if (warp < nb) {
+        const double s = warp_sum(um);
+        if (lane == 0) red[warp] = s;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double a = red[0];
+        for (int w = 1; w < nb; ++w) a += red[w];
+        const double Ug = G * a;
+        s_val[3] = Ug;
+        s_val[0] = delta / Ug;
+      }
+      __syncthreads();
+      U = s_val[3];
+    }
+    // K(delta): V_w += (delta / U) (a_w - a_parent(w))
+    if (task) {
+      const int p = sP[ti];
+      if (p >= 0) {
+        const size_t o = (size_t)c * npad;
+        V[o + ti] = madd(V[o + ti], s_val[0], __dsub_rn(sA[o + ti], sA[o + p]));
+      }
+    }
+    __syncthreads();
+    // velocities rebuilt and shifted; T = sum m v^2 / 2
+    // D(h): X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift
+    T = kinetic(rebuild(V, nullptr), tau);
+    const double fd = s_val[0];
+    if (task) {
+      const size_t o = (size_t)c * npad + ti;
+      X[o] = madd(X[o], fd, V[o]);
+    }
+    t_phys += fd;
+    __syncthreads();
+    if (tau < nk) rebuild(X, sx);
+  }
+  // the division's final state and scalars for the extrapolation
+  if (task) {
+    const size_t o = (size_t)c * npad + ti;
+    sX[slot * st + o] = X[o];
+    sV[slot * st + o] = V[o];
+  }
+  if (tid == 0) {
+    sc[slot * kScal + SC_T_PHYS] = t_phys;
+    sc[slot * kScal + SC_T_KIN] = T;
+    sc[slot * kScal + SC_U] = U;
+  }
 }
 
 // Shift to the centre-of-mass frame: w -= (sum m w) / M; optionally block sums of m w^2.
@@ -560,6 +862,20 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   k_shift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->Mtot, w, c->d.m, comblk_base,
                                          want_T ? Tblk_base : nullptr, c->nblk);
   MSTAR_LAUNCHED(c);
+  return cudaGetLastError();
+}
+
+// Every division of an attempt, from the first half drift to the last drift, in one launch
+// with one CTA per division (npad <= kDivisionCtaMax).
+cudaError_t launch_division_cta(mstar_ctx* c) {
+  const int npad = c->npad;
+  const int nch = kDivisionCtaThreads / npad;  // >= 3 (npad <= kDivisionCtaMax)
+  const size_t smem = division_cta_smem(npad);
+  k_division_cta<<<c->K, kDivisionCtaThreads, smem, c->stream>>>(
+      c->n, npad, c->K, nch, c->p.n_d, c->p.G, c->d.res + 4, c->B, c->Mtot, c->d.m, c->d.parent, c->d.gp,
+      c->d.child_off, c->d.child_idx, c->d.bylev, c->d.X0, c->d.V0, c->d.sX, c->d.sV, c->d.sc);
+  MSTAR_LAUNCHED(c);
+  c->force_evals += (long long)c->K * (c->K + 1);  // sum of n_k = 2 (k + 1) over the divisions
   return cudaGetLastError();
 }
 

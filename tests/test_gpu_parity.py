@@ -201,7 +201,7 @@ def test_division_streams_give_the_same_steps(n):
     m, r, v = W.plummer_smbh_binary(n - 2, 6)
     out = []
     for mode in (1, 2):
-        g = M.Integrator(m, r, v, division_streams=mode)
+        g = M.Integrator(m, r, v, division_schedule=mode)
         rc, st = g.step(10.0, 3)
         assert rc == 0
         S = g.state()
@@ -209,6 +209,67 @@ def test_division_streams_give_the_same_steps(n):
         g.close()
     (r1, v1, t1, a1, j1), (r2, v2, t2, a2, j2) = out
     assert np.array_equal(r1, r2) and np.array_equal(v1, v2) and t1 == t2 and (a1, j1) == (a2, j2)
+
+
+DIV_CTA_CASES = [("two", 0.6, 2), ("pyth", 25.0, 2), ("plummer64", 0.05, 2), ("plummer64", 2e-3, 2),
+                 ("plummer64", 0.05, 0), ("plummer64", 0.05, 1), ("p33", 0.06, 2), ("p100", 0.025, 2),
+                 ("p100", 0.025, 0), ("p129", 0.025, 2), ("p160", 0.03, 2), ("p160", 0.03, 1)]
+
+
+def div_cta_system(name):
+    if name in SYS:
+        return SYS[name]
+    return W.plummer(int(name[1:]), 8)
+
+
+@pytest.mark.parametrize("name,H,n_d", DIV_CTA_CASES)
+def test_division_cta_attempt_matches_oracle(name, H, n_d):
+    """One CTA per division for a whole attempt (pair sums, near pairs from the edge vectors,
+    kicks, rebuilds and drifts in one launch): the attempt's state agrees with the oracle to
+    1e-12, as the multi-kernel path does, for 2 ... 160 bodies (the last chunk of partners and
+    the padding ragged) and every near rule."""
+    m, r, v = div_cta_system(name)
+    g = M.Integrator(m, r, v, division_schedule=3, n_d=n_d)
+    o = O.System(m, r, v, n_d=n_d)
+    gs = g.attempt(H)
+    os_ = o.attempt(H)
+    assert relerr(gs["r"], os_["r"]) < 1e-12
+    assert relerr(gs["v"], os_["v"]) < 1e-12
+    assert abs(gs["t"] - os_["t"]) <= 1e-12 * abs(os_["t"])
+    check_eps(gs["eps"], os_["eps"])
+    g.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 64, 65, 128, 129, 160])
+def test_division_cta_agrees_with_the_level_path(n):
+    """The one-CTA schedule and the level-by-level schedule sum the pair forces in different
+    orders, so their attempts agree to rounding (1e-12) at a step well inside the tolerance.
+    (Controlled steps are not compared: where eps sits near its rounding floor, the next step
+    size follows that rounding.)"""
+    m, r, v = (W.kepler_binary(seed=1) if n == 2 else W.plummer(n, 8))
+    out = []
+    for mode in (1, 3):
+        g = M.Integrator(m, r, v, division_schedule=mode)
+        out.append(g.attempt(1e-3))
+        g.close()
+    a1, a3 = out
+    assert relerr(a3["r"], a1["r"]) < 1e-12 and relerr(a3["v"], a1["v"]) < 1e-12
+    assert abs(a3["t"] - a1["t"]) <= 1e-12 * abs(a1["t"])
+
+
+def test_division_cta_beyond_its_size_takes_the_size_rule():
+    """division_schedule 3 on a system of more than 160 padded bodies runs the size rule's
+    schedule: the same steps as the default."""
+    m, r, v = W.plummer(161, 8)
+    out = []
+    for mode in (0, 3):
+        g = M.Integrator(m, r, v, division_schedule=mode)
+        g.step(10.0, 2)
+        out.append(g.state())
+        g.close()
+    assert np.array_equal(out[0]["r"], out[1]["r"]) and np.array_equal(out[0]["v"], out[1]["v"])
+    with pytest.raises(M.MstarError):
+        M.Integrator(m, r, v, division_schedule=4)
 
 
 @pytest.mark.parametrize("n_d", [0, 1, 2])
@@ -499,14 +560,14 @@ def test_lidov_kozai_first_cycles_match_oracle():
 
 def test_graph_replay_matches_direct_launches_and_contexts_do_not_interfere():
     """An attempt is replayed as a captured CUDA graph; with profiling on it is launched kernel
-    by kernel. Both must give bit-identical results. Two contexts with different k_fix
+    by kernel (level by level in both). Both must give bit-identical results. Two contexts with different k_fix
     (6 and 8), used in alternation, must each still match the oracle: they share the module's
     constant Neville factors, which do not depend on k_fix."""
     m, r, v = W.workload("plummer64")
     H = 0.05
     res = []
     for prof in (False, True):
-        g = M.Integrator(m, r, v)
+        g = M.Integrator(m, r, v, division_schedule=1)
         M.mstar_profile_enable(g.ctx, prof)
         a1 = g.attempt(H)
         a2 = g.attempt(0.5 * H)
