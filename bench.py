@@ -55,9 +55,9 @@ L2_FLUSH_BYTES = 256 << 20
 #  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
 #    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
 #  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
-PAIR_TILE_SRC_SHA = "23e8af75ea0546f9"
-PAIR_TILE_PIPE_SRC_SHA = "2e6acdc6a5f9b120"
-PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 3.669e6, 2: 0.762e6, 3: 15.006e6, 4: 21.056e6, 5: 25.432e6, 6: 29.190e6, 7: 34.097e6, 8: 41.687e6}
+PAIR_TILE_SRC_SHA = "dd6ba7c4c9d94726"
+PAIR_TILE_PIPE_SRC_SHA = "dd6ba7c4c9d94726"
+PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 1.001e6, 2: 0.228e6, 3: 0.676e6, 4: 1.710e6, 5: 2.687e6, 6: 3.687e6, 7: 4.999e6, 8: 7.308e6}
 PAIR_TILE_FP64_PIPE_NCU = 0.870
 ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 # Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
@@ -480,7 +480,10 @@ def run_small_configs(args, dev, M, W, torch):
     for key, name, t_end, steps in (("plummer64_to_t1", "plummer64", 1.0, 1 << 30),
                                     ("plummer2048_smbh_binary_200_steps", "plummer2048_smbh_binary", 10.0, 200)):
         m, r, v = W.workload(name)
-        (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=3)
+        if len(m) <= 96:  # one CTA per division (the library's size rule): no pair tiles to tune
+            (tile, split), tile_ms = (0, 0), None
+        else:
+            (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=3)
         g = M.Integrator(m, r, v, device=dev, pair_tile=tile, pair_split=split)
         e0 = g.energy()["E"]
         torch.cuda.synchronize(dev)
@@ -493,6 +496,8 @@ def run_small_configs(args, dev, M, W, torch):
         out[key] = {"n": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
                     "t_reached": st["t"], "gbs_steps_per_s": st["accepted"] / wall,
                     "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0),
+                    "division_schedule": ("one CTA per division" if len(m) <= 96 else
+                                          ("a stream per division" if len(m) >= 1000 else "level by level")),
                     "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms}
         g.close()
     out["plummer64_to_t1_batch_of_one"] = run_batch_of_one(dev, M, W, torch)
@@ -501,8 +506,8 @@ def run_small_configs(args, dev, M, W, torch):
 
 def run_batch_of_one(dev, M, W, torch):
     """Plummer 64 to t = 1 as a batch of one system: each attempt is one graph launch of the
-    batched kernels (the system in one CTA, or over four with a split schedule) in place of the
-    ~130 launches of a single-system attempt. The schedule comes from the autotuner, run
+    batched kernels (the system in one CTA, or over four with a split schedule). The schedule
+    comes from the autotuner, run
     beforehand on a snapshot and not timed. The energy error is taken by mstar_energy on a
     context made from the end state."""
     m, r, v = W.workload("plummer64")
@@ -745,7 +750,9 @@ def run_mstar(args):
                "config": {"workload": WORKLOAD_DESC, "n": n, "gbs_steps_per_bench_step": 1,
                           "l2": "flushed between steps (256 MiB write)",
                           "parallelism": "replicas" if world > 1 else "single",
-                          "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms},
+                          "division_schedule": ("one CTA per division" if len(m) <= 96 else
+                                          ("a stream per division" if len(m) >= 1000 else "level by level")),
+                    "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms},
                "gbs_steps_per_s": total_steps / (ms_max * 1e-3), "attempts": acc + rej, "rejected": rej,
                "force_evals": fev, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                "gpu_launches": launches, "clocks": clocks, "batched": batched,
