@@ -622,7 +622,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
     return code;
   };
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
-      prepare_rebuild(c) != cudaSuccess)
+      prepare_rebuild(c) != cudaSuccess || prepare_division_cta(c) != cudaSuccess)
     return bail(MSTAR_ERR_CUDA);
   if (c->branched) {  // the streams and events of the per-division attempt graph
     if (cudaEventCreateWithFlags(&c->br_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MSTAR_ERR_CUDA);

@@ -169,14 +169,18 @@ cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged r
 constexpr int kLevelCtaMax = 256;
 cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau);
 // a whole attempt's divisions in one launch, one CTA of kDivisionCtaThreads threads each (pair
-// sums included): systems with npad <= kDivisionCtaMax (three tasks of 32 bodies per warp)
+// sums included): systems with npad <= kDivisionCtaMax (three tasks of 32 bodies per warp, at
+// most 15 tile pairs of 32 bodies)
 constexpr int kDivisionCtaThreads = 512;
+constexpr int kDivisionCtaTasks = kDivisionCtaThreads / 32;
 constexpr int kDivisionCtaMax = 160;
 constexpr int kDivisionCtaRule = 96;   // the size rule's limit (division_schedule 0)
 constexpr size_t division_cta_smem(int npad) {
   return (size_t)npad * (13 * sizeof(double) + sizeof(unsigned long long) + 5 * sizeof(int)) + sizeof(int) +
-         (size_t)(kDivisionCtaThreads / npad) * 4 * npad * sizeof(double);
+         (size_t)kDivisionCtaTasks * 7 * 32 * sizeof(double);
 }
+// at context creation: the division kernel's shared memory for this size (above 48 KB needs it)
+cudaError_t prepare_division_cta(mstar_ctx* c);
 cudaError_t launch_division_cta(mstar_ctx* c);
 
 cudaError_t launch_extrapolate(mstar_ctx* c);

@@ -371,20 +371,25 @@ __device__ __forceinline__ double warp_sum(double x) {
 // centre-of-mass sums of the three components run on different warps, and the per-warp
 // shuffle sums are added in warp order by one thread.
 //
-// Pair sums: thread (chunk ch, body i) sums i's far partners j in the ch-th of nch equal ranges
-// (each ordered far pair is evaluated on its own side, with the integer-pipe scalars of
-// k_pair_tiles) and the near partners of i (parent, children, grandparent, grandchildren,
-// siblings for N_d = 2, from the edge vectors) whose place in that list is ch modulo nch, with
-// the same scalars; the chunks are added in order ch = 0, 1, ... The sum of m_j / r over
-// partners j > i is exact within a chunk (UAcc).
+// Pair sums: the symmetric tiling of k_pair_tiles inside the CTA. The nb = npad / 32 body tiles
+// form nb (nb + 1) / 2 tile pairs (I <= J); each tile pair's partner steps (32, or 16 on the
+// diagonal) are split into S chunks, and warp w takes chunk w of the P S tasks. A task's lanes are
+// the bodies of tile I; at step k lane l meets body (l + k) mod 32 of tile J, so the 32 partner
+// sums are updated without conflicts in the task's shared j-side planes. Each unordered far pair
+// is evaluated once, with the integer-pipe scalars of k_pair_tiles. The task also takes its
+// share of its bodies' near partners (parent, children, grandparent, grandchildren, siblings for
+// N_d = 2, from the edge vectors): partner number k of body i goes to the task of rank k modulo
+// the (nb - I) S tasks whose i-side is tile I. A body then adds its tasks' partials in task
+// order. The sum of m_j / r is exact within a task (UAcc).
 __global__ void __launch_bounds__(kDivisionCtaThreads)
-k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double* __restrict__ par, double B,
+k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restrict__ par, double B,
                double Mtot, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ gp,
                const int* __restrict__ child_off, const int* __restrict__ child_idx, const int* __restrict__ bylev,
                const double* __restrict__ X0, const double* __restrict__ V0, double* __restrict__ sX,
                double* __restrict__ sV, double* __restrict__ sc) {
   // shared: edge positions X and velocities V, Cartesian positions sx, accelerations sA (3 npad
-  // each), masses (npad), chunk partials (nch x 4 x npad), mass significands (npad), then mass
+  // each), masses (npad), the tasks' partials (kDivisionCtaThreads / 32 tasks x 7 planes of 32:
+  // the i-side ax, ay, az, m/r sums, then the j-side sums), mass significands (npad), then mass
   // exponents, parents, grandparents, children offsets (npad + 1) and children (npad)
   extern __shared__ __align__(16) double div_sh[];
   double* X = div_sh;
@@ -393,7 +398,7 @@ k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double*
   double* sA = sx + 3 * (size_t)npad;
   double* sm = sA + 3 * (size_t)npad;
   double* part = sm + npad;
-  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)nch * 4 * npad);
+  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)kDivisionCtaTasks * 7 * 32);
   int* sme = reinterpret_cast<int*>(smm + npad);
   int* sP = sme + npad;
   int* sG = sP + npad;
@@ -483,13 +488,29 @@ k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double*
   };
 
   rebuild(X, sx);
-  const int pi_ch = tid / npad, i = tid - pi_ch * npad;
-  const bool pair_thread = pi_ch < nch;
-  const int j_lo = (pi_ch * npad) / nch, j_hi = ((pi_ch + 1) * npad) / nch;
+  // the pair-sum tasks: tile pairs (in tile_pair order) times S chunks of partner steps
+  const int ntp = nb * (nb + 1) / 2;
+  const int S = kDivisionCtaTasks / ntp > 0 ? kDivisionCtaTasks / ntp : 1;
+  const int ntask = ntp * S;  // <= kDivisionCtaTasks (ntp <= 15)
   const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
   for (int tau = 1; tau <= nk; ++tau) {
     __syncthreads();  // sx holds the rebuilt positions
-    if (pair_thread) {
+    if (warp < ntask) {
+      const int tp = warp / S, sc_ = warp - (warp / S) * S;
+      int I, J;
+      tile_pair(tp, nb, I, J);
+      const bool diag = I == J;
+      const int kb = diag ? 1 + (16 * sc_) / S : (32 * sc_) / S;
+      const int ke = diag ? 1 + (16 * (sc_ + 1)) / S : (32 * (sc_ + 1)) / S;
+      double* pt = part + (size_t)warp * 7 * 32;  // the task's 7 planes
+      double* jx = pt + 4 * 32;
+      double* jy = jx + 32;
+      double* jz = jy + 32;
+      jx[lane] = 0.0;
+      jy[lane] = 0.0;
+      jz[lane] = 0.0;
+      __syncwarp();
+      const int i = 32 * I + lane, j0 = 32 * J;
       const double xi = sx[i], yi = sx[npad + i], zi = sx[2 * npad + i];
       const MassSplit msi{smm[i], sme[i]};
       const int pi = sP[i], gpi = sG[i];
@@ -500,45 +521,49 @@ k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double*
       unsigned long long Rn;
       int eR;
       double sj, si;
-      // far partners of the chunk
-      for (int j = j_lo; j < j_hi; ++j) {
+      for (int k = kb; k < ke; ++k) {
+        const int jl = (lane + k) & 31, j = j0 + jl;
         const int pj = sP[j], gj = sG[j];
-        bool masked = i_pad | (j >= n) | (j == i);
+        bool masked = i_pad | (j >= n) | (diag & (k == 16) & (lane >= 16));
         masked |= nd1 & ((pi == j) | (pj == i));
         masked |= nd2 & ((gpi == j) | (gj == i) | (pi == pj));
         const double dx = sx[j] - xi, dy = sx[npad + j] - yi, dz = sx[2 * npad + j] - zi;
         const unsigned long long mjm = smm[j];
         const int mje = sme[j];
         pair_scalars_core(dx, dy, dz, MassSplit{mjm, mje}, msi, Rn, eR, sj, si);
-        if (!masked) {
-          ubad |= Rn == 0ull;
-          ax = fma(sj, dx, ax);
-          ay = fma(sj, dy, ay);
-          az = fma(sj, dz, az);
-          if (j > i) uacc.add(__umul64hi(mjm, Rn), mje + eR + 64);
-        }
+        sj = __longlong_as_double(masked ? 0ll : __double_as_longlong(sj));
+        si = __longlong_as_double(masked ? 0ll : __double_as_longlong(si));
+        ubad |= !masked && Rn == 0ull;
+        uacc.add(masked ? 0ull : __umul64hi(mjm, Rn), masked ? uacc.L : mje + eR + 64);
+        ax = fma(sj, dx, ax);
+        ay = fma(sj, dy, ay);
+        az = fma(sj, dz, az);
+        // partner sums are kept with the opposite sign and negated once at the end
+        jx[jl] = fma(si, dx, jx[jl]);
+        jy[jl] = fma(si, dy, jy[jl]);
+        jz[jl] = fma(si, dz, jz[jl]);
+        __syncwarp();
       }
-      // near partners number k = ch, ch + nch, ... of the list parent, children, grandparent,
-      // grandchildren, siblings; separation d = r_q - r_i from the edge vectors
+      // this task's share of body i's near partners: separation d = r_q - r_i from the edge
+      // vectors, (+-X_a) + (+-X_b) (no second term for b < 0), signs flipped on the bit patterns
       if (nd1 && !i_pad) {
-        int kc = 0;  // partners seen so far, mod nch
+        const int count = (nb - I) * S, rank = (J - I) * S + sc_;
+        int kc = 0;  // partners seen so far, mod count
         const double* Xx = X;
         const double* Xy = X + npad;
         const double* Xz = X + 2 * (size_t)npad;
-        // partner q at r_q - r_i = (+-X_a) + (+-X_b) (no second term for b < 0); the signs are
-        // flipped on the bit patterns
         auto flip = [](double x, bool neg) {
           return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
         };
-        auto near = [&](int q, int a, bool na, int b, bool nb) {
-          const bool mine = kc == pi_ch;
-          kc = kc + 1 == nch ? 0 : kc + 1;
+        auto near = [&](int q, int a, bool na, int b, bool nb_) {
+          const bool mine = kc == rank;
+          kc = kc + 1 == count ? 0 : kc + 1;
           if (!mine) return;
           double dx = flip(Xx[a], na), dy = flip(Xy[a], na), dz = flip(Xz[a], na);
           if (b >= 0) {
-            dx = __dadd_rn(dx, flip(Xx[b], nb));
-            dy = __dadd_rn(dy, flip(Xy[b], nb));
-            dz = __dadd_rn(dz, flip(Xz[b], nb));
+            dx = __dadd_rn(dx, flip(Xx[b], nb_));
+            dy = __dadd_rn(dy, flip(Xy[b], nb_));
+            dz = __dadd_rn(dz, flip(Xz[b], nb_));
           }
           pair_scalars_core(dx, dy, dz, MassSplit{smm[q], sme[q]}, msi, Rn, eR, sj, si);
           ubad |= Rn == 0ull;
@@ -569,27 +594,43 @@ k_division_cta(int n, int npad, int K, int nch, int n_d, double G, const double*
             }
         }
       }
-      double* q = part + (size_t)pi_ch * 4 * npad + i;
-      q[0] = ax;
-      q[npad] = ay;
-      q[2 * (size_t)npad] = az;
-      q[3 * (size_t)npad] = ubad ? __longlong_as_double(0x7ff8000000000000LL) : uacc.value();
+      const double ui = ubad ? __longlong_as_double(0x7ff8000000000000LL) : uacc.value();
+      if (diag) {  // both sides belong to tile I's bodies
+        pt[lane] = ax - jx[lane];
+        pt[32 + lane] = ay - jy[lane];
+        pt[64 + lane] = az - jz[lane];
+      } else {
+        pt[lane] = ax;
+        pt[32 + lane] = ay;
+        pt[64 + lane] = az;
+        const long long sgn = (long long)0x8000000000000000ull;
+        jx[lane] = __longlong_as_double(__double_as_longlong(jx[lane]) ^ sgn);
+        jy[lane] = __longlong_as_double(__double_as_longlong(jy[lane]) ^ sgn);
+        jz[lane] = __longlong_as_double(__double_as_longlong(jz[lane]) ^ sgn);
+      }
+      pt[96 + lane] = ui;
     }
     __syncthreads();
-    // chunk sums: component c of the accelerations (times G) and, on the c = 0 tasks, the
-    // body's m_i u_i
+    // sums over the tasks in task order: component c of body ti's acceleration (times G) and,
+    // on the c = 0 tasks, the body's m_i u_i
     double um = 0.0;
     if (task) {
-      const double* q = part + (size_t)c * npad + ti;
-      double s = q[0];
-      for (int k = 1; k < nch; ++k) s += q[(size_t)k * 4 * npad];
-      sA[(size_t)c * npad + ti] = G * s;
-      if (c == 0 && ti < n) {
-        const double* qu = part + 3 * (size_t)npad + ti;
-        double u = qu[0];
-        for (int k = 1; k < nch; ++k) u += qu[(size_t)k * 4 * npad];
-        um = sm[ti] * u;
-      }
+      const int t = ti >> 5, l = ti & 31;
+      double a = 0.0, u = 0.0;
+      int w = 0;
+      for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J)
+          for (int q = 0; q < S; ++q, ++w) {
+            const double* pt = part + (size_t)w * 7 * 32;
+            if (I == t) {
+              a += pt[c * 32 + l];
+              if (c == 0) u += pt[96 + l];
+            } else if (J == t) {
+              a += pt[(4 + c) * 32 + l];
+            }
+          }
+      sA[(size_t)c * npad + ti] = G * a;
+      if (c == 0 && ti < n) um = sm[ti] * u;
     }
     {
       if (warp < nb) {
@@ -865,14 +906,19 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   return cudaGetLastError();
 }
 
+cudaError_t prepare_division_cta(mstar_ctx* c) {
+  if (c->npad > kDivisionCtaMax) return cudaSuccess;
+  return cudaFuncSetAttribute(k_division_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)division_cta_smem(c->npad));
+}
+
 // Every division of an attempt, from the first half drift to the last drift, in one launch
 // with one CTA per division (npad <= kDivisionCtaMax).
 cudaError_t launch_division_cta(mstar_ctx* c) {
   const int npad = c->npad;
-  const int nch = kDivisionCtaThreads / npad;  // >= 3 (npad <= kDivisionCtaMax)
   const size_t smem = division_cta_smem(npad);
   k_division_cta<<<c->K, kDivisionCtaThreads, smem, c->stream>>>(
-      c->n, npad, c->K, nch, c->p.n_d, c->p.G, c->d.res + 4, c->B, c->Mtot, c->d.m, c->d.parent, c->d.gp,
+      c->n, npad, c->K, c->p.n_d, c->p.G, c->d.res + 4, c->B, c->Mtot, c->d.m, c->d.parent, c->d.gp,
       c->d.child_off, c->d.child_idx, c->d.bylev, c->d.X0, c->d.V0, c->d.sX, c->d.sV, c->d.sc);
   MSTAR_LAUNCHED(c);
   c->force_evals += (long long)c->K * (c->K + 1);  // sum of n_k = 2 (k + 1) over the divisions
