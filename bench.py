@@ -480,7 +480,7 @@ def run_small_configs(args, dev, M, W, torch):
     for key, name, t_end, steps in (("plummer64_to_t1", "plummer64", 1.0, 1 << 30),
                                     ("plummer2048_smbh_binary_200_steps", "plummer2048_smbh_binary", 10.0, 200)):
         m, r, v = W.workload(name)
-        if len(m) <= 96:  # one CTA per division (the library's size rule): no pair tiles to tune
+        if len(m) <= 160:  # a CTA cluster per division (the library's size rule): no pair tiles to tune
             (tile, split), tile_ms = (0, 0), None
         else:
             (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=3)
@@ -496,7 +496,7 @@ def run_small_configs(args, dev, M, W, torch):
         out[key] = {"n": n, "wall_s": wall, "accepted": st["accepted"], "rejected": st["rejected"],
                     "t_reached": st["t"], "gbs_steps_per_s": st["accepted"] / wall,
                     "pair_forces_per_s": st["force_evals"] * n * (n - 1) / wall, "abs_dE_over_E": abs((e1 - e0) / e0),
-                    "division_schedule": ("one CTA per division" if len(m) <= 96 else
+                    "division_schedule": ("a CTA cluster per division" if len(m) <= 160 else
                                           ("a stream per division" if len(m) >= 1000 else "level by level")),
                     "pair_tile": tile, "pair_split": split, "pair_tile_tuner_ms_per_attempt": tile_ms}
         g.close()

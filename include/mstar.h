@@ -91,11 +91,16 @@ typedef struct {
                         another's pair loop, 3 each division in one CTA from its first drift to
                         its last, pair sums included, all divisions in one launch (systems of at
                         most 160 padded bodies; larger ones take the size rule), 0 for the size
-                        rule (3 up to 96 padded bodies, 2 from 1000 bodies, else 1). 1 and 2
+                        rule (3 up to 160 padded bodies, 2 from 1000 bodies, else 1). 1 and 2
                         give bit-identical results; 3 sums the pair forces in another order, so
                         its results differ from theirs by rounding. Attempts that record an
                         adjoint trajectory or time the pair kernel, and the forward runs of the
                         adjoint, use 1. 0 */
+  int division_cluster; /* CTAs per division under division_schedule 3: 1, or 2, 4 or 8 as a
+                        thread-block cluster that shares out the pair sums and reads the partials
+                        through distributed shared memory, or 0 for the size rule (1 up to 32
+                        padded bodies, else 8). The pair sums are chunked by the cluster size, so
+                        results differ between sizes by rounding. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */

@@ -118,6 +118,9 @@ bool valid_params(const mstar_params* p) {
   if (p->pair_split != 0 && p->pair_split != 1 && p->pair_split != 2 && p->pair_split != 4 && p->pair_split != 8)
     return false;
   if (p->division_schedule < 0 || p->division_schedule > 3) return false;
+  if (p->division_cluster != 0 && p->division_cluster != 1 && p->division_cluster != 2 && p->division_cluster != 4 &&
+      p->division_cluster != 8)
+    return false;
   return true;
 }
 
@@ -511,6 +514,7 @@ void mstar_default_params(mstar_params* p) {
   p->pair_tile = 0;
   p->pair_split = 0;
   p->division_schedule = 0;
+  p->division_cluster = 0;
 }
 
 size_t mstar_workspace_bytes(int n, const mstar_params* p) {
@@ -587,6 +591,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   // systems, else a stream per division from 1000 bodies, else level by level
   const int ds = p->division_schedule;
   c->div_cta = (ds == 3 && c->npad <= kDivisionCtaMax) || (ds == 0 && c->npad <= kDivisionCtaRule);
+  c->div_cluster = p->division_cluster ? p->division_cluster : (c->npad <= 32 ? 1 : 8);
   c->branched = ds == 2 || ((ds == 0 || ds == 3) && !c->div_cta && n >= 1000);
   c->nblk = s.nblk;
   const size_t need = carve(s, nullptr, nullptr, nullptr);

@@ -82,6 +82,7 @@ struct mstar_ctx {
   int W = 0, T = 0, NT = 0, ntp = 0;  // pair tiling: warps/CTA, tile, tiles, tile pairs
   int S = 1;                          // warps sharing a tile pair's partner steps (32-body tiles)
   bool div_cta = false;               // attempts run each division in one CTA, in one launch
+  int div_cluster = 1;                // ... or in a cluster of this many CTAs (1, 2 or 4)
   bool branched = false;              // attempts issue each division on its own stream
   bool levelled = false;              // attempts go level by level (the adjoint's forward runs)
   cudaStream_t br_stream[mstar::kMaxKfix] = {};  // those streams (created with the context)
@@ -174,10 +175,10 @@ cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo,
 constexpr int kDivisionCtaThreads = 512;
 constexpr int kDivisionCtaTasks = kDivisionCtaThreads / 32;
 constexpr int kDivisionCtaMax = 160;
-constexpr int kDivisionCtaRule = 96;   // the size rule's limit (division_schedule 0)
+constexpr int kDivisionCtaRule = 160;  // the size rule's limit (division_schedule 0)
 constexpr size_t division_cta_smem(int npad) {
   return (size_t)npad * (13 * sizeof(double) + sizeof(unsigned long long) + 5 * sizeof(int)) + sizeof(int) +
-         (size_t)kDivisionCtaTasks * 7 * 32 * sizeof(double);
+         (size_t)2 * kDivisionCtaTasks * 7 * 32 * sizeof(double);
 }
 // at context creation: the division kernel's shared memory for this size (above 48 KB needs it)
 cudaError_t prepare_division_cta(mstar_ctx* c);

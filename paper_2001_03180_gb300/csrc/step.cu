@@ -9,6 +9,8 @@
 //
 // The drift/kick/rebuild arithmetic uses explicitly rounded FP64 operations (no
 // contraction), the same operation order as the CPU reference.
+#include <cooperative_groups.h>
+
 #include "device.cuh"
 #include "internal.h"
 
@@ -381,6 +383,15 @@ __device__ __forceinline__ double warp_sum(double x) {
 // N_d = 2, from the edge vectors): partner number k of body i goes to the task of rank k modulo
 // the (nb - I) S tasks whose i-side is tile I. A body then adds its tasks' partials in task
 // order. The sum of m_j / r is exact within a task (UAcc).
+//
+// With C > 1 a division runs on a cluster of C CTAs: the tasks are dealt out over the cluster
+// (task w to CTA w mod C), every CTA reads all partials through distributed shared memory after
+// a cluster barrier and adds them in the same task order, and every CTA runs the serial phases
+// on its own copy of the state, which stays bit-identical across the cluster; rank 0 writes the
+// results. The partials are double-buffered by substep, so one cluster barrier per substep
+// orders the writes of a substep's partials after every CTA's reads of the ones two substeps
+// before.
+template <int C>
 __global__ void __launch_bounds__(kDivisionCtaThreads)
 k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restrict__ par, double B,
                double Mtot, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ gp,
@@ -388,9 +399,10 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
                const double* __restrict__ X0, const double* __restrict__ V0, double* __restrict__ sX,
                double* __restrict__ sV, double* __restrict__ sc) {
   // shared: edge positions X and velocities V, Cartesian positions sx, accelerations sA (3 npad
-  // each), masses (npad), the tasks' partials (kDivisionCtaThreads / 32 tasks x 7 planes of 32:
-  // the i-side ax, ay, az, m/r sums, then the j-side sums), mass significands (npad), then mass
-  // exponents, parents, grandparents, children offsets (npad + 1) and children (npad)
+  // each), masses (npad), two buffers of the CTA's tasks' partials (kDivisionCtaThreads / 32
+  // tasks x 7 planes of 32: the i-side ax, ay, az, m/r sums, then the j-side sums), mass
+  // significands (npad), then mass exponents, parents, grandparents, children offsets (npad + 1)
+  // and children (npad)
   extern __shared__ __align__(16) double div_sh[];
   double* X = div_sh;
   double* V = X + 3 * (size_t)npad;
@@ -398,7 +410,7 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
   double* sA = sx + 3 * (size_t)npad;
   double* sm = sA + 3 * (size_t)npad;
   double* part = sm + npad;
-  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)kDivisionCtaTasks * 7 * 32);
+  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)2 * kDivisionCtaTasks * 7 * 32);
   int* sme = reinterpret_cast<int*>(smm + npad);
   int* sP = sme + npad;
   int* sG = sP + npad;
@@ -406,7 +418,8 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
   int* sCi = sCo + npad + 1;
   __shared__ double red[kDivisionCtaThreads / 32];
   __shared__ double s_val[4];
-  const int slot = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = blockIdx.x / C, rank = blockIdx.x - (blockIdx.x / C) * C;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nb = npad >> 5;  // warps per component
   const size_t st = (size_t)3 * npad;
   const double H = par[0], t0 = par[1];
@@ -488,21 +501,25 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
   };
 
   rebuild(X, sx);
-  // the pair-sum tasks: tile pairs (in tile_pair order) times S chunks of partner steps
+  // the pair-sum tasks: tile pairs (in tile_pair order) times S chunks of partner steps (at most
+  // 8 chunks: shorter ones cost more in set-up than they save), dealt out over the cluster
   const int ntp = nb * (nb + 1) / 2;
-  const int S = kDivisionCtaTasks / ntp > 0 ? kDivisionCtaTasks / ntp : 1;
-  const int ntask = ntp * S;  // <= kDivisionCtaTasks (ntp <= 15)
+  int S = (kDivisionCtaTasks * C) / ntp;
+  S = S < 1 ? 1 : (S > 8 ? 8 : S);
+  const int ntask = ntp * S;  // <= kDivisionCtaTasks C (ntp <= 15)
   const bool nd1 = n_d >= 1, nd2 = n_d >= 2;
   for (int tau = 1; tau <= nk; ++tau) {
+    double* partb = part + (size_t)(tau & 1) * kDivisionCtaTasks * 7 * 32;  // this substep's buffer
     __syncthreads();  // sx holds the rebuilt positions
-    if (warp < ntask) {
-      const int tp = warp / S, sc_ = warp - (warp / S) * S;
+    const int w = rank + C * warp;  // the warp's task
+    if (w < ntask) {
+      const int tp = w / S, sc_ = w - (w / S) * S;
       int I, J;
       tile_pair(tp, nb, I, J);
       const bool diag = I == J;
       const int kb = diag ? 1 + (16 * sc_) / S : (32 * sc_) / S;
       const int ke = diag ? 1 + (16 * (sc_ + 1)) / S : (32 * (sc_ + 1)) / S;
-      double* pt = part + (size_t)warp * 7 * 32;  // the task's 7 planes
+      double* pt = partb + (size_t)warp * 7 * 32;  // the task's 7 planes
       double* jx = pt + 4 * 32;
       double* jy = jx + 32;
       double* jz = jy + 32;
@@ -547,7 +564,7 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
       // this task's share of body i's near partners: separation d = r_q - r_i from the edge
       // vectors, (+-X_a) + (+-X_b) (no second term for b < 0), signs flipped on the bit patterns
       if (nd1 && !i_pad) {
-        const int count = (nb - I) * S, rank = (J - I) * S + sc_;
+        const int count = (nb - I) * S, share = (J - I) * S + sc_;
         int kc = 0;  // partners seen so far, mod count
         const double* Xx = X;
         const double* Xy = X + npad;
@@ -556,7 +573,7 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
           return neg ? __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull) : x;
         };
         auto near = [&](int q, int a, bool na, int b, bool nb_) {
-          const bool mine = kc == rank;
+          const bool mine = kc == share;
           kc = kc + 1 == count ? 0 : kc + 1;
           if (!mine) return;
           double dx = flip(Xx[a], na), dy = flip(Xy[a], na), dz = flip(Xz[a], na);
@@ -610,18 +627,23 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
       }
       pt[96 + lane] = ui;
     }
-    __syncthreads();
+    if constexpr (C > 1)
+      cooperative_groups::this_cluster().sync();  // every CTA's partials of this substep are written
+    else
+      __syncthreads();
     // sums over the tasks in task order: component c of body ti's acceleration (times G) and,
     // on the c = 0 tasks, the body's m_i u_i
     double um = 0.0;
     if (task) {
       const int t = ti >> 5, l = ti & 31;
       double a = 0.0, u = 0.0;
-      int w = 0;
+      int wt = 0;
       for (int I = 0; I < nb; ++I)
         for (int J = I; J < nb; ++J)
-          for (int q = 0; q < S; ++q, ++w) {
-            const double* pt = part + (size_t)w * 7 * 32;
+          for (int q = 0; q < S; ++q, ++wt) {
+            if (I != t && J != t) continue;
+            const double* pt = partb + (size_t)(wt / C) * 7 * 32;
+            if constexpr (C > 1) pt = cooperative_groups::this_cluster().map_shared_rank(pt, wt - (wt / C) * C);
             if (I == t) {
               a += pt[c * 32 + l];
               if (c == 0) u += pt[96 + l];
@@ -669,7 +691,12 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
     __syncthreads();
     if (tau < nk) rebuild(X, sx);
   }
-  // the division's final state and scalars for the extrapolation
+  // the division's final state and scalars for the extrapolation (every CTA of a cluster holds
+  // the same; no CTA leaves while another may still read its partials)
+  if constexpr (C > 1) {
+    cooperative_groups::this_cluster().sync();
+    if (rank != 0) return;
+  }
   if (task) {
     const size_t o = (size_t)c * npad + ti;
     sX[slot * st + o] = X[o];
@@ -908,20 +935,48 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
 
 cudaError_t prepare_division_cta(mstar_ctx* c) {
   if (c->npad > kDivisionCtaMax) return cudaSuccess;
-  return cudaFuncSetAttribute(k_division_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)division_cta_smem(c->npad));
+  const int smem = (int)division_cta_smem(c->npad);
+  cudaError_t e = cudaFuncSetAttribute(k_division_cta<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+template <int Cl>
+cudaError_t launch_division_cta_c(mstar_ctx* c) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->K * Cl);
+  cfg.blockDim = dim3(kDivisionCtaThreads);
+  cfg.dynamicSmemBytes = division_cta_smem(c->npad);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = Cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_division_cta<Cl>, c->n, c->npad, c->K, c->p.n_d, c->p.G,
+                            (const double*)(c->d.res + 4), c->B, c->Mtot, (const double*)c->d.m,
+                            (const int*)c->d.parent, (const int*)c->d.gp, (const int*)c->d.child_off,
+                            (const int*)c->d.child_idx, (const int*)c->d.bylev, (const double*)c->d.X0,
+                            (const double*)c->d.V0, c->d.sX, c->d.sV, c->d.sc);
 }
 
 // Every division of an attempt, from the first half drift to the last drift, in one launch
-// with one CTA per division (npad <= kDivisionCtaMax).
+// with one CTA, or a cluster of c->div_cluster CTAs, per division (npad <= kDivisionCtaMax).
 cudaError_t launch_division_cta(mstar_ctx* c) {
-  const int npad = c->npad;
-  const size_t smem = division_cta_smem(npad);
-  k_division_cta<<<c->K, kDivisionCtaThreads, smem, c->stream>>>(
-      c->n, npad, c->K, c->p.n_d, c->p.G, c->d.res + 4, c->B, c->Mtot, c->d.m, c->d.parent, c->d.gp,
-      c->d.child_off, c->d.child_idx, c->d.bylev, c->d.X0, c->d.V0, c->d.sX, c->d.sV, c->d.sc);
+  cudaError_t e;
+  switch (c->div_cluster) {
+    case 2: e = launch_division_cta_c<2>(c); break;
+    case 4: e = launch_division_cta_c<4>(c); break;
+    case 8: e = launch_division_cta_c<8>(c); break;
+    default: e = launch_division_cta_c<1>(c); break;
+  }
   MSTAR_LAUNCHED(c);
   c->force_evals += (long long)c->K * (c->K + 1);  // sum of n_k = 2 (k + 1) over the divisions
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

@@ -45,7 +45,7 @@ class mstar_params(C.Structure):
                 ("fac_max", C.c_double), ("q_first", C.c_double), ("t_tol", C.c_double),
                 ("G", C.c_double), ("k_fix", C.c_int), ("n_d", C.c_int), ("max_halvings", C.c_int),
                 ("max_time_iter", C.c_int), ("mst_method", C.c_int), ("mst_nsub", C.c_int),
-                ("pair_tile", C.c_int), ("pair_split", C.c_int), ("division_schedule", C.c_int)]
+                ("pair_tile", C.c_int), ("pair_split", C.c_int), ("division_schedule", C.c_int), ("division_cluster", C.c_int)]
 
 
 class mstar_stats(C.Structure):

@@ -222,14 +222,15 @@ def div_cta_system(name):
     return W.plummer(int(name[1:]), 8)
 
 
+@pytest.mark.parametrize("cluster", [1, 2, 4, 8])
 @pytest.mark.parametrize("name,H,n_d", DIV_CTA_CASES)
-def test_division_cta_attempt_matches_oracle(name, H, n_d):
+def test_division_cta_attempt_matches_oracle(name, H, n_d, cluster):
     """One CTA per division for a whole attempt (pair sums, near pairs from the edge vectors,
-    kicks, rebuilds and drifts in one launch): the attempt's state agrees with the oracle to
-    1e-12, as the multi-kernel path does, for 2 ... 160 bodies (the last chunk of partners and
-    the padding ragged) and every near rule."""
+    kicks, rebuilds and drifts in one launch), or a cluster of 2, 4 or 8 CTAs sharing the pair sums:
+    the attempt's state agrees with the oracle to 1e-12, as the multi-kernel path does, for
+    2 ... 160 bodies (ragged padding) and every near rule."""
     m, r, v = div_cta_system(name)
-    g = M.Integrator(m, r, v, division_schedule=3, n_d=n_d)
+    g = M.Integrator(m, r, v, division_schedule=3, division_cluster=cluster, n_d=n_d)
     o = O.System(m, r, v, n_d=n_d)
     gs = g.attempt(H)
     os_ = o.attempt(H)
@@ -248,13 +249,14 @@ def test_division_cta_agrees_with_the_level_path(n):
     size follows that rounding.)"""
     m, r, v = (W.kepler_binary(seed=1) if n == 2 else W.plummer(n, 8))
     out = []
-    for mode in (1, 3):
-        g = M.Integrator(m, r, v, division_schedule=mode)
+    for mode, cluster in ((1, 0), (3, 1), (3, 2), (3, 4), (3, 8)):
+        g = M.Integrator(m, r, v, division_schedule=mode, division_cluster=cluster)
         out.append(g.attempt(1e-3))
         g.close()
-    a1, a3 = out
-    assert relerr(a3["r"], a1["r"]) < 1e-12 and relerr(a3["v"], a1["v"]) < 1e-12
-    assert abs(a3["t"] - a1["t"]) <= 1e-12 * abs(a1["t"])
+    a1 = out[0]
+    for a3 in out[1:]:
+        assert relerr(a3["r"], a1["r"]) < 1e-12 and relerr(a3["v"], a1["v"]) < 1e-12
+        assert abs(a3["t"] - a1["t"]) <= 1e-12 * abs(a1["t"])
 
 
 def test_division_cta_beyond_its_size_takes_the_size_rule():
@@ -270,6 +272,8 @@ def test_division_cta_beyond_its_size_takes_the_size_rule():
     assert np.array_equal(out[0]["r"], out[1]["r"]) and np.array_equal(out[0]["v"], out[1]["v"])
     with pytest.raises(M.MstarError):
         M.Integrator(m, r, v, division_schedule=4)
+    with pytest.raises(M.MstarError):
+        M.Integrator(m, r, v, division_cluster=3)
 
 
 @pytest.mark.parametrize("n_d", [0, 1, 2])
