@@ -98,7 +98,7 @@ typedef struct {
                         adjoint, use 1. 0 */
   int division_cluster; /* CTAs per division under division_schedule 3: 1, or 2, 4 or 8 as a
                         thread-block cluster that shares out the pair sums and reads the partials
-                        through distributed shared memory, or 0 for the size rule (1 up to 32
+                        through distributed shared memory, or 0 for the size rule (4 up to 32
                         padded bodies, else 8). The pair sums are chunked by the cluster size, so
                         results differ between sizes by rounding. 0 */
 } mstar_params;

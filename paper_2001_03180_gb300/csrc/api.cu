@@ -591,7 +591,7 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   // systems, else a stream per division from 1000 bodies, else level by level
   const int ds = p->division_schedule;
   c->div_cta = (ds == 3 && c->npad <= kDivisionCtaMax) || (ds == 0 && c->npad <= kDivisionCtaRule);
-  c->div_cluster = p->division_cluster ? p->division_cluster : (c->npad <= 32 ? 1 : 8);
+  c->div_cluster = p->division_cluster ? p->division_cluster : (c->npad <= 32 ? 4 : 8);
   c->branched = ds == 2 || ((ds == 0 || ds == 3) && !c->div_cta && n >= 1000);
   c->nblk = s.nblk;
   const size_t need = carve(s, nullptr, nullptr, nullptr);

@@ -178,7 +178,7 @@ constexpr int kDivisionCtaMax = 160;
 constexpr int kDivisionCtaRule = 160;  // the size rule's limit (division_schedule 0)
 constexpr size_t division_cta_smem(int npad) {
   return (size_t)npad * (13 * sizeof(double) + sizeof(unsigned long long) + 5 * sizeof(int)) + sizeof(int) +
-         (size_t)2 * kDivisionCtaTasks * 7 * 32 * sizeof(double);
+         (size_t)2 * kDivisionCtaTasks * 7 * 32 * sizeof(double) + (size_t)8 * npad * sizeof(double);
 }
 // at context creation: the division kernel's shared memory for this size (above 48 KB needs it)
 cudaError_t prepare_division_cta(mstar_ctx* c);

@@ -385,12 +385,12 @@ __device__ __forceinline__ double warp_sum(double x) {
 // order. The sum of m_j / r is exact within a task (UAcc).
 //
 // With C > 1 a division runs on a cluster of C CTAs: the tasks are dealt out over the cluster
-// (task w to CTA w mod C), every CTA reads all partials through distributed shared memory after
-// a cluster barrier and adds them in the same task order, and every CTA runs the serial phases
-// on its own copy of the state, which stays bit-identical across the cluster; rank 0 writes the
-// results. The partials are double-buffered by substep, so one cluster barrier per substep
-// orders the writes of a substep's partials after every CTA's reads of the ones two substeps
-// before.
+// (task w to CTA w mod C), each CTA adds its own tasks' partials per body (in task order), and
+// after a cluster barrier every CTA reads the C CTAs' sums through distributed shared memory and
+// adds them in rank order. Every CTA runs the serial phases on its own copy of the state, which
+// stays bit-identical across the cluster; rank 0 writes the results. The per-CTA sums are
+// double-buffered by substep, so one cluster barrier per substep orders the writes of a
+// substep's sums after every CTA's reads of the ones two substeps before.
 template <int C>
 __global__ void __launch_bounds__(kDivisionCtaThreads)
 k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restrict__ par, double B,
@@ -400,9 +400,9 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
                double* __restrict__ sV, double* __restrict__ sc) {
   // shared: edge positions X and velocities V, Cartesian positions sx, accelerations sA (3 npad
   // each), masses (npad), two buffers of the CTA's tasks' partials (kDivisionCtaThreads / 32
-  // tasks x 7 planes of 32: the i-side ax, ay, az, m/r sums, then the j-side sums), mass
-  // significands (npad), then mass exponents, parents, grandparents, children offsets (npad + 1)
-  // and children (npad)
+  // tasks x 7 planes of 32: the i-side ax, ay, az, m/r sums, then the j-side sums), two buffers
+  // of the CTA's sums per body (4 planes of npad), mass significands (npad), then mass
+  // exponents, parents, grandparents, children offsets (npad + 1) and children (npad)
   extern __shared__ __align__(16) double div_sh[];
   double* X = div_sh;
   double* V = X + 3 * (size_t)npad;
@@ -410,7 +410,8 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
   double* sA = sx + 3 * (size_t)npad;
   double* sm = sA + 3 * (size_t)npad;
   double* part = sm + npad;
-  unsigned long long* smm = reinterpret_cast<unsigned long long*>(part + (size_t)2 * kDivisionCtaTasks * 7 * 32);
+  unsigned long long* smm =
+      reinterpret_cast<unsigned long long*>(part + (size_t)2 * kDivisionCtaTasks * 7 * 32 + (size_t)8 * npad);
   int* sme = reinterpret_cast<int*>(smm + npad);
   int* sP = sme + npad;
   int* sG = sP + npad;
@@ -502,7 +503,8 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
 
   rebuild(X, sx);
   // the pair-sum tasks: tile pairs (in tile_pair order) times S chunks of partner steps (at most
-  // 8 chunks: shorter ones cost more in set-up than they save), dealt out over the cluster
+  // 8 chunks: with 4 or 16 at most, attempts at N = 64 ... 160 took 2-16 % longer), dealt out
+  // over the cluster
   const int ntp = nb * (nb + 1) / 2;
   int S = (kDivisionCtaTasks * C) / ntp;
   S = S < 1 ? 1 : (S > 8 ? 8 : S);
@@ -627,30 +629,53 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
       }
       pt[96 + lane] = ui;
     }
-    if constexpr (C > 1)
-      cooperative_groups::this_cluster().sync();  // every CTA's partials of this substep are written
-    else
-      __syncthreads();
-    // sums over the tasks in task order: component c of body ti's acceleration (times G) and,
-    // on the c = 0 tasks, the body's m_i u_i
-    double um = 0.0;
+    __syncthreads();
+    // this CTA's sums over its tasks, in task order: component c of body ti's acceleration and,
+    // on the c = 0 tasks, the body's sum of m/r
+    double a = 0.0, u = 0.0;
     if (task) {
       const int t = ti >> 5, l = ti & 31;
-      double a = 0.0, u = 0.0;
       int wt = 0;
       for (int I = 0; I < nb; ++I)
         for (int J = I; J < nb; ++J)
           for (int q = 0; q < S; ++q, ++wt) {
-            if (I != t && J != t) continue;
+            if ((wt & (C - 1)) != rank || (I != t && J != t)) continue;  // C is a power of two
             const double* pt = partb + (size_t)(wt / C) * 7 * 32;
-            if constexpr (C > 1) pt = cooperative_groups::this_cluster().map_shared_rank(pt, wt - (wt / C) * C);
             if (I == t) {
               a += pt[c * 32 + l];
               if (c == 0) u += pt[96 + l];
-            } else if (J == t) {
+            } else {
               a += pt[(4 + c) * 32 + l];
             }
           }
+    }
+    if constexpr (C > 1) {
+      // the cluster's sums: every CTA adds the C CTAs' sums in rank order
+      double* loc = part + (size_t)2 * kDivisionCtaTasks * 7 * 32 + (size_t)(tau & 1) * 4 * npad;
+      if (task) {
+        loc[(size_t)c * npad + ti] = a;
+        if (c == 0) loc[3 * (size_t)npad + ti] = u;
+      }
+      cooperative_groups::this_cluster().sync();  // every CTA's sums of this substep are written
+      if (task) {
+        double rc[C], ru[C];
+#pragma unroll
+        for (int r = 0; r < C; ++r) {
+          const double* lr = cooperative_groups::this_cluster().map_shared_rank(loc, r);
+          rc[r] = lr[(size_t)c * npad + ti];
+          ru[r] = c == 0 ? lr[3 * (size_t)npad + ti] : 0.0;
+        }
+        a = rc[0];
+        u = ru[0];
+#pragma unroll
+        for (int r = 1; r < C; ++r) {
+          a += rc[r];
+          u += ru[r];
+        }
+      }
+    }
+    double um = 0.0;
+    if (task) {
       sA[(size_t)c * npad + ti] = G * a;
       if (c == 0 && ti < n) um = sm[ti] * u;
     }
