@@ -180,7 +180,8 @@ constexpr size_t division_cta_smem(int npad) {
   return (size_t)npad * (13 * sizeof(double) + sizeof(unsigned long long) + 5 * sizeof(int)) + sizeof(int) +
          (size_t)2 * kDivisionCtaTasks * 7 * 32 * sizeof(double) + (size_t)8 * npad * sizeof(double);
 }
-// at context creation: the division kernel's shared memory for this size (above 48 KB needs it)
+// at context creation: the division kernel's shared memory for this size (above 48 KB needs it),
+// and the largest cluster size up to the requested one that the device can launch
 cudaError_t prepare_division_cta(mstar_ctx* c);
 cudaError_t launch_division_cta(mstar_ctx* c);
 

@@ -958,6 +958,31 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   return cudaGetLastError();
 }
 
+// Clusters of Cl CTAs of the division kernel that the device can hold at once (0: it cannot
+// launch them at all, e.g. when a partition of the GPU has too few SMs per cluster).
+template <int Cl>
+int division_clusters_resident(const mstar_ctx* c) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(c->K * Cl);
+  cfg.blockDim = dim3(kDivisionCtaThreads);
+  cfg.dynamicSmemBytes = division_cta_smem(c->npad);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = Cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int num = 0;
+  if (cudaOccupancyMaxActiveClusters(&num, k_division_cta<Cl>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return num;
+}
+
+// At context creation: the division kernel's shared memory for this size (above 48 KB needs it),
+// and a cluster size the device can launch (halved from the requested one until it can).
 cudaError_t prepare_division_cta(mstar_ctx* c) {
   if (c->npad > kDivisionCtaMax) return cudaSuccess;
   const int smem = (int)division_cta_smem(c->npad);
@@ -965,7 +990,18 @@ cudaError_t prepare_division_cta(mstar_ctx* c) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_division_cta<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return e;
+  if (e != cudaSuccess || !c->div_cta) return e;
+  for (;;) {
+    int num = 1;
+    switch (c->div_cluster) {
+      case 8: num = division_clusters_resident<8>(c); break;
+      case 4: num = division_clusters_resident<4>(c); break;
+      case 2: num = division_clusters_resident<2>(c); break;
+      default: return cudaSuccess;
+    }
+    if (num > 0) return cudaSuccess;
+    c->div_cluster /= 2;
+  }
 }
 
 template <int Cl>
