@@ -343,6 +343,19 @@ int issue_attempt_branched(mstar_ctx* c) {
   return MSTAR_OK;
 }
 
+// Stream priority of division k's chain: the longer a division (n_k = 2 (k + 1) substeps), the
+// higher, so that the longest chain, which bounds the attempt, is served first where the
+// divisions' kernels compete for SMs.
+int division_priority(int k, int K) {
+  int lo = 0, hi = 0;  // least and greatest priority (greatest is the numerically smallest)
+  if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int levels = lo - hi + 1;
+  return lo - (int)((long long)k * levels / K);
+}
+
 // Capture issue_attempt once on a private stream and instantiate it. The launches depend
 // only on the context's sizes and buffers and on the trajectory record (H and t are read
 // from device memory), so the graph serves every later attempt with the same record. Any
@@ -366,7 +379,7 @@ cudaGraphExec_t build_attempt_graph(mstar_ctx* c) {
   c->launches = l0;
   c->force_evals = f0;
   cudaGraphExec_t exec = nullptr;
-  if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphInstantiateWithFlags(&exec, g, cudaGraphInstantiateFlagUseNodePriority) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
   if (!ok) {
     cudaGetLastError();
@@ -632,7 +645,8 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   if (c->branched) {  // the streams and events of the per-division attempt graph
     if (cudaEventCreateWithFlags(&c->br_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
     for (int k = 0; k < c->K; ++k)
-      if (cudaStreamCreateWithFlags(&c->br_stream[k], cudaStreamNonBlocking) != cudaSuccess ||
+      if (cudaStreamCreateWithPriority(&c->br_stream[k], cudaStreamNonBlocking, division_priority(k, c->K)) !=
+              cudaSuccess ||
           cudaEventCreateWithFlags(&c->br_join[k], cudaEventDisableTiming) != cudaSuccess)
         return bail(MSTAR_ERR_CUDA);
   }
