@@ -87,9 +87,10 @@ typedef struct {
                         differ from the unsplit loop by rounding only. 0 */
   int division_schedule; /* how an attempt's k_fix divisions are issued: 1 level by level (one
                         launch per kernel for every division active at that substep), 2 each
-                        division on its own stream, so that one division's small kernels overlap
-                        another's pair loop, 3 each division in one CTA from its first drift to
-                        its last, pair sums included, all divisions in one launch (systems of at
+                        division on its own stream (longer divisions at higher priority), so that
+                        one division's small kernels overlap another's pair loop, 3 each division
+                        on one CTA, or a cluster of them (division_cluster), from its first drift
+                        to its last, pair sums included, all divisions in one launch (systems of at
                         most 160 padded bodies; larger ones take the size rule), 0 for the size
                         rule (3 up to 160 padded bodies, 2 from 1000 bodies, else 1). 1 and 2
                         give bit-identical results; 3 sums the pair forces in another order, so
@@ -99,8 +100,9 @@ typedef struct {
   int division_cluster; /* CTAs per division under division_schedule 3: 1, or 2, 4 or 8 as a
                         thread-block cluster that shares out the pair sums and reads the partials
                         through distributed shared memory, or 0 for the size rule (4 up to 32
-                        padded bodies, else 8). The pair sums are chunked by the cluster size, so
-                        results differ between sizes by rounding. 0 */
+                        padded bodies, else 8; halved at context creation while the device cannot
+                        launch it). The pair sums are chunked by the cluster size, so results
+                        differ between sizes by rounding. 0 */
 } mstar_params;
 
 /* Counters of one mstar_step call, and the state after it. */
