@@ -92,7 +92,7 @@ size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
   t.comblk = c.take<double>(S * s.nblk * 3);
   t.sc = c.take<double>(S * kScal);
   t.Tkk = c.take<double>(6 * np + 1);
-  t.epsblk = c.take<double>(s.nblk);
+  t.epsblk = c.take<double>(2 * (size_t)s.nblk);
   t.res = c.take<double>(8);
   t.mom = c.take<double>((size_t)s.nblk * 8);
   t.dc = s.dcb ? c.take<char>(s.dcb) : nullptr;
@@ -214,8 +214,9 @@ void prof_flush(mstar_ctx* c) {
 // --------------------------------------------------------------------------- the GBS step
 
 // MST of the current positions, edge coordinates, and the derivative information at the
-// step start (one force evaluation); reads U0 and T0 back.
-int prepare_step(mstar_ctx* c, double* U0, double* T0) {
+// step start (one force evaluation), issued without reading anything back (the MST builders
+// may synchronise for their own checks); U0 and T0 land in d.res[2], d.res[3].
+int issue_prepare(mstar_ctx* c) {
   if (!c->mst_valid) {
     if (c->p.mst_method == 1) {
       CK(launch_mst_dc(c));
@@ -230,7 +231,14 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
   CK(launch_prepare(c));
   CK(launch_forces(c, c->K, c->K + 1, c->p.n_d));
   CK(launch_start_derivs(c));
-  int rc = sync_read_res(c);
+  return MSTAR_OK;
+}
+
+// issue_prepare, then U0 and T0 read back.
+int prepare_step(mstar_ctx* c, double* U0, double* T0) {
+  int rc = issue_prepare(c);
+  if (rc) return rc;
+  rc = sync_read_res(c);
   if (rc) return rc;
   prof_flush(c);
   *U0 = c->host_res[2];
@@ -278,6 +286,14 @@ int issue_attempt(mstar_ctx* c) {
       // one CTA per division: the whole level in one launch (the position rebuild leaves the
       // velocities and scalars that the trajectory record takes below as they were)
       CK(launch_level_cta(c, lo, K, lo2, tau));
+      if (tr) {
+        CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
+        CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
+      }
+      continue;
+    }
+    if (c->sub_cluster) {
+      CK(launch_substep_cluster(c, lo, K, lo2, tau));
       if (tr) {
         CK(save(tr->Vv + (tau - 1) * lvl + lo * st, c->d.sv + lo * st, (K - lo) * st));
         CK(save(tr->SC + tau * nsc, c->d.sc, nsc));
@@ -640,7 +656,8 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
     return code;
   };
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
-      prepare_rebuild(c) != cudaSuccess || prepare_division_cta(c) != cudaSuccess)
+      prepare_rebuild(c) != cudaSuccess || prepare_division_cta(c) != cudaSuccess ||
+      prepare_substep_cluster(c) != cudaSuccess)
     return bail(MSTAR_ERR_CUDA);
   if (c->branched) {  // the streams and events of the per-division attempt graph
     if (cudaEventCreateWithFlags(&c->br_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
@@ -858,10 +875,25 @@ int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) 
   while (st.accepted < max_gbs_steps) {
     if (std::fabs(t_end - c->t) <= tol) break;
     double U0, T0;
-    if ((rc = prepare_step(c, &U0, &T0))) break;
+    const double dt = t_end - c->t;
+    double eps = 0.0, tn = c->t;
+    // With the controller's step known (c->H != 0), the first attempt is issued right behind
+    // the step's preparation, with no read-back between them, and U0 is read with its result.
+    // The clamp below depends on U0 alone, so when it applies, that attempt is discarded and
+    // the clamped one run: the steps taken are the same as with U0 read first.
+    bool have_attempt = false;
+    if (c->H != 0.0) {
+      if ((rc = issue_prepare(c))) break;
+      if ((rc = run_attempt(c, std::fabs(c->H) * (dt < 0 ? -1.0 : 1.0), &eps, &tn))) break;
+      U0 = c->host_res[2];
+      T0 = c->host_res[3];
+      have_attempt = true;
+    } else if ((rc = prepare_step(c, &U0, &T0))) {
+      break;
+    }
+    (void)T0;
     // Sec. 2.4: first step ds = q U dt, then the controller's step clamped so that the
     // estimated end time t + ds/U does not pass t_end; past t_end, steps head back.
-    const double dt = t_end - c->t;
     double Hs = (c->H == 0.0) ? p.q_first * U0 * dt : std::fabs(c->H) * (dt < 0 ? -1.0 : 1.0);
     bool clamped = false;
     if (std::fabs(Hs / U0) >= std::fabs(dt)) {
@@ -871,11 +903,15 @@ int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) 
     if (clamped) {
       if (st.time_iters >= p.max_time_iter) break;
       st.time_iters++;
+      have_attempt = false;
     }
-    double eps = 0.0, tn = c->t;
     int halvings = 0;
     for (;;) {
-      if ((rc = run_attempt(c, Hs, &eps, &tn))) goto done;
+      if (have_attempt) {
+        have_attempt = false;
+      } else if ((rc = run_attempt(c, Hs, &eps, &tn))) {
+        goto done;
+      }
       if (eps <= p.eta_gbs) break;
       st.rejected++;
       if (++halvings > p.max_halvings) {

@@ -38,7 +38,8 @@ __global__ void __launch_bounds__(kBT)
 k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* __restrict__ Y,
       const double* __restrict__ Z, const float* __restrict__ f4, const int* __restrict__ comp,
       const int* __restrict__ nbr, unsigned long long* __restrict__ partD, int* __restrict__ partJ,
-      int* __restrict__ tie) {
+      int* __restrict__ tie, const int* __restrict__ stop) {
+  if (*stop) return;
   __shared__ float sx[kBT], sy[kBT], sz[kBT], se[kBT];
   __shared__ int sc[kBT];
   __shared__ int any;
@@ -113,9 +114,9 @@ k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* _
 // Merge the parts: exact minimum, ties flagged; cache the neighbour.
 __global__ void k_nfn_merge(int n, int npad, int nparts, const int* __restrict__ comp, int* __restrict__ nbr,
                             unsigned long long* __restrict__ nbrD, const unsigned long long* __restrict__ partD,
-                            const int* __restrict__ partJ, int* __restrict__ tie) {
+                            const int* __restrict__ partJ, int* __restrict__ tie, const int* __restrict__ stop) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *stop) return;
   const int b = nbr[i];
   if (b >= 0 && comp[b] != comp[i]) return;
   unsigned long long bD = ~0ull;
@@ -136,16 +137,16 @@ __global__ void k_nfn_merge(int n, int npad, int nparts, const int* __restrict__
 }
 
 __global__ void k_comp_min(int n, const int* __restrict__ comp, const unsigned long long* __restrict__ nbrD,
-                           unsigned long long* __restrict__ cmin) {
+                           unsigned long long* __restrict__ cmin, const int* __restrict__ stop) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) atomicMin(&cmin[comp[i]], nbrD[i]);
+  if (i < n && !*stop) atomicMin(&cmin[comp[i]], nbrD[i]);
 }
 
 __global__ void k_comp_edge(int n, const int* __restrict__ comp, const unsigned long long* __restrict__ nbrD,
                             const unsigned long long* __restrict__ cmin, int* __restrict__ cidx,
-                            int* __restrict__ ccnt, int* __restrict__ tie) {
+                            int* __restrict__ ccnt, int* __restrict__ tie, const int* __restrict__ stop) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *stop) return;
   const int c = comp[i];
   if (nbrD[i] == cmin[c]) {
     if (atomicAdd(&ccnt[c], 1) > 0) atomicOr(tie, 1);  // two cheapest edges of equal weight
@@ -157,9 +158,10 @@ __global__ void k_comp_edge(int n, const int* __restrict__ comp, const unsigned 
 // components that chose each other chose the same edge (weights distinct); the smaller
 // label becomes the root and records the edge once.
 __global__ void k_hook(int n, const int* __restrict__ comp, const int* __restrict__ nbr, const int* __restrict__ cidx,
-                       int* __restrict__ nxt, int* __restrict__ eu, int* __restrict__ ev, int* __restrict__ ecount) {
+                       int* __restrict__ nxt, int* __restrict__ eu, int* __restrict__ ev, int* __restrict__ ecount,
+                       const int* __restrict__ stop) {
   const int C = blockIdx.x * blockDim.x + threadIdx.x;
-  if (C >= n || comp[C] != C) return;
+  if (C >= n || *stop || comp[C] != C) return;
   const int i = cidx[C];
   const int j = nbr[i];
   const int T = comp[j];
@@ -180,14 +182,25 @@ __global__ void k_hook(int n, const int* __restrict__ comp, const int* __restric
 }
 
 __global__ void k_relabel(int n, int* __restrict__ comp, const int* __restrict__ nxt,
-                          unsigned long long* __restrict__ cmin, int* __restrict__ ccnt) {
+                          unsigned long long* __restrict__ cmin, int* __restrict__ ccnt, const int* __restrict__ stop) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || *stop) return;
   int c = comp[i];
   for (int guard = 0; guard < n && nxt[c] != c; ++guard) c = nxt[c];
   comp[i] = c;
   cmin[i] = ~0ull;
   ccnt[i] = 0;
+}
+
+// The gate of a round: flags[2] = 1 once the tree is complete (flags[1] = n - 1 edges) or a
+// tie has been seen (flags[0]); the round's six kernels then return at once. flags[3] counts
+// the rounds that ran. Rounds can thus be issued ahead of the host's check: a round issued
+// after the last one needed changes nothing (without the gate it would find no foreign
+// neighbour and report a tie). No kernel of a round writes flags[2].
+__global__ void k_round_gate(int n, int* __restrict__ flags) {
+  const int stop = (flags[0] != 0) || (flags[1] >= n - 1);
+  flags[2] = stop;
+  if (!stop) flags[3] += 1;
 }
 
 __global__ void k_boruvka_init(int n, const double* __restrict__ X, const double* __restrict__ Y,
@@ -363,7 +376,17 @@ cudaError_t launch_orient(mstar_ctx* c, const int* eu, const int* ev, int* adj_o
 // buffer, which is free while the tree is being built.
 cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
   const int n = c->n, npad = c->npad;
-  const int nparts = n >= 4096 ? 8 : (n >= 1024 ? 4 : 1);
+  // the candidates are split into parts, one CTA row each, until the search has about four
+  // CTAs per SM (a CTA scanning alone is bound by its latency) or a part would hold fewer than
+  // kBT candidates; at most 16
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  const int nbt = (n + kBT - 1) / kBT;
+  int nparts = 1;
+  while (nparts < 16 && nbt * nparts < 4 * sms && n / (2 * nparts) >= kBT) nparts *= 2;
   char* base = reinterpret_cast<char*>(c->d.P);
   auto take = [&](size_t bytes) {
     char* p = base;
@@ -385,7 +408,7 @@ cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
   int* queue = reinterpret_cast<int*>(take(sizeof(int) * npad));
   unsigned long long* partD = reinterpret_cast<unsigned long long*>(take(8 * (size_t)npad * nparts));
   int* partJ = reinterpret_cast<int*>(take(sizeof(int) * (size_t)npad * nparts));
-  int* flags = reinterpret_cast<int*>(take(sizeof(int) * 4));  // [0] tie, [1] edge count
+  int* flags = reinterpret_cast<int*>(take(sizeof(int) * 4));  // [0] tie, [1] edge count, [2] gate, [3] rounds run
   const size_t p_bytes = (size_t)c->nslots * c->NT * 4 * npad * sizeof(double);
   if ((size_t)(base - reinterpret_cast<char*>(c->d.P)) > p_bytes) {  // scratch does not fit: use Prim
     *tied = true;
@@ -401,26 +424,34 @@ cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
   MSTAR_LAUNCHED(c);
   int edges = 0;
   *tied = false;
-  for (int round = 0; round < 64 && edges < n - 1; ++round) {
-    k_nfn<<<dim3((n + kBT - 1) / kBT, nparts), kBT, 0, c->stream>>>(n, npad, nparts, X, Y, Z, f4, comp, nbr, partD,
-                                                                     partJ, flags);
-    k_nfn_merge<<<nb, 256, 0, c->stream>>>(n, npad, nparts, comp, nbr, nbrD, partD, partJ, flags);
-    k_comp_min<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin);
-    k_comp_edge<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, cidx, ccnt, flags);
-    k_hook<<<nb, 256, 0, c->stream>>>(n, comp, nbr, cidx, nxt, eu, ev, flags + 1);
-    k_relabel<<<nb, 256, 0, c->stream>>>(n, comp, nxt, cmin, ccnt);
-    c->launches += 6;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaMemcpyAsync(c->host_buf, flags, sizeof(int) * 2, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+  // The first check comes after as many rounds as the context's last build ran (consecutive
+  // steps build trees of nearly the same point set), then after every further round.
+  int round = 0;
+  while (round < 64 && edges < n - 1) {
+    const int batch = round == 0 ? (c->mst_rounds > 0 ? c->mst_rounds : 1) : 1;
+    for (int b = 0; b < batch && round < 64; ++b, ++round) {
+      k_round_gate<<<1, 1, 0, c->stream>>>(n, flags);
+      k_nfn<<<dim3((n + kBT - 1) / kBT, nparts), kBT, 0, c->stream>>>(n, npad, nparts, X, Y, Z, f4, comp, nbr,
+                                                                       partD, partJ, flags, flags + 2);
+      k_nfn_merge<<<nb, 256, 0, c->stream>>>(n, npad, nparts, comp, nbr, nbrD, partD, partJ, flags, flags + 2);
+      k_comp_min<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, flags + 2);
+      k_comp_edge<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, cidx, ccnt, flags, flags + 2);
+      k_hook<<<nb, 256, 0, c->stream>>>(n, comp, nbr, cidx, nxt, eu, ev, flags + 1, flags + 2);
+      k_relabel<<<nb, 256, 0, c->stream>>>(n, comp, nxt, cmin, ccnt, flags + 2);
+      c->launches += 7;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if ((e = cudaMemcpyAsync(c->host_buf, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
       return e;
     if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return e;
-    int fl[2];
+    int fl[4];
     std::memcpy(fl, c->host_buf, sizeof(fl));
     if (fl[0]) {
       *tied = true;
       return cudaSuccess;
     }
     edges = fl[1];
+    c->mst_rounds = fl[3];
   }
   if (edges != n - 1) {  // cannot happen without ties; be safe
     *tied = true;

@@ -51,7 +51,7 @@ struct Dev {
   double* comblk;   // slots x nblk x 3
   double* sc;       // slots x kScal scalars
   double* Tkk;      // extrapolated (X 3 planes, V 3 planes, t)
-  double* epsblk;   // nblk
+  double* epsblk;   // 2 nblk: the edge-position and edge-velocity maxima per block
   double* res;      // small results read by the host: [0] eps, [1] t, [2] U0, [3] T0
   double* mom;      // nblk x 8 block partials of T, P, L
   char* dc;         // divide-and-conquer tree scratch (mst_method 1 only)
@@ -89,6 +89,8 @@ struct mstar_ctx {
   cudaEvent_t br_fork = nullptr, br_join[mstar::kMaxKfix] = {};
   int pair_defer = -1;  // trailing slots of a pair launch summed by the finishing pass (-1: unset)
   size_t rebuild_smem = 0;  // shared memory of the staged rebuild (0: the plain kernel is used)
+  int sub_cluster = 0;      // CTAs of the cluster that runs a division's substep level (0: the multi-kernel path)
+  int sub_groups = 0;       // 64-body blocks per CTA of that cluster
   int nblk = 0;
   mstar_params p{};
   cudaStream_t stream = nullptr;
@@ -102,6 +104,7 @@ struct mstar_ctx {
   // host-side scalar state (the step control of Sec. 2.3-2.4 runs on the host)
   double t = 0.0, B = 0.0, H = 0.0, Mtot = 0.0;
   bool mst_valid = false;  // the MST/edge buffers describe the current state
+  int mst_rounds = 0;      // Boruvka rounds the last exact-MST build ran (issued before its first check)
   bool at_init = false;    // the state is still the one mstar_init set up (no step taken)
   mstar::AdjTraj* traj = nullptr;  // when set, run_attempt records its trajectory here
   long long launches = 0;
@@ -169,6 +172,14 @@ cudaError_t prepare_rebuild(mstar_ctx* c);  // at context creation: the staged r
 // their positions rebuilt
 constexpr int kLevelCtaMax = 256;
 cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau);
+// the same level of a division on a thread-block cluster (kLevelCtaMax < npad <= kSubstepClusterMax),
+// in the level-by-level schedule: bit-identical to the multi-kernel kick, rebuild, shift and drift
+// launches it replaces. Level-by-level steps of Plummer spheres with a central binary took 5-7 %
+// less time with it from 260 to 500 bodies, and 1-2 % more at 640 and 800; beside the pair loops
+// of other divisions (a stream per division) the clusters wait for whole SMs and slow those loops
+constexpr int kSubstepClusterMax = 576;
+cudaError_t prepare_substep_cluster(mstar_ctx* c);  // at context creation; sets sub_cluster
+cudaError_t launch_substep_cluster(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau);
 // a whole attempt's divisions in one launch, one CTA of kDivisionCtaThreads threads each (pair
 // sums included): systems with npad <= kDivisionCtaMax (three tasks of 32 bodies per warp, at
 // most 15 tile pairs of 32 bodies)

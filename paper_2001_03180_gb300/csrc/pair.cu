@@ -375,46 +375,64 @@ k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __r
 // u_p sums m_q / r_pq over partners q > p (each unordered pair once). The trailing slots
 // (blockIdx.y >= keep_from) sum their NT partial slots here (ascending, as the tile kernel does
 // for the other slots).
-__global__ void __launch_bounds__(kBlock)
+//
+// A CTA takes kBlock bodies with kFinishPlanes threads each: thread (c, b) sums plane c (ax, ay,
+// az, u) of body b over the slots, so the four sums run side by side (each in the same order
+// as one thread summing all four), and the first kBlock threads finish the bodies. Where the
+// pass runs beside pair launches of other divisions, which keep the FP64 pipe busy, its share
+// of the pipe grows with its warps.
+constexpr int kFinishPlanes = 4;
+__global__ void __launch_bounds__(kBlock * kFinishPlanes)
 k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const double* __restrict__ m,
               const int* __restrict__ parent, const int* __restrict__ gp, const int* __restrict__ child_off,
               const int* __restrict__ child_idx, const double* __restrict__ sX, const double* __restrict__ P,
               const double* __restrict__ Pt, double* __restrict__ sa, double* __restrict__ Ublk, int nblk,
               int keep_from) {
   __shared__ double scratch[32];
+  __shared__ double splane[kFinishPlanes][kBlock];
   const int slot = slot_lo + blockIdx.y;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  double um = 0.0;
-  if (p < n) {
-    NearAcc acc;
-    if ((int)blockIdx.y >= keep_from) {
-      const double* q = P + (size_t)slot * NT * 4 * npad + p;
+  const int plane = threadIdx.x / kBlock, b = threadIdx.x - plane * kBlock;
+  const int p = blockIdx.x * kBlock + b;
+  const bool deferred = (int)blockIdx.y >= keep_from;
+  if (deferred) {
+    double acc = 0.0;
+    if (p < n) {
+      const double* q = P + (size_t)slot * NT * 4 * npad + (size_t)plane * npad + p;
       int s = 0;
       for (; s + 4 <= NT; s += 4) {
-        double b[4][4];
+        double t[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const double* qs = q + (size_t)(s + k) * 4 * npad;
-          b[k][0] = qs[0];
-          b[k][1] = qs[(size_t)npad];
-          b[k][2] = qs[2 * (size_t)npad];
-          b[k][3] = qs[3 * (size_t)npad];
-        }
+        for (int k = 0; k < 4; ++k) t[k] = q[(size_t)(s + k) * 4 * npad];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          acc.ax += b[k][0];
-          acc.ay += b[k][1];
-          acc.az += b[k][2];
-          acc.u += b[k][3];
-        }
+        for (int k = 0; k < 4; ++k) acc += t[k];
       }
-      for (; s < NT; ++s) {
-        const double* qs = q + (size_t)s * 4 * npad;
-        acc.ax += qs[0];
-        acc.ay += qs[(size_t)npad];
-        acc.az += qs[2 * (size_t)npad];
-        acc.u += qs[3 * (size_t)npad];
+      for (; s < NT; ++s) acc += q[(size_t)s * 4 * npad];
+    }
+    splane[plane][b] = acc;
+    // the block's bodies' partials are read: drop their L2 lines, so that they are not
+    // written back to DRAM when later launches' partials evict them (every slot is written
+    // again before it is next read). NT x 4 runs of kBlock doubles, each starting on a
+    // 512-byte boundary; a line is dropped only where it lies below npad.
+    __syncthreads();
+    constexpr int kLinesPerRun = kBlock / 16;
+    const int b0 = blockIdx.x * kBlock;
+    const double* base = P + (size_t)slot * NT * 4 * npad + b0;
+    for (int l = threadIdx.x; l < NT * 4 * kLinesPerRun; l += blockDim.x) {
+      const int run = l / kLinesPerRun, line = l - run * kLinesPerRun;
+      if (b0 + 16 * line < npad) {
+        const double* a = base + (size_t)run * npad + 16 * line;
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
       }
+    }
+  }
+  double um = 0.0;
+  if (plane == 0 && p < n) {
+    NearAcc acc;
+    if (deferred) {
+      acc.ax = splane[0][b];
+      acc.ay = splane[1][b];
+      acc.az = splane[2][b];
+      acc.u = splane[3][b];
     } else {
       const double* q = Pt + (size_t)slot * 4 * npad + p;
       acc.ax = q[0];
@@ -429,23 +447,8 @@ k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const dou
     a[2 * (size_t)npad] = G * acc.az;
     um = m[p] * acc.u;
   }
-  if ((int)blockIdx.y >= keep_from) {
-    // the block's bodies' partials are read: drop their L2 lines, so that they are not
-    // written back to DRAM when later launches' partials evict them (every slot is written
-    // again before it is next read). NT x 4 runs of kBlock doubles, each starting on a
-    // 512-byte boundary; a line is dropped only where it lies below npad.
-    __syncthreads();
-    constexpr int kLinesPerRun = kBlock / 16;
-    const int b0 = blockIdx.x * kBlock;
-    const double* base = P + (size_t)slot * NT * 4 * npad + b0;
-    for (int l = threadIdx.x; l < NT * 4 * kLinesPerRun; l += kBlock) {
-      const int run = l / kLinesPerRun, line = l - run * kLinesPerRun;
-      if (b0 + 16 * line < npad) {
-        const double* a = base + (size_t)run * npad + 16 * line;
-        asm volatile("discard.global.L2 [%0], 128;" ::"l"(a) : "memory");
-      }
-    }
-  }
+  // the other planes' threads add zeros after the first kBlock threads' sum, so the block sum
+  // is that of the kBlock bodies alone
   const double s = block_sum(um, scratch);
   if (threadIdx.x == 0) Ublk[(size_t)slot * nblk + blockIdx.x] = G * s;
 }
@@ -518,7 +521,7 @@ cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d) {
   }
   if (e != cudaSuccess) return e;
   dim3 grid(c->nblk, nsl);
-  k_pair_finish<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->p.G, c->d.m, c->d.parent,
+  k_pair_finish<<<grid, kBlock * kFinishPlanes, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->p.G, c->d.m, c->d.parent,
                                                 c->d.gp, c->d.child_off, c->d.child_idx, c->d.sX, c->d.P,
                                                 c->d.Pt, c->d.sa, c->d.Ublk, c->nblk, keep_from);
   MSTAR_LAUNCHED(c);

@@ -36,6 +36,11 @@ __device__ __forceinline__ void block_argmin(unsigned long long& k, int& i, unsi
     int i2 = __shfl_down_sync(0xffffffffu, i, o);
     argmin_combine(k, i, k2, i2);
   }
+  if (blockDim.x == 32) {  // one warp: lane 0 holds the minimum
+    k = __shfl_sync(0xffffffffu, k, 0);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    return;
+  }
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (lane == 0) {
     rk[warp] = k;
@@ -237,17 +242,27 @@ k_prim(int n, int npad, const double* __restrict__ r, int* __restrict__ parent_o
       dirty = false;
     }
     // block reduction of the candidate summaries
-    Cand cw = c;
-    for (int o = 16; o > 0; o >>= 1) cand_combine(cw, cand_shfl_down(cw, o));
-    if (lane == 0) rc[warp] = cw;
-    __syncthreads();
-    if (warp == 0) {
-      cw = lane < nw ? rc[lane] : cand_identity();
-      for (int o = 16; o > 0; o >>= 1) cand_combine(cw, cand_shfl_down(cw, o));
-      if (lane == 0) wc = cw;
+    // the warp's summary by warp-wide minima (redux): the least upper bound and its index, the
+    // least lower bound and its index, and the least lower bound other than that one (the
+    // winner's own second bound, or another vertex's least bound); the same values the
+    // pairwise cand_combine tree gives, in every lane
+    Cand cw;
+    cw.hk = __reduce_min_sync(0xffffffffu, c.hk);
+    cw.hidx = (int)__reduce_min_sync(0xffffffffu, c.hk == cw.hk ? (unsigned)c.hidx : 0xffffffffu);
+    cw.l1 = __reduce_min_sync(0xffffffffu, c.l1);
+    cw.l1idx = (int)__reduce_min_sync(0xffffffffu, c.l1 == cw.l1 ? (unsigned)c.l1idx : 0xffffffffu);
+    cw.l2 = __reduce_min_sync(0xffffffffu, (c.l1 == cw.l1 && c.l1idx == cw.l1idx) ? c.l2 : c.l1);
+    if (nw > 1) {
+      if (lane == 0) rc[warp] = cw;
+      __syncthreads();
+      if (warp == 0) {
+        cw = lane < nw ? rc[lane] : cand_identity();
+        for (int o = 16; o > 0; o >>= 1) cand_combine(cw, cand_shfl_down(cw, o));
+        if (lane == 0) wc = cw;
+      }
+      __syncthreads();
+      cw = wc;
     }
-    __syncthreads();
-    cw = wc;
     int nxt;
     if (cw.l1idx == cw.hidx && cw.l2 > cw.hk) {
       nxt = cw.hidx;
@@ -417,6 +432,12 @@ cudaError_t launch_prim(mstar_ctx* c) {
     }
   int nt = ((n + vpt - 1) / vpt + 31) / 32 * 32;
   if (nt < 32) nt = 32;
+  // up to 96 bodies one warp takes every vertex (up to 3 each): its reductions need no
+  // shared-memory stage and no block barrier
+  if (n <= 96) {
+    vpt = (n + 31) / 32;
+    nt = 32;
+  }
   switch (vpt) {
     case 1: return run_prim<1>(c, nt);
     case 2: return run_prim<2>(c, nt);

@@ -9,6 +9,7 @@
 //
 // The drift/kick/rebuild arithmetic uses explicitly rounded FP64 operations (no
 // contraction), the same operation order as the CPU reference.
+#include <algorithm>
 #include <cooperative_groups.h>
 
 #include "device.cuh"
@@ -165,51 +166,58 @@ k_drift(int npad, int slot_lo, const double* __restrict__ par, double B, int tau
   }
 }
 
+// The three components' block sums of m w (kRebuildComps warps-pairs of kBlock threads, one
+// component each) into comblk: each is the sum that block_sum forms over kBlock threads (the
+// same shuffle tree in each of the component's two warps, then the two warp sums added).
+constexpr int kRebuildComps = 3;
+static_assert(kBlock == 64, "the component sums below assume two warps per component");
+__device__ __forceinline__ void component_block_sums(double x, double* scratch, double* out3) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) scratch[warp] = x;
+  __syncthreads();
+  if (threadIdx.x < kRebuildComps) out3[threadIdx.x] = scratch[2 * threadIdx.x] + scratch[2 * threadIdx.x + 1];
+}
+
 // Cartesian vector of every body from edge vectors: the path sum w_v = W_v + W_parent(v)
-// + ... up to the root (root: 0), plus block sums of m w for the centre of mass.
-__global__ void __launch_bounds__(kBlock)
+// + ... up to the root (root: 0), plus block sums of m w for the centre of mass. A CTA takes
+// kBlock bodies with one thread per component, so the three walks of a body run side by side
+// (each adds in the same order as one thread walking all three); beside pair launches of other
+// divisions, which keep the FP64 pipe busy, the walks' share of the pipe grows with their warps.
+__global__ void __launch_bounds__(kBlock * kRebuildComps)
 k_rebuild(int n, int npad, size_t stride, const int* __restrict__ parent, const int* __restrict__ bylev,
           const double* __restrict__ Wb, double* __restrict__ wb, const double* __restrict__ m,
           double* __restrict__ comblk, int nblk) {
-  __shared__ double scratch[32];
+  __shared__ double scratch[2 * kRebuildComps];
   const int slot = blockIdx.y;
-  const double* W = Wb + slot * stride;
-  double* wv = wb + slot * stride;
+  const int comp = threadIdx.x / kBlock, b = threadIdx.x - comp * kBlock;
+  const double* W = Wb + slot * stride + (size_t)comp * npad;
+  double* wv = wb + slot * stride + (size_t)comp * npad;
   // thread i takes body bylev[i]: the lanes of a warp walk paths of about equal length
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * kBlock + b;
   const int v = i < n ? bylev[i] : n;
-  double s[3] = {0.0, 0.0, 0.0};
+  double s = 0.0;
   if (v < n) {
-    for (int u = v; parent[u] >= 0; u = parent[u]) {
-      s[0] = __dadd_rn(s[0], W[u]);
-      s[1] = __dadd_rn(s[1], W[(size_t)npad + u]);
-      s[2] = __dadd_rn(s[2], W[2 * (size_t)npad + u]);
-    }
-    wv[v] = s[0];
-    wv[(size_t)npad + v] = s[1];
-    wv[2 * (size_t)npad + v] = s[2];
+    for (int u = v; parent[u] >= 0; u = parent[u]) s = __dadd_rn(s, W[u]);
+    wv[v] = s;
   }
   const double mv = v < n ? m[v] : 0.0;
-  for (int c = 0; c < 3; ++c) {
-    const double b = block_sum(__dmul_rn(mv, s[c]), scratch);
-    if (threadIdx.x == 0) comblk[((size_t)slot * nblk + blockIdx.x) * 3 + c] = b;
-  }
+  component_block_sums(__dmul_rn(mv, s), scratch, comblk + ((size_t)slot * nblk + blockIdx.x) * 3);
 }
 
 // k_rebuild with the slot's edge vectors (3 planes) and the parents staged in shared memory
 // first, for systems whose 28 npad bytes fit: every hop of a root path then costs a
 // shared-memory load instead of an L2 round trip. Each thread issues its 16-byte cp.async
 // copies back to back and waits for its own; the additions and their order are k_rebuild's.
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock * kRebuildComps)
 k_rebuild_staged(int n, int npad, size_t stride, const int* __restrict__ parent, const int* __restrict__ bylev,
                  const double* __restrict__ Wb, double* __restrict__ wb, const double* __restrict__ m,
                  double* __restrict__ comblk, int nblk) {
   extern __shared__ __align__(16) double sW[];  // 3 npad doubles, then npad parents
   int* sP = reinterpret_cast<int*>(sW + 3 * (size_t)npad);
-  __shared__ double scratch[32];
+  __shared__ double scratch[2 * kRebuildComps];
   const int slot = blockIdx.y;
   const double* W = Wb + slot * stride;
-  double* wv = wb + slot * stride;
   {
     const char* gW = reinterpret_cast<const char*>(W);
     const char* gP = reinterpret_cast<const char*>(parent);
@@ -225,24 +233,18 @@ k_rebuild_staged(int n, int npad, size_t stride, const int* __restrict__ parent,
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int comp = threadIdx.x / kBlock, b = threadIdx.x - comp * kBlock;
+  const double* sWc = sW + (size_t)comp * npad;
+  double* wv = wb + slot * stride + (size_t)comp * npad;
+  const int i = blockIdx.x * kBlock + b;
   const int v = i < n ? bylev[i] : n;
-  double s[3] = {0.0, 0.0, 0.0};
+  double s = 0.0;
   if (v < n) {
-    for (int u = v; sP[u] >= 0; u = sP[u]) {
-      s[0] = __dadd_rn(s[0], sW[u]);
-      s[1] = __dadd_rn(s[1], sW[npad + u]);
-      s[2] = __dadd_rn(s[2], sW[2 * (size_t)npad + u]);
-    }
-    wv[v] = s[0];
-    wv[(size_t)npad + v] = s[1];
-    wv[2 * (size_t)npad + v] = s[2];
+    for (int u = v; sP[u] >= 0; u = sP[u]) s = __dadd_rn(s, sWc[u]);
+    wv[v] = s;
   }
   const double mv = v < n ? m[v] : 0.0;
-  for (int c = 0; c < 3; ++c) {
-    const double b = block_sum(__dmul_rn(mv, s[c]), scratch);
-    if (threadIdx.x == 0) comblk[((size_t)slot * nblk + blockIdx.x) * 3 + c] = b;
-  }
+  component_block_sums(__dmul_rn(mv, s), scratch, comblk + ((size_t)slot * nblk + blockIdx.x) * 3);
 }
 
 // Sum over the CTA, returned to every thread (block_sum leaves it in thread 0).
@@ -353,6 +355,216 @@ k_level_cta(int n, int npad, int slot_lo, int pos_lo, const double* __restrict__
   sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &s_bc[0]);  // ends with a barrier
   level_body(n, npad, slot, slot >= pos_lo, par[0], B, Mtot, tau, s_bc[0], sa + slot * st, m, sP, bylev,
              sV + slot * st, sX + slot * st, sW, sv + slot * st, sr + slot * st, scratch, s_bc, sc);
+}
+
+// One substep level of a division on a thread-block cluster of C CTAs, for systems too large for
+// one CTA (k_level_cta) whose staged edge vectors still fit in shared memory: the kick (k_kick),
+// the velocity rebuild and shift with the kinetic energy (k_rebuild, k_shift), the drift
+// (k_drift) and, when the division kicks again, the position rebuild and shift - six launches,
+// with five cluster barriers in place of the kernel boundaries.
+//
+// Every operation, and every sum's association, is that of the multi-kernel path, so the
+// results are bit-identical to it: the 64-body blocks of those kernels are kept as groups of
+// 3 x 64 threads (one thread per component), dealt out over the cluster's CTAs. The blocks of
+// the tree walks take the bodies in level order (as k_rebuild), those of the element-wise
+// phases in index order (as k_kick, k_shift, k_drift). Each block's partial sums (m w for the
+// centre of mass, m w^2 for the kinetic energy) are written into every CTA's shared memory,
+// and every CTA then adds the nblk partials in sum_partials' order. The edge vectors that a
+// walk needs and the walks' results are exchanged the same way: each value is written by the
+// CTA that computes it into every CTA's copy (distributed shared memory).
+constexpr int kScGroupThreads = 3 * kBlock;  // a 64-body block, one thread per component
+static_assert(kBlock == 64, "the substep cluster's block sums assume two warps per component");
+
+// One CTA's share of a rebuild: the path sums of its level-order blocks over the edge vectors in
+// sW, written with the blocks' centre-of-mass partials into every CTA of the cluster.
+template <int C>
+__device__ __forceinline__ void cluster_walks(int n, int npad, int nblk, int rank, int G, int g, int comp, int b,
+                                              const int* __restrict__ bylev, const double* __restrict__ m,
+                                              const int* sP, const double* sW, double* sQ, double* sCom,
+                                              double* scr) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int t = threadIdx.x - g * kScGroupThreads;
+  const int passes = (nblk + C * G - 1) / (C * G);
+  for (int it = 0; it < passes; ++it) {
+    const int blk = (it * C + rank) * G + g;
+    const int i = blk * kBlock + b;
+    const int v = (blk < nblk && i < n) ? bylev[i] : n;
+    double s = 0.0;
+    if (v < n) {
+      const double* W = sW + (size_t)comp * npad;
+      for (int u = v; sP[u] >= 0; u = sP[u]) s = __dadd_rn(s, W[u]);
+      const size_t o = (size_t)comp * npad + v;
+#pragma unroll
+      for (int r = 0; r < C; ++r) cl.map_shared_rank(sQ, r)[o] = s;
+    }
+    double x = __dmul_rn(v < n ? m[v] : 0.0, s);
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) scr[g * 6 + (t >> 5)] = x;
+    __syncthreads();
+    if (t < 3 && blk < nblk) {
+      const double val = scr[g * 6 + 2 * t] + scr[g * 6 + 2 * t + 1];
+#pragma unroll
+      for (int r = 0; r < C; ++r) cl.map_shared_rank(sCom, r)[blk * 3 + t] = val;
+    }
+    __syncthreads();
+  }
+}
+
+// The centre of mass from the blocks' partials (warp c sums component c in sum_partials' order)
+// into s_com[0..2]; holds a barrier.
+__device__ __forceinline__ void cluster_com(int nblk, const double* sCom, double* s_com) {
+  const int tid = threadIdx.x;
+  if (tid < 96) {
+    const int c = tid >> 5, lane = tid & 31;
+    double s = 0.0;
+    for (int bb = lane; bb < nblk; bb += 32) s += sCom[bb * 3 + c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) s_com[c] = s;
+  }
+  __syncthreads();
+}
+
+template <int C>
+__global__ void __launch_bounds__(kScGroupThreads * 5)
+k_substep_cluster(int n, int npad, int nblk, int slot_lo, int pos_lo, int tau, const double* __restrict__ par,
+                  double B, double Mtot, const double* __restrict__ m, const int* __restrict__ parent,
+                  const int* __restrict__ bylev, const double* __restrict__ sa, double* __restrict__ sV,
+                  double* __restrict__ sv, double* __restrict__ sX, double* __restrict__ sr,
+                  const double* __restrict__ Ublk, double* __restrict__ Tblk, double* __restrict__ sc) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  // shared: staged edge vectors (3 npad), walk results (3 npad), centre-of-mass partials
+  // (3 nblk), kinetic partials (nblk), parents (npad ints)
+  extern __shared__ __align__(16) double sub_sh[];
+  double* sW = sub_sh;
+  double* sQ = sW + 3 * (size_t)npad;
+  double* sCom = sQ + 3 * (size_t)npad;
+  double* sT = sCom + 3 * (size_t)nblk;
+  int* sP = reinterpret_cast<int*>(sT + nblk);
+  __shared__ double scr[5 * 6];
+  __shared__ double s_sc[4];
+  __shared__ double sq3[5][3][kBlock];
+  const int rank = (int)cl.block_rank();
+  const int slot = slot_lo + (int)blockIdx.x / C;
+  const bool pos = slot >= pos_lo;
+  const int tid = threadIdx.x;
+  const int G = (int)blockDim.x / kScGroupThreads;
+  const int g = tid / kScGroupThreads, t = tid - g * kScGroupThreads;
+  const int comp = t / kBlock, b = t - comp * kBlock;
+  const int passes = (nblk + C * G - 1) / (C * G);
+  const size_t st = (size_t)3 * npad;
+  const double H = par[0];
+  double* V = sV + slot * st;
+  double* X = sX + slot * st;
+  const double* a = sa + slot * st;
+
+  for (int u = tid; u < npad; u += blockDim.x) sP[u] = u < n ? parent[u] : -1;
+  sum_partials(Ublk + (size_t)slot * nblk, nblk, 1, &s_sc[0]);  // ends with a barrier
+  const double U = s_sc[0];
+  cl.sync();  // every CTA of the cluster runs before any writes into its shared memory
+  // K(delta), as k_kick: V_w += (delta / U) (a_w - a_parent(w))
+  const double fk = (H / (double)(2 * (slot + 1))) / U;
+  for (int it = 0; it < passes; ++it) {
+    const int blk = (it * C + rank) * G + g;
+    const int w = blk * kBlock + b;
+    if (blk < nblk && w < npad) {
+      const size_t o = (size_t)comp * npad + w;
+      double x = V[o];
+      if (w < n) {
+        const int p = sP[w];
+        if (p >= 0) {
+          x = madd(x, fk, __dsub_rn(a[o], a[(size_t)comp * npad + p]));
+          V[o] = x;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < C; ++r) cl.map_shared_rank(sW, r)[o] = x;
+    }
+  }
+  if (rank == 0 && tid == 0) sc[slot * kScal + SC_U] = U;
+  cl.sync();
+  // velocity rebuild (k_rebuild), then the shift and the kinetic partials (k_shift)
+  cluster_walks<C>(n, npad, nblk, rank, G, g, comp, b, bylev, m, sP, sW, sQ, sCom, scr);
+  cl.sync();
+  cluster_com(nblk, sCom, &s_sc[1]);
+  double* vout = sv + slot * st;
+  for (int it = 0; it < passes; ++it) {
+    const int blk = (it * C + rank) * G + g;
+    const int w = blk * kBlock + b;
+    const bool own = blk < nblk && w < n;
+    double q = 0.0;
+    if (own) {
+      const size_t o = (size_t)comp * npad + w;
+      q = __dsub_rn(sQ[o], s_sc[1 + comp] / Mtot);
+      vout[o] = q;
+    }
+    sq3[g][comp][b] = q;
+    __syncthreads();
+    if (comp == 0) {
+      double t2 = 0.0;
+      if (own) {
+        const double q0 = sq3[g][0][b], q1 = sq3[g][1][b], q2 = sq3[g][2][b];
+        t2 = __dmul_rn(m[w], __dadd_rn(__dadd_rn(__dmul_rn(q0, q0), __dmul_rn(q1, q1)), __dmul_rn(q2, q2)));
+      }
+      for (int o = 16; o > 0; o >>= 1) t2 += __shfl_down_sync(0xffffffffu, t2, o);
+      if ((t & 31) == 0) scr[g * 6 + (t >> 5)] = t2;
+    }
+    __syncthreads();
+    if (t == 0 && blk < nblk) {
+      const double val = scr[g * 6] + scr[g * 6 + 1];
+      Tblk[(size_t)slot * nblk + blk] = val;
+#pragma unroll
+      for (int r = 0; r < C; ++r) cl.map_shared_rank(sT, r)[blk] = val;
+    }
+    __syncthreads();
+  }
+  cl.sync();
+  // D(h), as k_drift: X += f V, t += f with f = h / (T + B); h = delta, or delta/2 for the last drift
+  if (tid < 32) {
+    double s = 0.0;
+    for (int bb = tid; bb < nblk; bb += 32) s += sT[bb];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (tid == 0) s_sc[0] = s;
+  }
+  __syncthreads();
+  const double T = 0.5 * s_sc[0];
+  const int nk = 2 * (slot + 1);
+  const double delta = H / (double)nk;
+  const double h = (tau == nk) ? 0.5 * delta : delta;
+  const double fd = h / (T + B);
+  for (int it = 0; it < passes; ++it) {
+    const int blk = (it * C + rank) * G + g;
+    const int w = blk * kBlock + b;
+    if (blk < nblk && w < npad) {
+      const size_t o = (size_t)comp * npad + w;
+      const double x = madd(X[o], fd, sW[o]);
+      X[o] = x;
+      if (pos) {
+#pragma unroll
+        for (int r = 0; r < C; ++r) cl.map_shared_rank(sW, r)[o] = x;
+      }
+    }
+  }
+  if (rank == 0 && tid == 0) {
+    sc[slot * kScal + SC_T_PHYS] += fd;
+    sc[slot * kScal + SC_T_KIN] = T;
+  }
+  if (!pos) return;  // nothing of this CTA's shared memory is read by another CTA after the last barrier
+  cl.sync();
+  // position rebuild and shift (k_rebuild, k_shift)
+  cluster_walks<C>(n, npad, nblk, rank, G, g, comp, b, bylev, m, sP, sW, sQ, sCom, scr);
+  cl.sync();
+  cluster_com(nblk, sCom, &s_sc[1]);
+  double* rout = sr + slot * st;
+  for (int it = 0; it < passes; ++it) {
+    const int blk = (it * C + rank) * G + g;
+    const int w = blk * kBlock + b;
+    if (blk < nblk && w < n) {
+      const size_t o = (size_t)comp * npad + w;
+      rout[o] = __dsub_rn(sQ[o], s_sc[1 + comp] / Mtot);
+    }
+  }
 }
 
 // Sum over a warp (lane 0 holds it): a fixed shuffle tree.
@@ -784,14 +996,21 @@ __device__ __forceinline__ double norm3(double x, double y, double z) {
 // (Sec. 4.2), and the error of Eq. gbs-criterion:
 // eps = max_q |T_KK - T_{K-1,K-1}|_q / |S_q(s0) + delta_K S'_q(s0)| over X_v, V_v, t with
 // S' = V / (T0 + B) for X, A0 / U0 for V, 1 / (T0 + B) for t, delta_K = H / n_K.
-__global__ void __launch_bounds__(kBlock)
+// CTA (b, part) takes the 64 bodies of block b with one thread per component, for the edge
+// positions (part 0, which also takes t) or the edge velocities (part 1): the six tableaux of a
+// body run on six threads, and the first thread of each body forms its error term. The maximum
+// over the CTAs' maxima (k_eps_final) does not depend on their order.
+__global__ void __launch_bounds__(3 * kBlock)
 k_extrapolate(int n, int npad, int K, const double* __restrict__ par, double B, const int* __restrict__ parent,
               const double* __restrict__ sX, const double* __restrict__ sV, const double* __restrict__ X0,
               const double* __restrict__ V0, const double* __restrict__ A0, const double* __restrict__ sc,
-              double* __restrict__ Tkk, double* __restrict__ epsblk) {
+              double* __restrict__ Tkk, double* __restrict__ epsblk, int nblk) {
   __shared__ double scratch[32];
+  __shared__ double sd[3][kBlock];
   const double H = par[0], t0 = par[1];
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int part = blockIdx.y;
+  const int comp = threadIdx.x / kBlock, b = threadIdx.x - comp * kBlock;
+  const int v = blockIdx.x * kBlock + b;
   const double T0 = sc[K * kScal + SC_T_KIN], U0 = sc[K * kScal + SC_U];
   const double rate = 1.0 / (T0 + B);
   const double delta = H / (double)(2 * K);
@@ -799,31 +1018,23 @@ k_extrapolate(int n, int npad, int K, const double* __restrict__ par, double B, 
   double e = 0.0;
   if (v < n) {
     double S[kMaxKfix];
-    double dX[3], dV[3];
-    for (int c = 0; c < 3; ++c) {
-      double tkk, tp = 0.0;
-      for (int k = 0; k < K; ++k) S[k] = sX[k * slot_stride + (size_t)c * npad + v];
-      neville(S, K, tkk, tp);
-      Tkk[(size_t)c * npad + v] = tkk;
-      dX[c] = __dsub_rn(tkk, tp);
-      for (int k = 0; k < K; ++k) S[k] = sV[k * slot_stride + (size_t)c * npad + v];
-      neville(S, K, tkk, tp);
-      Tkk[(size_t)(3 + c) * npad + v] = tkk;
-      dV[c] = __dsub_rn(tkk, tp);
-    }
-    if (parent[v] >= 0) {
-      double q[3], g[3];
-      for (int c = 0; c < 3; ++c) {
-        const size_t o = (size_t)c * npad + v;
-        q[c] = madd(X0[o], delta, __dmul_rn(V0[o], rate));
-        g[c] = madd(V0[o], delta, A0[o] / U0);
-      }
-      const double rx = norm3(dX[0], dX[1], dX[2]) / fmax(norm3(q[0], q[1], q[2]), 1e-300);
-      const double rv = norm3(dV[0], dV[1], dV[2]) / fmax(norm3(g[0], g[1], g[2]), 1e-300);
-      e = nanmax(rx, rv);
-    }
+    const double* src = part == 0 ? sX : sV;
+    double tkk, tp = 0.0;
+    for (int k = 0; k < K; ++k) S[k] = src[k * slot_stride + (size_t)comp * npad + v];
+    neville(S, K, tkk, tp);
+    Tkk[(size_t)(3 * part + comp) * npad + v] = tkk;
+    sd[comp][b] = __dsub_rn(tkk, tp);
   }
-  if (v == 0) {
+  __syncthreads();
+  if (comp == 0 && v < n && parent[v] >= 0) {
+    double q[3];
+    for (int c = 0; c < 3; ++c) {
+      const size_t o = (size_t)c * npad + v;
+      q[c] = part == 0 ? madd(X0[o], delta, __dmul_rn(V0[o], rate)) : madd(V0[o], delta, A0[o] / U0);
+    }
+    e = norm3(sd[0][b], sd[1][b], sd[2][b]) / fmax(norm3(q[0], q[1], q[2]), 1e-300);
+  }
+  if (part == 0 && v == 0 && comp == 0) {
     double S[kMaxKfix];
     for (int k = 0; k < K; ++k) S[k] = sc[k * kScal + SC_T_PHYS];
     double tkk, tp = 0.0;
@@ -832,8 +1043,8 @@ k_extrapolate(int n, int npad, int K, const double* __restrict__ par, double B, 
     const double rt = fabs(__dsub_rn(tkk, tp)) / fmax(fabs(madd(t0, delta, rate)), 1e-300);
     e = nanmax(e, rt);
   }
-  const double b = block_nanmax(e, scratch);
-  if (threadIdx.x == 0) epsblk[blockIdx.x] = b;
+  const double bm = block_nanmax(e, scratch);
+  if (threadIdx.x == 0) epsblk[(size_t)part * nblk + blockIdx.x] = bm;
 }
 
 __global__ void k_eps_final(int npad, const double* __restrict__ epsblk, int nblk, const double* __restrict__ Tkk,
@@ -943,10 +1154,10 @@ cudaError_t launch_rebuild(mstar_ctx* c, const double* W, double* w, size_t stri
   const size_t staged = (size_t)c->npad * (3 * sizeof(double) + sizeof(int));
   cudaError_t e;
   if (staged <= c->rebuild_smem) {
-    k_rebuild_staged<<<grid, kBlock, staged, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w,
+    k_rebuild_staged<<<grid, kBlock * kRebuildComps, staged, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w,
                                                            c->d.m, comblk_base, c->nblk);
   } else {
-    k_rebuild<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w, c->d.m,
+    k_rebuild<<<grid, kBlock * kRebuildComps, 0, c->stream>>>(c->n, c->npad, stride, c->d.parent, c->d.bylev, W, w, c->d.m,
                                               comblk_base, c->nblk);
   }
   MSTAR_LAUNCHED(c);
@@ -1053,6 +1264,99 @@ cudaError_t launch_level_cta(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo,
   return cudaGetLastError();
 }
 
+size_t substep_cluster_smem(int npad, int nblk) {
+  return (size_t)(6 * (size_t)npad + 4 * (size_t)nblk) * sizeof(double) + (size_t)npad * sizeof(int);
+}
+
+template <int Cl>
+int substep_clusters_resident(const mstar_ctx* c, int G) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(Cl);
+  cfg.blockDim = dim3(kScGroupThreads * G);
+  cfg.dynamicSmemBytes = substep_cluster_smem(c->npad, c->nblk);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = Cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int num = 0;
+  if (cudaOccupancyMaxActiveClusters(&num, k_substep_cluster<Cl>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return num;
+}
+
+// At context creation, for kLevelCtaMax < npad <= kSubstepClusterMax: the cluster substep
+// kernel's shared memory, and the largest cluster of up to 8 CTAs that the device can launch
+// (c->sub_cluster stays 0, and the multi-kernel path serves, if none can).
+cudaError_t prepare_substep_cluster(mstar_ctx* c) {
+  c->sub_cluster = 0;
+  if (c->npad <= kLevelCtaMax || c->npad > kSubstepClusterMax) return cudaSuccess;
+  const int smem = (int)substep_cluster_smem(c->npad, c->nblk);
+  cudaError_t e = cudaFuncSetAttribute(k_substep_cluster<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substep_cluster<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_substep_cluster<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  for (int Cl = 8; Cl >= 2; Cl /= 2) {
+    const int G = std::min(5, (c->nblk + Cl - 1) / Cl);
+    int num = 0;
+    switch (Cl) {
+      case 8: num = substep_clusters_resident<8>(c, G); break;
+      case 4: num = substep_clusters_resident<4>(c, G); break;
+      default: num = substep_clusters_resident<2>(c, G); break;
+    }
+    if (num > 0) {
+      c->sub_cluster = Cl;
+      c->sub_groups = G;
+      return cudaSuccess;
+    }
+  }
+  return cudaSuccess;
+}
+
+template <int Cl>
+cudaError_t launch_substep_cluster_c(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(Cl * (slot_hi - slot_lo));
+  cfg.blockDim = dim3(kScGroupThreads * c->sub_groups);
+  cfg.dynamicSmemBytes = substep_cluster_smem(c->npad, c->nblk);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = Cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_substep_cluster<Cl>, c->n, c->npad, c->nblk, slot_lo, pos_lo, tau,
+                            (const double*)(c->d.res + 4), c->B, c->Mtot, (const double*)c->d.m,
+                            (const int*)c->d.parent, (const int*)c->d.bylev, (const double*)c->d.sa, c->d.sV,
+                            c->d.sv, c->d.sX, c->d.sr, (const double*)c->d.Ublk, c->d.Tblk, c->d.sc);
+}
+
+// One substep level (kick, velocity rebuild, drift, position rebuild) of the divisions
+// [slot_lo, slot_hi) in one launch, a cluster of c->sub_cluster CTAs per division; the
+// divisions >= pos_lo get their positions rebuilt.
+cudaError_t launch_substep_cluster(mstar_ctx* c, int slot_lo, int slot_hi, int pos_lo, int tau) {
+  if (slot_hi <= slot_lo) return cudaSuccess;
+  cudaError_t e;
+  switch (c->sub_cluster) {
+    case 8: e = launch_substep_cluster_c<8>(c, slot_lo, slot_hi, pos_lo, tau); break;
+    case 4: e = launch_substep_cluster_c<4>(c, slot_lo, slot_hi, pos_lo, tau); break;
+    case 2: e = launch_substep_cluster_c<2>(c, slot_lo, slot_hi, pos_lo, tau); break;
+    default: return cudaErrorInvalidValue;
+  }
+  MSTAR_LAUNCHED(c);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 // Allows the staged rebuild kernel the shared memory a context of this size needs (at
 // context creation, outside any stream capture); larger systems keep k_rebuild.
 cudaError_t prepare_rebuild(mstar_ctx* c) {
@@ -1067,13 +1371,13 @@ cudaError_t prepare_rebuild(mstar_ctx* c) {
 }
 
 cudaError_t launch_extrapolate(mstar_ctx* c) {
-  k_extrapolate<<<c->nblk, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B, c->d.parent, c->d.sX,
-                                                  c->d.sV, c->d.X0, c->d.V0, c->d.A0, c->d.sc, c->d.Tkk,
-                                                  c->d.epsblk);
+  k_extrapolate<<<dim3(c->nblk, 2), 3 * kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B,
+                                                                c->d.parent, c->d.sX, c->d.sV, c->d.X0, c->d.V0,
+                                                                c->d.A0, c->d.sc, c->d.Tkk, c->d.epsblk, c->nblk);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_eps_final<<<1, kBlock, 0, c->stream>>>(c->npad, c->d.epsblk, c->nblk, c->d.Tkk, c->d.res);
+  k_eps_final<<<1, kBlock, 0, c->stream>>>(c->npad, c->d.epsblk, 2 * c->nblk, c->d.Tkk, c->d.res);
   MSTAR_LAUNCHED(c);
   return cudaGetLastError();
 }
