@@ -29,11 +29,37 @@ __device__ __forceinline__ double d2_exact(const double* X, const double* Y, con
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// Float bounds of the FP64 squared distance ((dx*dx)+(dy*dy))+(dz*dz) of two vertices from
+// their float copies: each coordinate difference errs by at most (|x_i| + |x_j|) 2^-24 + |dx|
+// 2^-24, and e = e_i + e_j holds (max|coordinate_i| + max|coordinate_j|) 2^-23 + 2e-37.
+// (1 -/+ 2^-20) covers the relative rounding of the float sums of squares and the FP64
+// distance's own (< 2^-50); 2^-144 the absolute rounding (<= 2^-150 per operation) of squares
+// and sums below 2^-126. Overflowing squares make hi infinite, which bounds nothing away.
+__device__ __forceinline__ float d2_lower(float dx, float dy, float dz, float e) {
+  const float lx = fmaxf(fmaf(dx, -0x1p-22f, dx) - e, 0.0f);
+  const float ly = fmaxf(fmaf(dy, -0x1p-22f, dy) - e, 0.0f);
+  const float lz = fmaxf(fmaf(dz, -0x1p-22f, dz) - e, 0.0f);
+  return fmaxf(((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f) - 0x1p-144f, 0.0f);
+}
+__device__ __forceinline__ float d2_upper(float dx, float dy, float dz, float e) {
+  const float hx = fmaf(dx, 0x1p-22f, dx) + e, hy = fmaf(dy, 0x1p-22f, dy) + e, hz = fmaf(dz, 0x1p-22f, dz) + e;
+  return ((hx * hx + hy * hy) + hz * hz) * (1.0f + 0x1p-20f) + 0x1p-144f;
+}
+
+constexpr int kNfnList = 4;  // candidates a thread lists for exact evaluation
+
 // Nearest foreign neighbour (smallest exact squared distance to a vertex of another
 // component) of every vertex whose cached neighbour is missing or has become internal;
 // CTA (tile, part) scans the part-th slice of the candidates. Writes per (vertex, part)
 // the exact distance bits and the neighbour; exact equal distances to two different
-// candidates set *tie.
+// candidates at the minimum set *tie.
+//
+// Three steps, so that the FP64 distances (and their divergent, long-latency code) run only
+// for the few candidates that can be the nearest: the least float upper bound over the
+// foreign candidates; the candidates whose float lower bound does not exceed it, listed in
+// index order (a candidate above it is strictly farther than the nearest); their exact
+// distances. A vertex with more than kNfnList listed candidates scans the part again, taking
+// the exact distance of every candidate whose lower bound does not exceed the bound.
 __global__ void __launch_bounds__(kBT)
 k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* __restrict__ Y,
       const double* __restrict__ Z, const float* __restrict__ f4, const int* __restrict__ comp,
@@ -42,6 +68,7 @@ k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* _
   if (*stop) return;
   __shared__ float sx[kBT], sy[kBT], sz[kBT], se[kBT];
   __shared__ int sc[kBT];
+  __shared__ int slist[kNfnList][kBT];
   __shared__ int any;
   const int i = blockIdx.x * kBT + threadIdx.x;
   const int part = blockIdx.y;
@@ -59,56 +86,66 @@ k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* _
   if (!any) return;
   const float xi = i < n ? f4[4 * i] : 0.0f, yi = i < n ? f4[4 * i + 1] : 0.0f, zi = i < n ? f4[4 * i + 2] : 0.0f;
   const float ei = i < n ? f4[4 * i + 3] : 0.0f;
-  // running best: exact distance bits, index, and a float upper bound (with margin)
-  unsigned long long bD = ~0ull;
-  int bj = -1;
-  float bhi = __int_as_float(0x7f800000);
-  int mytie = 0;
   const int per = (n + nparts - 1) / nparts;
   const int j_lo = part * per, j_hi = min(n, j_lo + per);
-  for (int t0 = j_lo; t0 < j_hi; t0 += kBT) {
-    __syncthreads();
-    const int j = t0 + threadIdx.x;
-    if (j < j_hi) {
-      sx[threadIdx.x] = f4[4 * j];
-      sy[threadIdx.x] = f4[4 * j + 1];
-      sz[threadIdx.x] = f4[4 * j + 2];
-      se[threadIdx.x] = f4[4 * j + 3];
-      sc[threadIdx.x] = comp[j];
-    }
-    __syncthreads();
-    if (!need) continue;
-    const int cnt = min(kBT, j_hi - t0);
-    for (int q = 0; q < cnt; ++q) {
-      // a lower bound of |r_i - r_j|^2 from the float copies: each coordinate difference
-      // errs by at most (|x_i| + |x_j| + |dx|) 2^-24; ei, ej hold max|coordinate| 2^-23.
-      const float dx = fabsf(xi - sx[q]), dy = fabsf(yi - sy[q]), dz = fabsf(zi - sz[q]);
-      const float e = ei + se[q];
-      const float lx = fmaxf(fmaf(dx, -0x1p-22f, dx) - e, 0.0f);
-      const float ly = fmaxf(fmaf(dy, -0x1p-22f, dy) - e, 0.0f);
-      const float lz = fmaxf(fmaf(dz, -0x1p-22f, dz) - e, 0.0f);
-      // (1 - 2^-20) covers the relative rounding of normal results; 2^-144 the absolute
-      // rounding (<= 2^-150 per operation) of squares and sums that fall below 2^-126
-      const float lo = fmaxf(((lx * lx + ly * ly) + lz * lz) * (1.0f - 0x1p-20f) - 0x1p-144f, 0.0f);
-      if (lo <= bhi && sc[q] != ci) {
-        const int jj = t0 + q;
-        const double d = d2_exact(X, Y, Z, i, jj);
-        const unsigned long long db = key_bits(d);
-        if (db < bD) {
-          bD = db;
-          bj = jj;
-          bhi = __double2float_ru(d) * (1.0f + 0x1p-20f);
-        } else if (db == bD && jj != bj) {
-          mytie = 1;
+  float bhi = __int_as_float(0x7f800000);
+  int listed = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int t0 = j_lo; t0 < j_hi; t0 += kBT) {
+      __syncthreads();
+      const int j = t0 + threadIdx.x;
+      if (j < j_hi) {
+        sx[threadIdx.x] = f4[4 * j];
+        sy[threadIdx.x] = f4[4 * j + 1];
+        sz[threadIdx.x] = f4[4 * j + 2];
+        se[threadIdx.x] = f4[4 * j + 3];
+        sc[threadIdx.x] = comp[j];
+      }
+      __syncthreads();
+      if (!need) continue;
+      const int cnt = min(kBT, j_hi - t0);
+      if (pass == 0) {
+        for (int q = 0; q < cnt; ++q) {
+          const float h = d2_upper(fabsf(xi - sx[q]), fabsf(yi - sy[q]), fabsf(zi - sz[q]), ei + se[q]);
+          if (sc[q] != ci) bhi = fminf(bhi, h);
+        }
+      } else {
+        for (int q = 0; q < cnt; ++q) {
+          const float lo = d2_lower(fabsf(xi - sx[q]), fabsf(yi - sy[q]), fabsf(zi - sz[q]), ei + se[q]);
+          if (lo <= bhi && sc[q] != ci) {
+            if (listed < kNfnList) slist[listed][threadIdx.x] = t0 + q;
+            ++listed;
+          }
         }
       }
     }
   }
-  if (need) {
-    partD[(size_t)part * npad + i] = bD;
-    partJ[(size_t)part * npad + i] = bj;
-    if (mytie) atomicOr(tie, 1);
+  if (!need) return;
+  unsigned long long bD = ~0ull;
+  int bj = -1;
+  int mytie = 0;
+  auto consider = [&](int jj) {
+    const unsigned long long db = key_bits(d2_exact(X, Y, Z, i, jj));
+    if (db < bD) {
+      bD = db;
+      bj = jj;
+    } else if (db == bD && jj != bj) {
+      mytie = 1;
+    }
+  };
+  if (listed <= kNfnList) {
+    for (int k = 0; k < listed; ++k) consider(slist[k][threadIdx.x]);
+  } else {
+    for (int jj = j_lo; jj < j_hi; ++jj) {
+      if (comp[jj] == ci) continue;
+      const float lo = d2_lower(fabsf(xi - f4[4 * jj]), fabsf(yi - f4[4 * jj + 1]), fabsf(zi - f4[4 * jj + 2]),
+                                ei + f4[4 * jj + 3]);
+      if (lo <= bhi) consider(jj);
+    }
   }
+  partD[(size_t)part * npad + i] = bD;
+  partJ[(size_t)part * npad + i] = bj;
+  if (mytie) atomicOr(tie, 1);
 }
 
 // Merge the parts: exact minimum, ties flagged; cache the neighbour.

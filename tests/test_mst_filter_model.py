@@ -170,3 +170,56 @@ def test_prim_key_interval_and_quick_test():
         a = ad.max(axis=1)
         quick = ((a.astype(np.float64) * (1.0 - 2.0 ** -22)).astype(np.float32) - (eu + ew)).astype(np.float64)
         assert np.all(quick <= np.sqrt(d) * (1 + 2.0 ** -50))
+
+
+def _grow(d, e):
+    """fmaf(d, 2^-22, d) + e: the fmaf is exact in float64, then rounded once; then the sum."""
+    t = (d.astype(np.float64) * (1.0 + 2.0 ** -22)).astype(np.float32)
+    return (t + e).astype(np.float32)
+
+
+def _upper_plain(hx, hy, hz):
+    return (((hx * hx + hy * hy) + hz * hz) * F(1.0 + 2.0 ** -20) + MARGIN).astype(np.float32)
+
+
+def _upper_fused(hx, hy, hz):
+    """The upper bound with the additions contracted (fma(hz, hz, fma(hy, hy, hx*hx)), then
+    fma(s, 2^-20, s) + margin), as the compiler may emit it."""
+    out = np.empty(len(hx), np.float32)
+    for k in range(len(hx)):
+        s = _fma32(hz[k], hz[k], _fma32(hy[k], hy[k], hx[k] * hx[k]))
+        out[k] = _fma32(s, F(2.0 ** -20), s) + MARGIN
+    return out
+
+
+def test_nearest_neighbour_upper_bound_never_falls_below_the_fp64_distance():
+    """k_nfn's first step takes the least float upper bound over a vertex's candidates and
+    lists only the candidates whose lower bound does not exceed it: safe only if the upper
+    bound is never below the FP64 squared distance (overflow gives inf, which is safe)."""
+    rng = np.random.default_rng(31)
+    with np.errstate(over="ignore"):
+        for ri, rj in _cases(rng, 20000):
+            fi, fj = _f32_of(ri), _f32_of(rj)
+            e = _err_bound(fi[:, 0], fi[:, 1], fi[:, 2]) + _err_bound(fj[:, 0], fj[:, 1], fj[:, 2])
+            hx, hy, hz = (_grow(np.abs(fi[:, c] - fj[:, c]), e) for c in range(3))
+            d = _d2_exact(ri[:, 0], ri[:, 1], ri[:, 2], rj[:, 0], rj[:, 1], rj[:, 2])
+            hi = _upper_plain(hx, hy, hz).astype(np.float64)
+            assert np.all(hi >= d), (hi[hi < d][:4], d[hi < d][:4])
+            sub = np.concatenate([np.flatnonzero(d < 1e-36)[:300], np.arange(300)])
+            hf = _upper_fused(hx[sub], hy[sub], hz[sub]).astype(np.float64)
+            assert np.all(hf >= d[sub])
+
+
+def test_nearest_neighbour_bounds_are_tight():
+    """For well separated pairs the upper bound is within 1e-5 of the distance, so the listed
+    candidates are those within about 1e-5 of the nearest."""
+    rng = np.random.default_rng(32)
+    ri = rng.uniform(-1, 1, (1000, 3))
+    rj = rng.uniform(-1, 1, (1000, 3))
+    fi, fj = _f32_of(ri), _f32_of(rj)
+    e = _err_bound(fi[:, 0], fi[:, 1], fi[:, 2]) + _err_bound(fj[:, 0], fj[:, 1], fj[:, 2])
+    hx, hy, hz = (_grow(np.abs(fi[:, c] - fj[:, c]), e) for c in range(3))
+    d = _d2_exact(ri[:, 0], ri[:, 1], ri[:, 2], rj[:, 0], rj[:, 1], rj[:, 2])
+    hi = _upper_plain(hx, hy, hz).astype(np.float64)
+    ok = d > 1e-2
+    assert np.all(hi[ok] < d[ok] * (1 + 1e-5))
