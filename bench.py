@@ -55,9 +55,9 @@ L2_FLUSH_BYTES = 256 << 20
 #  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
 #    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
 #  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
-PAIR_TILE_SRC_SHA = "dd6ba7c4c9d94726"
-PAIR_TILE_PIPE_SRC_SHA = "dd6ba7c4c9d94726"
-PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 1.001e6, 2: 0.228e6, 3: 0.676e6, 4: 1.710e6, 5: 2.687e6, 6: 3.687e6, 7: 4.999e6, 8: 7.308e6}
+PAIR_TILE_SRC_SHA = "93955719e3540027"
+PAIR_TILE_PIPE_SRC_SHA = "93955719e3540027"
+PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 1.041e6, 2: 0.228e6, 3: 0.622e6, 4: 1.555e6, 5: 2.581e6, 6: 3.603e6, 7: 4.897e6, 8: 10.164e6}
 PAIR_TILE_FP64_PIPE_NCU = 0.870
 ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 # Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
@@ -105,6 +105,9 @@ def parse():
                     help="skip the single-system extras (small configurations, tree builders, rebuild test, adjoint)")
     ap.add_argument("--no-single-context", action="store_true",
                     help="skip timing the one-context-per-system path beside the batch")
+    ap.add_argument("--pair-tile", default=None,
+                    help="TILExSPLIT (e.g. 128x1) for the headline steps instead of the tuner's pick (profiling: "
+                         "under a profiler the tuner's serialised timings can pick another tiling)")
     return ap.parse_args()
 
 
@@ -567,6 +570,8 @@ def run_mstar(args):
     n = len(m)
     # the pair loop's tiling, timed on this system before anything is measured (setup)
     (tile, split), tile_ms = tuned_pair_loop(M, m, r, v, repeats=2)
+    if args.pair_tile:
+        tile, split = (int(x) for x in args.pair_tile.lower().split("x"))
     g = M.Integrator(m, r, v, device=dev, pair_tile=tile, pair_split=split)
     stream = g.stream
     e_init = g.energy()["E"]
