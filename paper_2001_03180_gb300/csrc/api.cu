@@ -86,6 +86,7 @@ size_t carve(const Shape& s, void* base, Dev* d, double** stage) {
   t.sa = c.take<double>(S * n3);
   t.P = c.take<double>(S * (size_t)s.NT * 4 * np);
   t.Pt = c.take<double>(S * 4 * np);
+  t.Nb = c.take<double>(S * 4 * np);
   t.tcnt = c.take<int>(S * (size_t)s.NT);
   t.Ublk = c.take<double>(S * s.nblk);
   t.Tblk = c.take<double>(S * s.nblk);

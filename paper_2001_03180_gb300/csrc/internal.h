@@ -45,6 +45,7 @@ struct Dev {
   double* sa;
   double* P;        // pair partials: slots x NT x 4 x npad
   double* Pt;       // their sums per body: slots x 4 x npad (ax, ay, az, sum of m/r)
+  double* Nb;       // the near pairs' sums per body: slots x 4 x npad (written by the pair launches)
   int* tcnt;        // per slot and tile, the tile-pair CTAs counted in (0 between launches)
   double* Ublk;     // slots x nblk
   double* Tblk;     // slots x nblk

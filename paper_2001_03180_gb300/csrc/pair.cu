@@ -96,19 +96,44 @@ __device__ __forceinline__ void finish_tile(int t, int npad, int NT, const doubl
   if (tid == 0) cnt[t] = 0;
 }
 
+// The near pairs of Sec. 3.4 (N_d <= 2) of the CTA's bodies, one per thread, into Nb (4 planes:
+// ax, ay, az and the sum of m/r over partners of higher index). They depend on the slot's edge
+// vectors alone, so the pair launches take them in CTAs of their own ahead of the tile pairs,
+// and the finishing pass adds them to the tile sums instead of walking the near partners itself.
+__device__ __forceinline__ void near_block(int n, int npad, int slot, int n_d, const double* __restrict__ m,
+                                           const int* __restrict__ parent, const int* __restrict__ gp,
+                                           const int* __restrict__ child_off, const int* __restrict__ child_idx,
+                                           const double* __restrict__ sX, double* __restrict__ Nb) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  NearAcc acc;
+  near_terms(p, npad, n_d, sX + (size_t)slot * 3 * npad, m, parent, gp, child_off, child_idx, acc);
+  double* o = Nb + (size_t)slot * 4 * npad + p;
+  o[0] = acc.ax;
+  o[(size_t)npad] = acc.ay;
+  o[2 * (size_t)npad] = acc.az;
+  o[3 * (size_t)npad] = acc.u;
+}
+
 template <int W>
 __global__ void __launch_bounds__(32 * W)
 k_pair_tiles(int n, int npad, int NT, int slot_lo, int n_d, const double* __restrict__ m,
              const int* __restrict__ parent, const int* __restrict__ gp, const double* __restrict__ sr,
-             double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from) {
+             double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from,
+             const int* __restrict__ child_off, const int* __restrict__ child_idx, const double* __restrict__ sX,
+             double* __restrict__ Nb, int nnear) {
   constexpr int T = 32 * W;
   __shared__ double sx[T], sy[T], sz[T], sax[T], say[T], saz[T];
   __shared__ unsigned long long smm[T];
   __shared__ int sp[T], sg[T], sme[T];
 
   const int slot = slot_lo + blockIdx.y;
+  if ((int)blockIdx.x < nnear) {
+    near_block(n, npad, slot, n_d, m, parent, gp, child_off, child_idx, sX, Nb);
+    return;
+  }
   int I, J;
-  tile_pair(blockIdx.x, NT, I, J);
+  tile_pair((int)blockIdx.x - nnear, NT, I, J);
   const double* rx = sr + (size_t)slot * 3 * npad;
   const double* ry = rx + npad;
   const double* rz = ry + npad;
@@ -239,7 +264,9 @@ template <int S>
 __global__ void __launch_bounds__(32 * S)
 k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __restrict__ m,
                 const int* __restrict__ parent, const int* __restrict__ gp, const double* __restrict__ sr,
-                double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from) {
+                double* __restrict__ P, double* __restrict__ Pt, int* __restrict__ tcnt, int keep_from,
+                const int* __restrict__ child_off, const int* __restrict__ child_idx,
+                const double* __restrict__ sX, double* __restrict__ Nb, int nnear) {
   constexpr int T = 32;
   __shared__ double sx[T], sy[T], sz[T];
   __shared__ double sax[S][T], say[S][T], saz[S][T];     // partner sums, one copy per warp
@@ -247,8 +274,12 @@ k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __r
   __shared__ unsigned long long smm[T];
   __shared__ int sp[T], sg[T], sme[T];
   const int slot = slot_lo + blockIdx.y;
+  if ((int)blockIdx.x < nnear) {
+    near_block(n, npad, slot, n_d, m, parent, gp, child_off, child_idx, sX, Nb);
+    return;
+  }
   int I, J;
-  tile_pair(blockIdx.x, NT, I, J);
+  tile_pair((int)blockIdx.x - nnear, NT, I, J);
   const double* rx = sr + (size_t)slot * 3 * npad;
   const double* ry = rx + npad;
   const double* rz = ry + npad;
@@ -384,10 +415,8 @@ k_pair_tiles_ks(int n, int npad, int NT, int slot_lo, int n_d, const double* __r
 constexpr int kFinishPlanes = 4;
 __global__ void __launch_bounds__(kBlock * kFinishPlanes)
 k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const double* __restrict__ m,
-              const int* __restrict__ parent, const int* __restrict__ gp, const int* __restrict__ child_off,
-              const int* __restrict__ child_idx, const double* __restrict__ sX, const double* __restrict__ P,
-              const double* __restrict__ Pt, double* __restrict__ sa, double* __restrict__ Ublk, int nblk,
-              int keep_from) {
+              const double* __restrict__ Nb, const double* __restrict__ P, const double* __restrict__ Pt,
+              double* __restrict__ sa, double* __restrict__ Ublk, int nblk, int keep_from) {
   __shared__ double scratch[32];
   __shared__ double splane[kFinishPlanes][kBlock];
   const int slot = slot_lo + blockIdx.y;
@@ -440,7 +469,13 @@ k_pair_finish(int n, int npad, int NT, int slot_lo, int n_d, double G, const dou
       acc.az = q[2 * (size_t)npad];
       acc.u = q[3 * (size_t)npad];
     }
-    near_terms(p, npad, n_d, sX + (size_t)slot * 3 * npad, m, parent, gp, child_off, child_idx, acc);
+    if (n_d >= 1) {  // the near pairs, from the pair launch's near CTAs
+      const double* nb = Nb + (size_t)slot * 4 * npad + p;
+      acc.ax += nb[0];
+      acc.ay += nb[(size_t)npad];
+      acc.az += nb[2 * (size_t)npad];
+      acc.u += nb[3 * (size_t)npad];
+    }
     double* a = sa + (size_t)slot * 3 * npad + p;
     a[0] = G * acc.ax;
     a[(size_t)npad] = G * acc.ay;
@@ -475,14 +510,18 @@ int defer_slots(const mstar_ctx* c, K kernel, int threads) {
 
 template <int W, int S>
 cudaError_t run_tiles(mstar_ctx* c, int slot_lo, int nsl, int n_d, int keep_from) {
-  dim3 grid(c->ntp, nsl);
+  constexpr int threads = S == 1 ? 32 * W : 32 * S;
+  const int nnear = n_d >= 1 ? (c->n + threads - 1) / threads : 0;  // the near CTAs come first
+  dim3 grid(nnear + c->ntp, nsl);
   if (c->prof) prof_begin(c);
   if constexpr (S == 1)
     k_pair_tiles<W><<<grid, 32 * W, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
-                                                    c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
+                                                    c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from,
+                                                    c->d.child_off, c->d.child_idx, c->d.sX, c->d.Nb, nnear);
   else
     k_pair_tiles_ks<S><<<grid, 32 * S, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->d.m, c->d.parent,
-                                                       c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from);
+                                                       c->d.gp, c->d.sr, c->d.P, c->d.Pt, c->d.tcnt, keep_from,
+                                                       c->d.child_off, c->d.child_idx, c->d.sX, c->d.Nb, nnear);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -521,9 +560,9 @@ cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d) {
   }
   if (e != cudaSuccess) return e;
   dim3 grid(c->nblk, nsl);
-  k_pair_finish<<<grid, kBlock * kFinishPlanes, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->p.G, c->d.m, c->d.parent,
-                                                c->d.gp, c->d.child_off, c->d.child_idx, c->d.sX, c->d.P,
-                                                c->d.Pt, c->d.sa, c->d.Ublk, c->nblk, keep_from);
+  k_pair_finish<<<grid, kBlock * kFinishPlanes, 0, c->stream>>>(c->n, c->npad, c->NT, slot_lo, n_d, c->p.G,
+                                                                c->d.m, c->d.Nb, c->d.P, c->d.Pt, c->d.sa,
+                                                                c->d.Ublk, c->nblk, keep_from);
   MSTAR_LAUNCHED(c);
   c->force_evals += nsl;
   return cudaGetLastError();
