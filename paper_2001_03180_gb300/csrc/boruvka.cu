@@ -281,7 +281,6 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
   __shared__ unsigned long long rk[32];
   __shared__ int ri[32];
   __shared__ int part[1024];
-  __shared__ int qtail;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int v = tid; v < n; v += nt) {
     s_a[v] = 0;
@@ -335,19 +334,11 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
   const int b0 = tid * chunk, b1 = min(n, b0 + chunk);
   int sum = 0;
   for (int v = b0; v < b1; ++v) sum += s_a[v];
-  part[tid] = sum;
-  __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int t = 0; t < nt; ++t) {
-      const int x = part[t];
-      part[t] = acc;
-      acc += x;
-    }
-    s_off[n] = acc;
+  {
+    int total;
+    sum = block_exclusive_scan(sum, part, &total);
+    if (tid == 0) s_off[n] = total;
   }
-  __syncthreads();
-  sum = part[tid];
   for (int v = b0; v < b1; ++v) {
     s_off[v] = sum;
     sum += s_a[v];
@@ -366,34 +357,52 @@ k_orient(int n, const double* __restrict__ X, const double* __restrict__ Y, cons
   if (tid == 0) {
     s_a[root] = -1;
     s_q[0] = root;
-    qtail = 1;
     root_out[0] = root;
   }
   __syncthreads();
-  // Level by level: [h, t) is the current level. Every thread reads the level's end t before
-  // the barrier, and no thread appends to the queue before it, so all threads see the same
-  // t, take the same number of turns and leave the loop together.
-  int h = 0, depth = 0;
-  while (true) {
-    const int t = min(qtail, n);
-    __syncthreads();
-    if (h >= t) break;
-    for (int q = h + tid; q < t; q += nt) {
-      const int u = s_q[q];
-      level[u] = depth;
-      for (int a = s_off[u]; a < s_off[u + 1]; ++a) {
-        const int w = s_adj[a];
-        if (s_a[w] == -2) {  // a tree: w is reached from u only
-          s_a[w] = u;
-          const int slot = atomicAdd(&qtail, 1);
-          if (slot < n) s_q[slot] = w;
+  // Level by level in warp 0: [h, t) is the current level, taken 32 vertices at a time, one per
+  // lane. Each lane walks its vertex's neighbours; in every round the lanes that found an
+  // unvisited neighbour append it at their rank among them (ballot), so the queue order is
+  // fixed given the adjacency lists and no block barrier is needed between levels (a level holds ~35 vertices on average
+  // at N = 2050, where 59 levels with block barriers cost about 1 us each). In a tree a vertex
+  // is reached from its parent only, so no vertex is appended twice. (Parent and level do not
+  // depend on the order of the adjacency lists, which the atomic fill above leaves open.)
+  if (tid < 32) {
+    const int lane = tid;
+    const unsigned lt = (1u << lane) - 1u;
+    int h = 0, t = 1, depth = 0;
+    while (h < t) {
+      int tail = t;
+      for (int base = h; base < t; base += 32) {
+        const int q = base + lane;
+        const int u = q < t ? s_q[q] : -1;
+        if (u >= 0) level[u] = depth;
+        int a = u >= 0 ? s_off[u] : 0;
+        const int aend = u >= 0 ? s_off[u + 1] : 0;
+        while (__any_sync(0xffffffffu, a < aend)) {
+          int w = -1;
+          if (a < aend) {
+            w = s_adj[a];
+            ++a;
+            if (s_a[w] != -2) w = -1;
+          }
+          const unsigned found = __ballot_sync(0xffffffffu, w >= 0);
+          if (w >= 0) {
+            s_a[w] = u;
+            const int slot = tail + __popc(found & lt);
+            if (slot < n) s_q[slot] = w;
+          }
+          tail += __popc(found);
+          __syncwarp();  // this round's marks and appends are seen by every lane in the next
         }
+        __syncwarp();
       }
+      h = t;
+      t = min(tail, n);
+      ++depth;
     }
-    h = t;
-    ++depth;
-    __syncthreads();
   }
+  __syncthreads();
   for (int v = tid; v < n; v += nt) {
     parent[v] = s_a[v];
     queue[v] = s_q[v];

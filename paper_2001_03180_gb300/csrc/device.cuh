@@ -338,6 +338,32 @@ __device__ __forceinline__ double block_nanmax(double x, double* scratch) {
   return s;
 }
 
+// Exclusive prefix sum of one int per thread over the block (blockDim a multiple of 32, at most
+// 1024): shuffle scans within the warps, then of the warp totals in warp 0. *total receives the
+// block's sum. Every thread must call it (it holds barriers); ws: 32 ints of shared memory.
+__device__ __forceinline__ int block_exclusive_scan(int x, int* ws, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int incl = x;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) ws[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? ws[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    ws[lane] = w;  // inclusive totals of the warps
+  }
+  __syncthreads();
+  const int before = warp > 0 ? ws[warp - 1] : 0;
+  *total = ws[nw - 1];
+  return before + incl - x;
+}
+
 // Sum of nb per-block partials in a fixed order, computed by warp 0 of every block that
 // needs it (so every block obtains bit-identical values); result broadcast via *out.
 __device__ __forceinline__ void sum_partials(const double* part, int nb, int stride, double* out) {

@@ -336,19 +336,11 @@ k_tree(int n, int npad, const int* __restrict__ parent, const int* __restrict__ 
   const int b = tid * chunk, e = min(n, b + chunk);
   int s = 0;
   for (int w = b; w < e; ++w) s += cnt[w];
-  part[tid] = s;
-  __syncthreads();
-  if (tid == 0) {
-    int acc = 0;
-    for (int t = 0; t < nt; ++t) {
-      int x = part[t];
-      part[t] = acc;
-      acc += x;
-    }
-    child_off[n] = acc;
+  {
+    int total;
+    s = block_exclusive_scan(s, part, &total);
+    if (tid == 0) child_off[n] = total;
   }
-  __syncthreads();
-  s = part[tid];
   for (int w = b; w < e; ++w) {
     int x = cnt[w];
     cnt[w] = s;  // now the offset

@@ -11,6 +11,11 @@ level. A warp that ran ahead could then expand its part of the level and append 
 before a slower warp read the tail: the slow warp took a later end, expanded next-level vertices
 a level early (their depth one short) and left the loop out of step with the others. The fixed
 loop puts a barrier between every warp's read of the tail and any append.
+
+The kernel now runs the walk in one warp (`run_warp_ballot` below): a level is taken 32 vertices
+at a time, one per lane; in every round the lanes that found an unvisited neighbour append it at
+their rank among them (a ballot), so there is no shared tail counter, no block barrier, and the
+queue order is fixed given the adjacency lists.
 """
 import numpy as np
 import pytest
@@ -178,3 +183,62 @@ def test_old_loop_fails_under_random_schedules_too():
     for seed in range(60):
         bad += not check(n, edges, root, *run_model(n, edges, root, 4, 8, "random", fixed=False, seed=seed))
     assert bad > 0
+
+
+def run_warp_ballot(n, edges, root, lanes=32):
+    """The one-warp loop of k_orient, lane by lane: the same reads, ballots and appends."""
+    adj = [[] for _ in range(n)]
+    for a, b in edges:
+        adj[a].append(b)
+        adj[b].append(a)
+    s_q = [0] * n
+    s_a = [-2] * n
+    level = [-9] * n
+    s_a[root] = -1
+    s_q[0] = root
+    h, t, depth = 0, 1, 0
+    while h < t:
+        tail = t
+        for base in range(h, t, lanes):
+            us = [s_q[base + ln] if base + ln < t else -1 for ln in range(lanes)]
+            pos = [0] * lanes
+            for ln, u in enumerate(us):
+                if u >= 0:
+                    level[u] = depth
+            while any(u >= 0 and pos[ln] < len(adj[u]) for ln, u in enumerate(us)):
+                found = []
+                for ln, u in enumerate(us):   # every lane reads before any lane writes (one round)
+                    w = -1
+                    if u >= 0 and pos[ln] < len(adj[u]):
+                        w = adj[u][pos[ln]]
+                        pos[ln] += 1
+                        if s_a[w] != -2:
+                            w = -1
+                    found.append(w)
+                rank = 0
+                for ln, w in enumerate(found):
+                    if w >= 0:
+                        s_a[w] = us[ln]
+                        if tail + rank < n:
+                            s_q[tail + rank] = w
+                        rank += 1
+                tail += rank
+        h, t, depth = t, min(tail, n), depth + 1
+    return s_a, level, s_q
+
+
+@pytest.mark.parametrize("tree", ["star", "random40", "random200", "random2050", "path"])
+@pytest.mark.parametrize("lanes", [4, 32])
+def test_one_warp_ballot_loop_is_exact_and_level_ordered(tree, lanes):
+    if tree == "star":
+        edges, root = star_of_paths(arms=40, length=6)
+    elif tree == "path":
+        edges, root = star_of_paths(arms=1, length=70)
+    else:
+        edges, root = random_tree(int(tree[6:]), seed=int(tree[6:]))
+    n = len(edges) + 1
+    s_a, level, s_q = run_warp_ballot(n, edges, root, lanes)
+    assert check(n, edges, root, s_a, level, s_q, False)
+    # the queue lists the tree level by level, and the same order every time
+    assert [level[u] for u in s_q] == sorted(level[u] for u in s_q)
+    assert run_warp_ballot(n, edges, root, lanes)[2] == s_q
