@@ -436,8 +436,12 @@ int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
 // The extrapolated MST coordinates become the Cartesian state (COM frame).
 int accept_state(mstar_ctx* c) {
   const size_t n3 = (size_t)3 * c->npad;
-  CK(launch_rebuild(c, c->d.Tkk, c->d.r, 0, 1, 0, nullptr, c->d.comblk));
-  CK(launch_rebuild(c, c->d.Tkk + n3, c->d.v, 0, 1, 0, nullptr, c->d.comblk));
+  if (c->d.v == c->d.r + n3) {  // positions and velocities in one launch (two slots n3 apart)
+    CK(launch_rebuild(c, c->d.Tkk, c->d.r, n3, 2, 0, nullptr, c->d.comblk));
+  } else {
+    CK(launch_rebuild(c, c->d.Tkk, c->d.r, 0, 1, 0, nullptr, c->d.comblk));
+    CK(launch_rebuild(c, c->d.Tkk + n3, c->d.v, 0, 1, 0, nullptr, c->d.comblk));
+  }
   c->mst_valid = false;
   return MSTAR_OK;
 }
