@@ -338,6 +338,30 @@ __device__ __forceinline__ double block_nanmax(double x, double* scratch) {
   return s;
 }
 
+// sum_partials for three interleaved components (part[b * 3 + c], c = 0, 1, 2) at once, each in
+// sum_partials' order: the three chains overlap instead of running one after another.
+__device__ __forceinline__ void sum_partials3(const double* part, int nb, double* out3) {
+  if (threadIdx.x < 32) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) {
+      s0 += part[(size_t)b * 3];
+      s1 += part[(size_t)b * 3 + 1];
+      s2 += part[(size_t)b * 3 + 2];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_down_sync(0xffffffffu, s0, o);
+      s1 += __shfl_down_sync(0xffffffffu, s1, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
+      out3[0] = s0;
+      out3[1] = s1;
+      out3[2] = s2;
+    }
+  }
+  __syncthreads();
+}
+
 // Exclusive prefix sum of one int per thread over the block (blockDim a multiple of 32, at most
 // 1024): shuffle scans within the warps, then of the warp totals in warp 0. *total receives the
 // block's sum. Every thread must call it (it holds barriers); ws: 32 ints of shared memory.

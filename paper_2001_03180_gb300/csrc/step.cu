@@ -953,7 +953,7 @@ k_shift(int n, int npad, size_t stride, double Mtot, double* __restrict__ wb, co
   __shared__ double scratch[32];
   __shared__ double sc3[3];
   const int slot = blockIdx.y;
-  for (int c = 0; c < 3; ++c) sum_partials(comblk + (size_t)slot * nblk * 3 + c, nblk, 3, &sc3[c]);
+  sum_partials3(comblk + (size_t)slot * nblk * 3, nblk, sc3);
   double* wv = wb + slot * stride;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   double t2 = 0.0;
