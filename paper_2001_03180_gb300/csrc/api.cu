@@ -660,6 +660,8 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
     mstar_free(c);
     return code;
   };
+  prefer_shared_pair_kernels();
+  prefer_shared_step_kernels();
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
       prepare_rebuild(c) != cudaSuccess || prepare_division_cta(c) != cudaSuccess ||
       prepare_substep_cluster(c) != cudaSuccess)

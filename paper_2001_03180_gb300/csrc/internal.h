@@ -151,6 +151,10 @@ constexpr int kDcMaxSub = 1024;              // largest subgraph count the GPU b
 
 // pair.cu: slots [slot_lo, slot_hi) -> sa, Ublk. n_d as in params (0 = all Cartesian).
 cudaError_t launch_forces(mstar_ctx* c, int slot_lo, int slot_hi, int n_d);
+// at context creation: every kernel of an attempt prefers the largest shared-memory share, so that
+// the CTAs of different kernels can share an SM (a hint; nothing fails without it)
+void prefer_shared_pair_kernels();
+void prefer_shared_step_kernels();
 
 // step.cu
 cudaError_t launch_prepare(mstar_ctx* c);   // X0, V0, slot K copies, T0 partials

@@ -1370,6 +1370,21 @@ cudaError_t prepare_rebuild(mstar_ctx* c) {
   return cudaSuccess;
 }
 
+// The largest shared-memory share for the O(N) kernels of an attempt (see
+// prefer_shared_pair_kernels in pair.cu).
+void prefer_shared_step_kernels() {
+  const int sh = cudaSharedmemCarveoutMaxShared;
+  cudaFuncSetAttribute(k_rebuild_staged, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_rebuild, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_kick, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_drift, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_shift, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_init_drift, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_extrapolate, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaFuncSetAttribute(k_eps_final, cudaFuncAttributePreferredSharedMemoryCarveout, sh);
+  cudaGetLastError();
+}
+
 cudaError_t launch_extrapolate(mstar_ctx* c) {
   k_extrapolate<<<dim3(c->nblk, 2), 3 * kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B,
                                                                 c->d.parent, c->d.sX, c->d.sV, c->d.X0, c->d.V0,
