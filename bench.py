@@ -55,9 +55,9 @@ L2_FLUSH_BYTES = 256 << 20
 #  - DRAM bytes (read + write) of one launch by the number of division slots it evaluates;
 #    an attempt launches the kernel for 1 (step start), 8, 8, 7, 7, ..., 1, 1 slots;
 #  - the FP64 pipe's active fraction (sm__inst_executed_pipe_fp64 over its peak).
-PAIR_TILE_SRC_SHA = "0485359445a458ae"
-PAIR_TILE_PIPE_SRC_SHA = "0485359445a458ae"
-PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 0.174e6, 2: 0.498e6, 3: 1.290e6, 4: 2.621e6, 5: 3.578e6, 6: 4.652e6, 7: 6.052e6, 8: 11.827e6}
+PAIR_TILE_SRC_SHA = "54214f1fde9b5cd9"
+PAIR_TILE_PIPE_SRC_SHA = "54214f1fde9b5cd9"
+PAIR_TILE_DRAM_BYTES_BY_SLOTS = {1: 0.166e6, 2: 0.510e6, 3: 1.295e6, 4: 2.572e6, 5: 3.626e6, 6: 4.615e6, 7: 6.120e6, 8: 11.925e6}
 PAIR_TILE_FP64_PIPE_NCU = 0.870
 ATTEMPT_SLOT_PATTERN = [1] + [k for k in range(8, 0, -1) for _ in range(2)]
 # Algorithmic DRAM bytes of one force evaluation per body: positions 24 and mass 8 read,
