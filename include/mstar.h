@@ -85,8 +85,10 @@ typedef struct {
                         1, 2, 4 or 8, or 0 for the size rule (4 up to 512 bodies, else 1); the
                         other tiles take 1. Partial sums are added in warp order, so results
                         differ from the unsplit loop by rounding only. 0 */
-  int division_schedule; /* how an attempt's k_fix divisions are issued: 1 level by level (one
-                        launch per kernel for every division active at that substep), 2 each
+  int division_schedule; /* how an attempt's k_fix divisions are issued: 1 level by level (the
+                        kernels of a substep level for every division active at it: one CTA per
+                        division for up to 256 padded bodies, a thread-block cluster per division
+                        for up to 576, else one launch per kernel; all bit-identical), 2 each
                         division on its own stream (longer divisions at higher priority), so that
                         one division's small kernels overlap another's pair loop, 3 each division
                         on one CTA, or a cluster of them (division_cluster), from its first drift
@@ -133,7 +135,10 @@ MSTAR_API int mstar_init(mstar_ctx** out, int n, const double* m, const double* 
    or max_gbs_steps steps were accepted, or max_time_iter clamped steps were taken.
    Each step: MST (Prim), edge coordinates, one pair-loop evaluation at the step start
    (for the error norm's S'), k_fix concurrent leapfrog divisions, Neville-Aitken
-   extrapolation, the convergence test; rejected steps are retried with H/2.
+   extrapolation, the convergence test; rejected steps are retried with H/2. Once the
+   controller's step is known, a step's first attempt is issued right behind its preparation
+   and U0 is read back with that attempt's result; when the clamp to t_end then applies, that
+   attempt is discarded and the clamped one taken, so the steps are those of reading U0 first.
    out (may be NULL) receives the counters of this call. Errors: NO_CONVERGENCE, CUDA. */
 MSTAR_API int mstar_step(mstar_ctx* ctx, double t_end, int max_gbs_steps, mstar_stats* out);
 
