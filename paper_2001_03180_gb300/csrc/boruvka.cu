@@ -64,8 +64,22 @@ __global__ void __launch_bounds__(kBT)
 k_nfn(int n, int npad, int nparts, const double* __restrict__ X, const double* __restrict__ Y,
       const double* __restrict__ Z, const float* __restrict__ f4, const int* __restrict__ comp,
       const int* __restrict__ nbr, unsigned long long* __restrict__ partD, int* __restrict__ partJ,
-      int* __restrict__ tie, const int* __restrict__ stop) {
-  if (*stop) return;
+      int* __restrict__ flags) {
+  // The round's gate: flags[2] = 1 once the tree is complete (flags[1] = n - 1 edges, written
+  // by the previous round's k_hook) or a tie has been seen (flags[0]); the round's kernels then
+  // return at once, and flags[3] counts the rounds that ran. Rounds can thus be issued ahead of
+  // the host's check: a round after the last one needed changes nothing (without the gate it
+  // would find no foreign neighbour and report a tie). The search opens every round, so its
+  // first CTA publishes the decision for the round's later kernels (none of which writes
+  // flags[2]). A tie set by another CTA while the search runs can make CTAs decide differently;
+  // the build then falls back to the Prim kernel, so nothing of that round is used.
+  const bool stop = (flags[0] != 0) || (flags[1] >= n - 1);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+    flags[2] = stop;
+    if (!stop) flags[3] += 1;
+  }
+  if (stop) return;
+  int* tie = flags;
   __shared__ float sx[kBT], sy[kBT], sz[kBT], se[kBT];
   __shared__ int sc[kBT];
   __shared__ int slist[kNfnList][kBT];
@@ -237,17 +251,6 @@ __global__ void k_relabel(int n, int* __restrict__ comp, const int* __restrict__
   comp[i] = c;
   cmin[i] = ~0ull;
   ccnt[i] = 0;
-}
-
-// The gate of a round: flags[2] = 1 once the tree is complete (flags[1] = n - 1 edges) or a
-// tie has been seen (flags[0]); the round's six kernels then return at once. flags[3] counts
-// the rounds that ran. Rounds can thus be issued ahead of the host's check: a round issued
-// after the last one needed changes nothing (without the gate it would find no foreign
-// neighbour and report a tie). No kernel of a round writes flags[2].
-__global__ void k_round_gate(int n, int* __restrict__ flags) {
-  const int stop = (flags[0] != 0) || (flags[1] >= n - 1);
-  flags[2] = stop;
-  if (!stop) flags[3] += 1;
 }
 
 __global__ void k_boruvka_init(int n, const double* __restrict__ X, const double* __restrict__ Y,
@@ -486,16 +489,15 @@ cudaError_t launch_mst_boruvka(mstar_ctx* c, bool* tied) {
   while (round < 64 && edges < n - 1) {
     const int batch = round == 0 ? (c->mst_rounds > 0 ? c->mst_rounds : 1) : 1;
     for (int b = 0; b < batch && round < 64; ++b, ++round) {
-      k_round_gate<<<1, 1, 0, c->stream>>>(n, flags);
       k_nfn<<<dim3((n + kBT - 1) / kBT, nparts), kBT, 0, c->stream>>>(n, npad, nparts, X, Y, Z, f4, comp, nbr,
-                                                                       partD, partJ, flags, flags + 2);
+                                                                       partD, partJ, flags);
       k_nfn_merge<<<(n + 63) / 64, 64, 0, c->stream>>>(n, npad, nparts, comp, nbr, nbrD, partD, partJ, flags,
                                                        flags + 2);
       k_comp_min<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, flags + 2);
       k_comp_edge<<<nb, 256, 0, c->stream>>>(n, comp, nbrD, cmin, cidx, ccnt, flags, flags + 2);
       k_hook<<<nb, 256, 0, c->stream>>>(n, comp, nbr, cidx, nxt, eu, ev, flags + 1, flags + 2);
       k_relabel<<<nb, 256, 0, c->stream>>>(n, comp, nxt, cmin, ccnt, flags + 2);
-      c->launches += 7;
+      c->launches += 6;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = cudaMemcpyAsync(c->host_buf, flags, sizeof(int) * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
