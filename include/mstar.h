@@ -136,9 +136,10 @@ MSTAR_API int mstar_init(mstar_ctx** out, int n, const double* m, const double* 
    Each step: MST (Prim), edge coordinates, one pair-loop evaluation at the step start
    (for the error norm's S'), k_fix concurrent leapfrog divisions, Neville-Aitken
    extrapolation, the convergence test; rejected steps are retried with H/2. Once the
-   controller's step is known, a step's first attempt is issued right behind its preparation
-   and U0 is read back with that attempt's result; when the clamp to t_end then applies, that
-   attempt is discarded and the clamped one taken, so the steps are those of reading U0 first.
+   controller's step is known, a step's first attempt is issued right behind the MST and edge
+   coordinates, runs the step-start evaluation beside its divisions, and U0 is read back with
+   that attempt's result; when the clamp to t_end then applies, that attempt is discarded and
+   the clamped one taken, so the steps are those of reading U0 first.
    out (may be NULL) receives the counters of this call. Errors: NO_CONVERGENCE, CUDA. */
 MSTAR_API int mstar_step(mstar_ctx* ctx, double t_end, int max_gbs_steps, mstar_stats* out);
 

@@ -214,10 +214,10 @@ void prof_flush(mstar_ctx* c) {
 
 // --------------------------------------------------------------------------- the GBS step
 
-// MST of the current positions, edge coordinates, and the derivative information at the
-// step start (one force evaluation), issued without reading anything back (the MST builders
-// may synchronise for their own checks); U0 and T0 land in d.res[2], d.res[3].
-int issue_prepare(mstar_ctx* c) {
+// MST of the current positions and the edge coordinates (with the step start's kinetic
+// partials), issued without reading anything back (the MST builders may synchronise for their
+// own checks).
+int issue_tree_and_edges(mstar_ctx* c) {
   if (!c->mst_valid) {
     if (c->p.mst_method == 1) {
       CK(launch_mst_dc(c));
@@ -230,9 +230,22 @@ int issue_prepare(mstar_ctx* c) {
     c->mst_valid = true;
   }
   CK(launch_prepare(c));
+  return MSTAR_OK;
+}
+
+// The step-start force evaluation and the derivative information it gives (A0; U0 and T0 into
+// d.res[2], d.res[3] and the step-start slot's scalars).
+int issue_start_eval(mstar_ctx* c) {
   CK(launch_forces(c, c->K, c->K + 1, c->p.n_d));
   CK(launch_start_derivs(c));
   return MSTAR_OK;
+}
+
+// issue_tree_and_edges, then issue_start_eval.
+int issue_prepare(mstar_ctx* c) {
+  int rc = issue_tree_and_edges(c);
+  if (rc) return rc;
+  return issue_start_eval(c);
 }
 
 // issue_prepare, then U0 and T0 read back.
@@ -254,11 +267,33 @@ int prepare_step(mstar_ctx* c, double* U0, double* T0) {
 // With a trajectory record the states of every level are saved on the way.
 int issue_attempt_branched(mstar_ctx* c);
 
+// With c->att_start: the step-start force evaluation on st_stream, forked from the context's
+// stream before anything of the attempt, and joined before the extrapolation.
+int fork_start_eval(mstar_ctx* c) {
+  if (!c->att_start) return MSTAR_OK;
+  cudaStream_t main_stream = c->stream;
+  CK(cudaEventRecord(c->st_fork, main_stream));
+  CK(cudaStreamWaitEvent(c->st_stream, c->st_fork, 0));
+  c->stream = c->st_stream;
+  int rc = issue_start_eval(c);
+  if (!rc && cudaEventRecord(c->st_join, c->stream) != cudaSuccess) rc = MSTAR_ERR_CUDA;
+  c->stream = main_stream;
+  return rc;
+}
+
+int join_start_eval(mstar_ctx* c) {
+  if (c->att_start) CK(cudaStreamWaitEvent(c->stream, c->st_join, 0));
+  return MSTAR_OK;
+}
+
 int issue_attempt(mstar_ctx* c) {
   // attempts that record a trajectory, time the pair kernel or serve the adjoint go level by level
   const bool plain = !c->traj && !c->prof && !c->levelled;
+  int rc = fork_start_eval(c);
+  if (rc) return rc;
   if (plain && c->div_cta) {
     CK(launch_division_cta(c));
+    if ((rc = join_start_eval(c))) return rc;
     CK(launch_extrapolate(c));
     return MSTAR_OK;
   }
@@ -313,6 +348,7 @@ int issue_attempt(mstar_ctx* c) {
       CK(launch_rebuild(c, c->d.sX + lo2 * st, c->d.sr + lo2 * st, st, K - lo2, 0, nullptr,
                         c->d.comblk + (size_t)lo2 * c->nblk * 3));
   }
+  if ((rc = join_start_eval(c))) return rc;
   CK(launch_extrapolate(c));
   return MSTAR_OK;
 }
@@ -356,6 +392,8 @@ int issue_attempt_branched(mstar_ctx* c) {
   c->stream = main_stream;
   CK(e);
   for (int k = 0; k < K; ++k) CK(cudaStreamWaitEvent(main_stream, c->br_join[k], 0));
+  const int rc = join_start_eval(c);
+  if (rc) return rc;
   CK(launch_extrapolate(c));
   return MSTAR_OK;
 }
@@ -403,29 +441,42 @@ cudaGraphExec_t build_attempt_graph(mstar_ctx* c) {
     c->att_graph_off = true;
     return nullptr;
   }
-  c->att_graphs.push_back({c->traj, c->levelled, exec});
+  c->att_graphs.push_back({c->traj, c->levelled, c->att_start, exec, c->att_launches, c->att_evals});
   return exec;
 }
 
 // One attempt with fictitious step H; reads eps and the extrapolated time back. Without
-// profiling the attempt is one graph launch.
-int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew) {
+// profiling the attempt is one graph launch. With start, the attempt also runs the step-start
+// force evaluation (issue_start_eval) beside its divisions; U0 and T0 are then read back with
+// eps and t.
+int run_attempt(mstar_ctx* c, double H, double* eps, double* tnew, bool start = false) {
   CK(stage_attempt_scalars(c, H));
+  c->att_start = start;
   cudaGraphExec_t exec = nullptr;
+  long long g_launches = 0, g_evals = 0;
   if (!c->prof && !c->att_graph_off) {
     for (const auto& ag : c->att_graphs)
-      if (ag.traj == c->traj && ag.levelled == c->levelled) exec = ag.exec;
-    if (!exec) exec = build_attempt_graph(c);
+      if (ag.traj == c->traj && ag.levelled == c->levelled && ag.start == start) {
+        exec = ag.exec;
+        g_launches = ag.launches;
+        g_evals = ag.evals;
+      }
+    if (!exec && (exec = build_attempt_graph(c))) {
+      g_launches = c->att_launches;
+      g_evals = c->att_evals;
+    }
   }
+  int rc = MSTAR_OK;
   if (exec) {
-    CK(cudaGraphLaunch(exec, c->stream));
-    c->launches += c->att_launches;
-    c->force_evals += c->att_evals;
+    if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) rc = MSTAR_ERR_CUDA;
+    c->launches += g_launches;
+    c->force_evals += g_evals;
   } else {
-    const int rc = issue_attempt(c);
-    if (rc) return rc;
+    rc = issue_attempt(c);
   }
-  int rc = sync_read_res(c);
+  c->att_start = false;
+  if (rc) return rc;
+  rc = sync_read_res(c);
   if (rc) return rc;
   prof_flush(c);
   *eps = c->host_res[0];
@@ -589,6 +640,9 @@ void mstar_free(mstar_ctx* c) {
     if (c->br_join[k]) cudaEventDestroy(c->br_join[k]);
   }
   if (c->br_fork) cudaEventDestroy(c->br_fork);
+  if (c->st_stream) cudaStreamDestroy(c->st_stream);
+  if (c->st_fork) cudaEventDestroy(c->st_fork);
+  if (c->st_join) cudaEventDestroy(c->st_join);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->host_res) cudaFreeHost(c->host_res);
   if (c->host_buf) cudaFreeHost(c->host_buf);
@@ -665,6 +719,10 @@ int mstar_init(mstar_ctx** out, int n, const double* m, const double* r, const d
   if (cudaMemsetAsync(c->ws, 0, need, c->stream) != cudaSuccess || upload_step_constants(c) != cudaSuccess ||
       prepare_rebuild(c) != cudaSuccess || prepare_division_cta(c) != cudaSuccess ||
       prepare_substep_cluster(c) != cudaSuccess)
+    return bail(MSTAR_ERR_CUDA);
+  if (cudaStreamCreateWithFlags(&c->st_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->st_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->st_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(MSTAR_ERR_CUDA);
   if (c->branched) {  // the streams and events of the per-division attempt graph
     if (cudaEventCreateWithFlags(&c->br_fork, cudaEventDisableTiming) != cudaSuccess) return bail(MSTAR_ERR_CUDA);
@@ -890,8 +948,11 @@ int mstar_step(mstar_ctx* c, double t_end, int max_gbs_steps, mstar_stats* out) 
     // the clamped one run: the steps taken are the same as with U0 read first.
     bool have_attempt = false;
     if (c->H != 0.0) {
-      if ((rc = issue_prepare(c))) break;
-      if ((rc = run_attempt(c, std::fabs(c->H) * (dt < 0 ? -1.0 : 1.0), &eps, &tn))) break;
+      // the step-start force evaluation runs inside the attempt, beside its divisions, where the
+      // attempt replays as a graph (profiled attempts keep it ahead of the attempt)
+      const bool beside = !c->prof && !c->att_graph_off && c->st_stream;
+      if ((rc = beside ? issue_tree_and_edges(c) : issue_prepare(c))) break;
+      if ((rc = run_attempt(c, std::fabs(c->H) * (dt < 0 ? -1.0 : 1.0), &eps, &tn, beside))) break;
       U0 = c->host_res[2];
       T0 = c->host_res[3];
       have_attempt = true;

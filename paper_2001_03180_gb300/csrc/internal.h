@@ -118,8 +118,16 @@ struct mstar_ctx {
   struct AttGraph {
     const mstar::AdjTraj* traj;
     bool levelled;
+    bool start;  // the graph also runs the step-start force evaluation, beside the divisions
     cudaGraphExec_t exec;
+    long long launches, evals;  // kernel launches and force evaluations per replay
   };
+  // attempts issued with att_start run the step-start force evaluation (and the derivatives that
+  // end it) on st_stream beside the divisions, joined before the extrapolation, the only kernel
+  // of an attempt that reads its results
+  bool att_start = false;
+  cudaStream_t st_stream = nullptr;
+  cudaEvent_t st_fork = nullptr, st_join = nullptr;
   cudaStream_t cap = nullptr;
   std::vector<AttGraph> att_graphs;
   bool att_graph_off = false;  // capture failed once: launch directly

@@ -90,11 +90,15 @@ k_start_derivs(int n, int npad, int K, const int* __restrict__ parent, const dou
 __global__ void __launch_bounds__(kBlock)
 k_init_drift(int n, int npad, int K, const double* __restrict__ par, double B, const double* __restrict__ X0,
              const double* __restrict__ V0, double* __restrict__ sX, double* __restrict__ sV,
-             double* __restrict__ sc) {
+             double* __restrict__ sc, const double* __restrict__ Tblk, int nblk) {
+  __shared__ double sT;
   const double H = par[0], t0 = par[1];  // the attempt's fictitious step and start time
   const int slot = blockIdx.y;
   const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  const double T0 = sc[K * kScal + SC_T_KIN];
+  // T0 as k_start_derivs forms it, from the step start's kinetic partials (the step-start force
+  // evaluation, which k_start_derivs ends, may still be running beside the divisions)
+  sum_partials(Tblk + (size_t)K * nblk, nblk, 1, &sT);
+  const double T0 = 0.5 * sT;
   const double delta = H / (double)(2 * (slot + 1));
   const double f = (0.5 * delta) / (T0 + B);
   if (w < npad) {
@@ -609,7 +613,7 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
                double Mtot, const double* __restrict__ m, const int* __restrict__ parent, const int* __restrict__ gp,
                const int* __restrict__ child_off, const int* __restrict__ child_idx, const int* __restrict__ bylev,
                const double* __restrict__ X0, const double* __restrict__ V0, double* __restrict__ sX,
-               double* __restrict__ sV, double* __restrict__ sc) {
+               double* __restrict__ sV, double* __restrict__ sc, const double* __restrict__ Tblk, int nblk) {
   // shared: edge positions X and velocities V, Cartesian positions sx, accelerations sA (3 npad
   // each), masses (npad), two buffers of the CTA's tasks' partials (kDivisionCtaThreads / 32
   // tasks x 7 planes of 32: the i-side ax, ay, az, m/r sums, then the j-side sums), two buffers
@@ -636,7 +640,9 @@ k_division_cta(int n, int npad, int K, int n_d, double G, const double* __restri
   const int nb = npad >> 5;  // warps per component
   const size_t st = (size_t)3 * npad;
   const double H = par[0], t0 = par[1];
-  const double T0 = sc[K * kScal + SC_T_KIN];
+  __shared__ double sT0;
+  sum_partials(Tblk + (size_t)K * nblk, nblk, 1, &sT0);  // T0 as k_start_derivs forms it
+  const double T0 = 0.5 * sT0;
   const int nk = 2 * (slot + 1);
   const double delta = H / (double)nk;
   for (int u = tid; u < npad; u += blockDim.x) {
@@ -1123,7 +1129,7 @@ cudaError_t stage_attempt_scalars(mstar_ctx* c, double H) {
 cudaError_t launch_init_drift(mstar_ctx* c) {
   dim3 grid(c->nblk, c->K);
   k_init_drift<<<grid, kBlock, 0, c->stream>>>(c->n, c->npad, c->K, c->d.res + 4, c->B, c->d.X0, c->d.V0, c->d.sX,
-                                              c->d.sV, c->d.sc);
+                                              c->d.sV, c->d.sc, c->d.Tblk, c->nblk);
   MSTAR_LAUNCHED(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1233,7 +1239,7 @@ cudaError_t launch_division_cta_c(mstar_ctx* c) {
                             (const double*)(c->d.res + 4), c->B, c->Mtot, (const double*)c->d.m,
                             (const int*)c->d.parent, (const int*)c->d.gp, (const int*)c->d.child_off,
                             (const int*)c->d.child_idx, (const int*)c->d.bylev, (const double*)c->d.X0,
-                            (const double*)c->d.V0, c->d.sX, c->d.sV, c->d.sc);
+                            (const double*)c->d.V0, c->d.sX, c->d.sV, c->d.sc, (const double*)c->d.Tblk, c->nblk);
 }
 
 // Every division of an attempt, from the first half drift to the last drift, in one launch
